@@ -1,0 +1,110 @@
+"""Forces and the four-stage time step (Sec. II.D).
+
+Test infrastructure only (see ``oracle/__init__``).
+
+Parameters come in a plain dict `p` (reduced units: Delta r = 1, kT given,
+eps = 1/(4 pi l_B)):
+  dims (Nx, Ny, Nz); bc (bottom, top) 0 = Dirichlet, 1 = Neumann; phi_b;
+  surf_charge; kernel_es, kernel_hy (kernels.Kernel); lB; eta; kT; dt; psi;
+  fp_table; lj_sigma/lj_xi/lj_rc [ns][ns]; wall_sigma/wall_xi/wall_rc [ns];
+  wall_type; E_ext (3,); gamma_coef [ns][2][2][7]; D_tot, D_wet [ns];
+  wet, drift (bools); seed.
+
+Stage 1: rho = S^es q, Poisson (Eq. poisson).  Stage 2: E^P = J^es(-grad phi)
+(Eq. efieldop), F = q E^P + near field (Eqs. fullElectro, LC) + LJ
+(Eq. closerange) + wall + q E_ext (Eq. totalforce).  Stage 3: f = S^hy F +
+f_th + stochastic stress, Stokes solve.  Stage 4: midpoint update
+(Eqs. step1-step2) with the dry tensor of Eqs. diff1-diff2 and its Ito drift
+(Eq. ions3).  A dry-only step (no hydrodynamic grid) is Euler-Maruyama on
+Eq. ions3 with V = 0.
+"""
+import numpy as np
+
+from . import gridops, poisson, particles, mobility, stokes, philox
+
+
+def electrostatic_field(p, pos, q):
+    """(rho, phi, E^P at the ions)."""
+    dims = p['dims']
+    rho = gridops.spread_charge(p['kernel_es'], pos, q, dims, p['bc'])
+    phi = poisson.solve(rho, p['bc'], p['lB'], p['phi_b'], p['surf_charge'])
+    slopes = poisson.wall_slopes(p['bc'], p['surf_charge'], p['lB'])
+    E = gridops.efield_at_ions(p['kernel_es'], pos, phi, p['bc'], p['phi_b'], slopes)
+    return rho, phi, E
+
+
+def forces(p, pos, q, species, pair_dtype=np.float64):
+    """Total force, Eq. totalforce.  Returns (F (3,N), counts, parts dict)."""
+    rho, phi, E = electrostatic_field(p, pos, q)
+    Fp = q[None, :] * E
+    Fn, counts = particles.near_field(pos, q, species, p, p['fp_table'], pair_dtype)
+    Fw = particles.wall_force(pos, species, p)
+    F = Fp + Fn
+    F[1] += Fw
+    F += q[None, :] * np.asarray(p['E_ext'], dtype=np.float64)[:, None]
+    return F, counts, dict(rho=rho, phi=phi, E=E, Fp=Fp, Fn=Fn, Fw=Fw)
+
+
+def wrap_reflect(pos, dims):
+    """Periodic wrap in x, z (one shift) and specular reflection at the walls."""
+    Nx, Ny, Nz = dims
+    x = pos.copy()
+    for d, L in ((0, Nx), (2, Nz)):
+        x[d] = np.where(x[d] < 0, x[d] + L, np.where(x[d] >= L, x[d] - L, x[d]))
+    y = x[1]
+    x[1] = np.where(y < 0, -y, np.where(y > Ny, 2.0 * Ny - y, y))
+    return x
+
+
+def dry_increment(p, pos, species, F, step, replica=0, first_index=0):
+    """Dry part of Eq. ions3 over one step: dt (D Gamma F / kT + div D) +
+    sqrt(2 dt D Gamma) W, W from Philox tag 1."""
+    Ny = p['dims'][1]
+    sp_ = np.asarray(species)
+    Dd = (np.asarray(p['D_tot']) - np.asarray(p['D_wet']))[sp_]
+    G, dGp = mobility.dry_tensor(pos[1], Ny, species, p)
+    W = philox.ion_normals(pos.shape[1], step, replica, philox.TAG_DRY, p['seed'], first_index)
+    inc = p['dt'] * (Dd[None, :] * G * F / p['kT'])
+    if p.get('drift', True):
+        inc[1] += p['dt'] * Dd * dGp
+    inc += np.sqrt(2.0 * p['dt'] * Dd[None, :] * np.maximum(G, 0.0)) * W
+    return inc
+
+
+def dry_step(p, pos, q, species, step, pair_dtype=np.float64):
+    """One Euler-Maruyama step of the dry-diffusion dynamics."""
+    F, counts, parts = forces(p, pos, q, species, pair_dtype)
+    new = wrap_reflect(pos + dry_increment(p, pos, species, F, step), p['dims'])
+    return new, F, counts
+
+
+def fluid_forcing(p, pos, F, step):
+    """f = S^hy F + f_th + stochastic stress (each optional by flags)."""
+    dims = p['dims']
+    fx, fy, fz = gridops.spread_force(p['kernel_hy'], pos, F, dims)
+    if p.get('drift', True) and p['kT'] > 0:
+        tx, ty, tz = stokes.rfd_forcing(p['kernel_hy'], pos, dims, p['kT'], step, 0, p['seed'])
+        fx, fy, fz = fx + tx, fy + ty, fz + tz
+    if p['kT'] > 0:
+        nx, ny, nz = stokes.noise_forcing(dims, p['eta'], p['kT'], p['dt'], step, 0, p['seed'])
+        fx, fy, fz = fx + nx, fy + ny, fz + nz
+    fy = fy.copy()
+    fy[:, 0, :] = 0.0
+    fy[:, -1, :] = 0.0
+    return fx, fy, fz
+
+
+def wet_step(p, pos, q, species, step, pair_dtype=np.float64):
+    """One step of the four-stage algorithm with the midpoint scheme."""
+    F, counts, parts = forces(p, pos, q, species, pair_dtype)
+    fx, fy, fz = fluid_forcing(p, pos, F, step)
+    u, v, w, pr = stokes.solve(fx, fy, fz, p['eta'])
+    V1 = gridops.interp_velocity(p['kernel_hy'], pos, u, v, w)
+    if p.get('drift', True):
+        xs = pos + 0.5 * p['dt'] * V1
+        V = gridops.interp_velocity(p['kernel_hy'], xs, u, v, w)
+    else:
+        V = V1
+    inc = p['dt'] * V + dry_increment(p, pos, species, F, step)
+    new = wrap_reflect(pos + inc, p['dims'])
+    return new, F, counts, dict(parts, u=u, v=v, w=w, p=pr, V1=V1, V=V)

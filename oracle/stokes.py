@@ -1,0 +1,163 @@
+"""Staggered (MAC) steady Stokes solve with no-slip walls, stochastic stress
+and RFD thermal forcing.
+
+Test infrastructure only (see ``oracle/__init__``).
+
+Eq. disc_stokes / stokes_temporal:  grad_h p - eta lap_h v = f,  div_h v = 0,
+on the MAC grid (normal velocities on faces, p at centres), periodic in x and
+z, no-slip walls at y = 0 and y = Ny (Eq. fluidbc): v_y = 0 on the wall faces,
+tangential ghosts u(-1) = -u(0) so the velocity vanishes on the wall.  The
+saddle-point system is assembled in full, with the pressure gauge
+sum(p) = 0 added by bordering, and solved by a sparse direct solver.
+
+Stochastic forcing sqrt(2 kT eta / (dV dt)) div_h Z (Eq. stokes_temporal),
+reading of the cited staggered construction: Z symmetric, diagonal entries
+sqrt(2) N(0,1) at cell centres, off-diagonal entries N(0,1) on edges (xy:
+(x=i, y=j), j = 0..Ny; xz: (x=i, z=k); yz: (y=j, z=k), j = 0..Ny), with the
+off-diagonal entries on the wall edges (y = 0, Ny) scaled by sqrt(2) so that
+the noise covariance D D^T equals -L + Div^T Div with L the no-slip viscous
+operator (fluctuation-dissipation balance; checked in the tests).  Normals
+come from Philox counters (cell index in an Nx * (Ny+1) * Nz lattice, step,
+replica, tag): tag 3 gives (Zxx, Zyy, Zzz, Zxy), tag 4 gives (Zxz, Zyz, -, -).
+
+Thermal forcing, Eq. thermforce, by random finite differences (only cited;
+reading): f_th = (kT/delta) [S(x + delta W/2) W - S(x - delta W/2) W] with W
+from Philox tag 2 per ion and delta = 1e-4.
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import gridops, philox
+
+
+def _ops(dims):
+    """Sparse blocks: (Lu, Lv, Lw) = -lap_h with no-slip rules, gradients and
+    divergences.  Unknown layout: u (Nz,Ny,Nx), v interior (Nz,Ny-1,Nx) for
+    faces j = 1..Ny-1, w (Nz,Ny,Nx), p (Nz,Ny,Nx)."""
+    Nx, Ny, Nz = dims
+    nc = Nx * Ny * Nz
+    nv = Nx * (Ny - 1) * Nz
+    ic = np.arange(nc).reshape(Nz, Ny, Nx)
+    iv = np.arange(nv).reshape(Nz, Ny - 1, Nx)
+
+    def lap_cell():
+        r, c, v = [], [], []
+        for ax in (0, 2):
+            for sh in (1, -1):
+                r.append(ic.ravel()); c.append(np.roll(ic, sh, axis=ax).ravel()); v.append(-np.ones(nc))
+        r.append(ic[:, 1:, :].ravel()); c.append(ic[:, :-1, :].ravel()); v.append(-np.ones(ic[:, 1:, :].size))
+        r.append(ic[:, :-1, :].ravel()); c.append(ic[:, 1:, :].ravel()); v.append(-np.ones(ic[:, 1:, :].size))
+        d = np.full((Nz, Ny, Nx), 6.0)
+        d[:, 0, :] += 1.0       # ghost u(-1) = -u(0)
+        d[:, -1, :] += 1.0
+        r.append(ic.ravel()); c.append(ic.ravel()); v.append(d.ravel())
+        return sp.csr_matrix((np.concatenate(v), (np.concatenate(r), np.concatenate(c))), shape=(nc, nc))
+
+    def lap_face():
+        r, c, v = [], [], []
+        for ax in (0, 2):
+            for sh in (1, -1):
+                r.append(iv.ravel()); c.append(np.roll(iv, sh, axis=ax).ravel()); v.append(-np.ones(nv))
+        r.append(iv[:, 1:, :].ravel()); c.append(iv[:, :-1, :].ravel()); v.append(-np.ones(iv[:, 1:, :].size))
+        r.append(iv[:, :-1, :].ravel()); c.append(iv[:, 1:, :].ravel()); v.append(-np.ones(iv[:, 1:, :].size))
+        r.append(iv.ravel()); c.append(iv.ravel()); v.append(np.full(nv, 6.0))   # wall faces v = 0
+        return sp.csr_matrix((np.concatenate(v), (np.concatenate(r), np.concatenate(c))), shape=(nv, nv))
+
+    # gradients (cell -> face)
+    Gx = sp.csr_matrix((np.concatenate([np.ones(nc), -np.ones(nc)]),
+                        (np.concatenate([ic.ravel(), ic.ravel()]),
+                         np.concatenate([ic.ravel(), np.roll(ic, 1, axis=2).ravel()]))), shape=(nc, nc))
+    Gz = sp.csr_matrix((np.concatenate([np.ones(nc), -np.ones(nc)]),
+                        (np.concatenate([ic.ravel(), ic.ravel()]),
+                         np.concatenate([ic.ravel(), np.roll(ic, 1, axis=0).ravel()]))), shape=(nc, nc))
+    # y-face j (1..Ny-1) = iv[:, j-1]: p(j) - p(j-1)
+    Gy = sp.csr_matrix((np.concatenate([np.ones(nv), -np.ones(nv)]),
+                        (np.concatenate([iv.ravel(), iv.ravel()]),
+                         np.concatenate([ic[:, 1:, :].ravel(), ic[:, :-1, :].ravel()]))), shape=(nv, nc))
+    Lc = lap_cell()
+    return Lc, lap_face(), Lc, Gx, Gy, Gz
+
+
+def solve(fx, fy, fz, eta):
+    """Velocity (u on x-faces, v on y-faces incl. zero wall faces, w) and p.
+
+    fy has shape (Nz, Ny+1, Nx); its wall rows are ignored.
+    """
+    Nz, Ny, Nx = fx.shape
+    dims = (Nx, Ny, Nz)
+    Lu, Lv, Lw, Gx, Gy, Gz = _ops(dims)
+    nc = Nx * Ny * Nz
+    nv = Nx * (Ny - 1) * Nz
+    Z = None
+    ones = sp.csr_matrix(np.ones((nc, 1)))
+    A = sp.bmat([
+        [eta * Lu, None, None, Gx, None],
+        [None, eta * Lv, None, Gy, None],
+        [None, None, eta * Lw, Gz, None],
+        [-Gx.T, -Gy.T, -Gz.T, None, ones],
+        [None, None, None, ones.T, None]], format='csc')
+    b = np.concatenate([fx.ravel(), fy[:, 1:Ny, :].ravel(), fz.ravel(), np.zeros(nc), [0.0]])
+    x = spla.spsolve(A, b)
+    u = x[:nc].reshape(Nz, Ny, Nx)
+    v = np.zeros((Nz, Ny + 1, Nx))
+    v[:, 1:Ny, :] = x[nc:nc + nv].reshape(Nz, Ny - 1, Nx)
+    w = x[nc + nv:2 * nc + nv].reshape(Nz, Ny, Nx)
+    p = x[2 * nc + nv:3 * nc + nv].reshape(Nz, Ny, Nx)
+    return u, v, w, p
+
+
+def divergence(u, v, w):
+    """div_h v at cell centres."""
+    return (np.roll(u, -1, axis=2) - u) + (v[:, 1:, :] - v[:, :-1, :]) + (np.roll(w, -1, axis=0) - w)
+
+
+def stress_fields(dims, step, replica, seed):
+    """Z components from Philox: centres (Zxx, Zyy, Zzz), edges (Zxy, Zxz, Zyz)
+    on an (Nz, Ny+1, Nx) lattice, wall edges of Zxy and Zyz scaled by sqrt 2."""
+    Nx, Ny, Nz = dims
+    cell = np.arange(Nx * (Ny + 1) * Nz, dtype=np.uint64)
+    a = philox.normals4(cell, step, replica, philox.TAG_STRESS_A, seed)
+    b = philox.normals4(cell, step, replica, philox.TAG_STRESS_B, seed)
+    sh = (Nz, Ny + 1, Nx)
+    Zxx = np.sqrt(2.0) * a[0].reshape(sh)[:, :Ny, :]
+    Zyy = np.sqrt(2.0) * a[1].reshape(sh)[:, :Ny, :]
+    Zzz = np.sqrt(2.0) * a[2].reshape(sh)[:, :Ny, :]
+    Zxy = a[3].reshape(sh).copy()
+    Zxz = b[0].reshape(sh)[:, :Ny, :]
+    Zyz = b[1].reshape(sh).copy()
+    for Zw in (Zxy, Zyz):
+        Zw[:, 0, :] *= np.sqrt(2.0)
+        Zw[:, Ny, :] *= np.sqrt(2.0)
+    return Zxx, Zyy, Zzz, Zxy, Zxz, Zyz
+
+
+def stress_divergence(Zxx, Zyy, Zzz, Zxy, Zxz, Zyz):
+    """div_h Z on the faces.  Edge placement: Zxy[k, j, i] at (x=i, y=j),
+    Zxz[k, j, i] at (x=i, z=k), Zyz[k, j, i] at (y=j, z=k)."""
+    Nz, Ny, Nx = Zxx.shape
+    dx = (Zxx - np.roll(Zxx, 1, axis=2)) + (Zxy[:, 1:, :] - Zxy[:, :-1, :]) \
+        + (np.roll(Zxz, -1, axis=0) - Zxz)
+    dy = np.zeros((Nz, Ny + 1, Nx))
+    dy[:, 1:Ny, :] = (np.roll(Zxy, -1, axis=2)[:, 1:Ny, :] - Zxy[:, 1:Ny, :]) \
+        + (Zyy[:, 1:, :] - Zyy[:, :-1, :]) \
+        + (np.roll(Zyz, -1, axis=0)[:, 1:Ny, :] - Zyz[:, 1:Ny, :])
+    dz = (np.roll(Zxz, -1, axis=2) - Zxz) + (Zyz[:, 1:, :] - Zyz[:, :-1, :]) \
+        + (Zzz - np.roll(Zzz, 1, axis=0))
+    return dx, dy, dz
+
+
+def noise_forcing(dims, eta, kT, dt, step, replica, seed):
+    amp = np.sqrt(2.0 * kT * eta / dt)
+    Z = stress_fields(dims, step, replica, seed)
+    dx, dy, dz = stress_divergence(*Z)
+    return amp * dx, amp * dy, amp * dz
+
+
+def rfd_forcing(kernel, pos, dims, kT, step, replica, seed, delta=1e-4, first_index=0):
+    """Thermal forcing f_th by random finite differences (reading above)."""
+    N = pos.shape[1]
+    W = philox.ion_normals(N, step, replica, philox.TAG_RFD, seed, first_index)
+    plus = gridops.spread_force(kernel, pos + 0.5 * delta * W, W, dims)
+    minus = gridops.spread_force(kernel, pos - 0.5 * delta * W, W, dims)
+    return tuple((kT / delta) * (a - b) for a, b in zip(plus, minus))
