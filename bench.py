@@ -1,0 +1,289 @@
+"""Throughput of the DISCOS wall-bounded hot path on GB300.
+
+Workload (one GPU): a 128 x 64 x 128 channel with dielectric (Neumann) walls,
+20,000 +-1 ions, Debye length ~4 cells, E_x = 0.05, full wet step (cell
+list, charge spreading, Poisson, field interpolation, P3M near field with
+images, LJ and wall forces, force spreading with RFD thermal forcing,
+stochastic stress, staggered Stokes, two velocity interpolations, midpoint
+update with the near-wall dry tensor), single-precision bulk with double
+wall-normal solves.  One step = one pass of that path over all ions.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica (the path does not
+shard; replicas only) and rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ion-timesteps/s"
+WORKLOAD = "wet_channel_128x64x128: 128x64x128 cells, Neumann walls, 20000 ions, full wet step, FP32+FP64 islands"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def clocks_sampler():
+    """Start nvidia-smi sampling of clocks and throttle reasons; returns a stop fn."""
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    path = os.path.join("/tmp", f"discos_clocks_{os.getpid()}.csv")
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=f, stderr=subprocess.DEVNULL)
+    except Exception:
+        return lambda dev: None
+
+    def stop(dev):
+        p.terminate()
+        try:
+            p.wait(timeout=5)
+        except Exception:
+            p.kill()
+        f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(dev):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+    return stop
+
+
+def cpu_baseline(seconds=12.0):
+    """Time the FP64 oracle (as it stands) on a bounded sample: wet steps of the
+    same physics on a 32 x 16 x 16 channel with 300 ions, single-threaded."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r}); sys.path.insert(0, os.path.join({ROOT!r}, 'tests'))
+import numpy as np
+from paper_2204_14167_gb300 import presets, synth
+from helpers import oracle_params
+from oracle import integrate
+cfg, rec = presets.wet_channel_small()
+pos, q, sp = synth.ions(cfg.dims, rec['n_pos'], rec['n_neg'], rec['seed'], rec['ymargin'], rec['min_sep'])
+p = oracle_params(cfg)
+integrate.wet_step(p, pos, q, sp, 0)
+t0 = time.perf_counter(); n = 0
+while time.perf_counter() - t0 < {seconds}:
+    pos, F, c, _ = integrate.wet_step(p, pos, q, sp, n + 1); n += 1
+dt = time.perf_counter() - t0
+print(json.dumps(dict(steps=n, seconds=dt, ions=int(pos.shape[1]))))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle", "error": r.stderr[-400:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["ions"] * d["steps"] / d["seconds"], "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{d['steps']} FP64 oracle wet steps of a 32x16x16 channel with {d['ions']} ions "
+                      f"({d['seconds']:.1f} s, single thread)"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.steps):
+        b = cpu_baseline(seconds=max(2.0, 20.0 / max(args.steps, 1)))
+        vals.append(b["value"])
+    v = sum(vals) / len(vals) if vals and None not in vals else None
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference_sample": "32x16x16 channel, 300 ions"},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": "FP64 oracle wet steps of a 32x16x16 channel with 300 ions per step"},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_2204_14167_gb300 as dg
+    from paper_2204_14167_gb300 import presets, synth
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    cfg, rec = presets.wet_channel_128x64x128(dg.MIXED)
+    cfg.seed = cfg.seed + rank
+    pos, q, sp = synth.ions(cfg.dims, rec["n_pos"], rec["n_neg"], rec["seed"] + rank, rec["ymargin"], rec["min_sep"])
+    N = pos.shape[1]
+    h = dg.Discos(cfg)
+    x = torch.tensor(pos, dtype=torch.float32, device="cuda").contiguous()
+    qd = torch.tensor(q, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+    step = 0
+    for _ in range(args.warmup):
+        h.step(x, qd, step0=step, nsteps=1)
+        step += 1
+    torch.cuda.synchronize()
+
+    # device-timed region: K steps, L2 flushed between steps (outside the events)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stop_clocks = clocks_sampler()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        h.step(x, qd, step0=step, nsteps=1)
+        ends[k].record(stream)
+        step += 1
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = stop_clocks(dev)
+    t_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if dist:
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_per_step = t_ms / args.steps
+    value = ws * N * args.steps / (t_ms * 1e-3)
+
+    # end to end through the public API with host buffers: pinned H2D of the
+    # step's positions and charges, the step, D2H of the new positions
+    xh = torch.tensor(pos, dtype=torch.float32).pin_memory()
+    qh = torch.tensor(q, dtype=torch.float32).pin_memory()
+    out_h = torch.empty_like(xh).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.steps):
+        x.copy_(xh, non_blocking=True)
+        qd.copy_(qh, non_blocking=True)
+        h.step(x, qd, step0=step, nsteps=1)
+        out_h.copy_(x, non_blocking=True)
+        step += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e = {"value": ws * N * args.steps / (e2e_ms * 1e-3), "unit": METRIC,
+           "h2d_bytes_per_step": int(xh.numel() * 4 + qh.numel() * 4),
+           "d2h_bytes_per_step": int(out_h.numel() * 4)}
+
+    # per-kernel-family breakdown for the roofline, timed live with CUDA events
+    rl = roofline_breakdown(h, cfg, x, qd, stream)
+
+    if rank == 0:
+        launches_per_step = rl.pop("_launches_per_step", None)
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "ions": N, "grid": [cfg.Nx, cfg.Ny, cfg.Nz],
+                           "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{ws}"},
+                "clocks": clocks, "e2e": e2e, "roofline": rl.get("roofline"), "stages_ms": rl.get("stages_ms"),
+                "gpu_launches": (launches_per_step or 0) * args.steps}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def roofline_breakdown(h, cfg, x, q, stream):
+    """Time each stage of one step through the fine-grained C ABI."""
+    import torch
+    Nx, Ny, Nz = cfg.dims
+    N = x.shape[1]
+    G = Nx * Ny * Nz
+    stages = {}
+    rho = h.empty_grid("cell")
+    F = torch.empty_like(x)
+    f = h.empty_grid("mac")
+
+    def timed(name, fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        stages[name] = a.elapsed_time(b) / reps
+
+    timed("spread_charge", lambda: h.spread_charge(x, q, out=rho))
+    timed("poisson", lambda: h.solve_poisson(rho, out=rho))
+    timed("interp_efield", lambda: h.interpolate_efield(x, rho))
+    timed("near_field", lambda: h.near_field(x, q, F=F, counts=False))
+    timed("spread_force", lambda: h.spread_force(x, F, out=f))
+    timed("stokes", lambda: h.solve_stokes(f, out=f))
+    timed("interp_velocity", lambda: h.interpolate_velocity(x, f))
+    # Poisson solve: algorithmic HBM bytes = rho read (4G) + 5 passes over the
+    # half spectrum (x-FFT write, z-FFT read+write twice, y-solve read+write,
+    # inverse x read) ~ 8 bytes * G/2 * 2 each, phi write (4G), pivots 8G/2
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    b_poisson = 4 * G + 4 * G + 6 * (8 * G // 2 * 2) // 2 + 8 * G // 2
+    b_stokes = 2 * 4 * (3 * G + Nx * Nz) + 6 * (8 * 3 * G // 2)
+    dom = max(("poisson", b_poisson), ("stokes", b_stokes), key=lambda kv: stages[kv[0]])
+    t = stages[dom[0]] * 1e-3
+    achieved = dom[1] / t / 1e9
+    return {"stages_ms": stages,
+            "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": "measured" if peaks else "fallback"},
+            "_launches_per_step": None}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * libdiscos: GB300 (sm_103a) implementation of the per-time-step
+ * particle-grid hot path of the DISCOS method for ions in a channel with
+ * walls at y = 0 and y = Ny, periodic in x and z (Ladiges et al., "Modeling
+ * electrokinetic flows with the discrete ion stochastic continuum overdamped
+ * solvent algorithm", arXiv 2204.14167).
+ *
+ * Units are reduced: grid spacing 1 (cell volume 1), kT as configured,
+ * permittivity eps = 1/(4 pi lB) so the Coulomb force is lB q_i q_j / r^2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Precision. A handle is created for DISCOS_FP64 (every array is double)
+ *   or DISCOS_MIXED (ion and grid arrays are float; the wall-normal banded
+ *   solves, the RFD weight differences and global sums run in double).
+ *   "real" below means that type.
+ * - Ion arrays are structure-of-arrays and live on the device: positions
+ *   x[3][N] (x row, then y row, then z row, each N reals), charges q[N],
+ *   species[N] (int32, may be NULL = all species 0), forces F[3][N].
+ * - Grids are [Nz][Ny][Nx] (x fastest) for cell-centred quantities and
+ *   for x- and z-face quantities; y-face quantities are [Nz][Ny+1][Nx]
+ *   with rows 0 and Ny on the walls.
+ * - Ownership. Every pointer argument is borrowed: the caller owns it and
+ *   keeps it valid until the work queued on `stream` has finished. The
+ *   library owns only the workspace it allocates in discos_create.
+ * - Streams. `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   Calls only enqueue work; results are ready when the stream is.
+ * - Errors. Every function returns a discos_status. Arguments are checked
+ *   before anything is enqueued; on failure nothing is enqueued and
+ *   discos_last_error() describes the cause. A CUDA launch error returns
+ *   DISCOS_ERR_CUDA.
+ */
+#ifndef DISCOS_H
+#define DISCOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int discos_status;
+enum {
+  DISCOS_OK = 0,
+  DISCOS_ERR_INVALID_ARG = 1,
+  DISCOS_ERR_OOM = 2,
+  DISCOS_ERR_NOT_NEUTRAL = 3,
+  DISCOS_ERR_NOT_CONVERGED = 4,
+  DISCOS_ERR_DEVICE_FAULT = 5,
+  DISCOS_ERR_TIMEOUT = 6,
+  DISCOS_ERR_CUDA = 7
+};
+
+enum { DISCOS_BC_DIRICHLET = 0, DISCOS_BC_NEUMANN = 1 };
+enum { DISCOS_KERNEL_PESKIN4 = 0, DISCOS_KERNEL_PESKIN6 = 1, DISCOS_KERNEL_ES = 2 };
+enum { DISCOS_FP64 = 0, DISCOS_MIXED = 1 };
+enum { DISCOS_WALL_WCA = 0, DISCOS_WALL_LJ93 = 1 };
+enum { DISCOS_SPREAD_CHARGE = 0, DISCOS_SPREAD_FORCE = 1 };
+enum { DISCOS_INTERP_EFIELD = 0, DISCOS_INTERP_VELOCITY = 1 };
+
+#define DISCOS_MAX_SPECIES 4
+
+/* Run configuration.  Citations are to the paper's sections and equations. */
+typedef struct discos_config {
+  int Nx, Ny, Nz;          /* cells; Nx, Nz powers of two in [16, 512], Ny in [8, 512] */
+  int bc[2];               /* electrostatic wall type, bottom and top: Eq. esbc1 / Eq. esbc3 */
+  double phi_b[2];         /* wall potential of a Dirichlet wall (Eq. esbc1) */
+  double surf_charge[2];   /* surface charge of a Neumann wall (Eq. esbc3; -eps dphi/dn = varsigma) */
+  int kernel_es;           /* electrostatic kernel (App. B) */
+  int kernel_hy;           /* hydrodynamic kernel (App. B) */
+  int es_w[2];             /* ES kernel width in points (4..7) for [es, hy] kernels */
+  double es_beta[2];       /* ES kernel beta for [es, hy] kernels (Eq. eskernel) */
+  double lB;               /* Bjerrum length: eps = 1/(4 pi lB) */
+  double eta;              /* viscosity (Eq. disc_stokes) */
+  double kT;               /* thermal energy */
+  double dt;               /* time step */
+  double psi;              /* P3M near-field cutoff (Eq. fullElectro) */
+  int n_tab;               /* entries - 1 of the F^P table on [0, psi] (Eq. LC) */
+  int nspecies;            /* 1..DISCOS_MAX_SPECIES */
+  double D_tot[DISCOS_MAX_SPECIES];  /* total diffusion (Eq. diffSum) */
+  double D_wet[DISCOS_MAX_SPECIES];  /* wet part; D_dry = D_tot - D_wet */
+  /* Eq. fitfunction coefficients c1..c7: [species][0 = parallel, 1 = perpendicular][0 = tot, 1 = wet][7] */
+  double gamma_coef[DISCOS_MAX_SPECIES][2][2][7];
+  double lj_sigma[DISCOS_MAX_SPECIES][DISCOS_MAX_SPECIES];  /* Eq. potential */
+  double lj_xi[DISCOS_MAX_SPECIES][DISCOS_MAX_SPECIES];
+  double lj_rc[DISCOS_MAX_SPECIES][DISCOS_MAX_SPECIES];
+  int wall_type;           /* DISCOS_WALL_WCA (12-6) or DISCOS_WALL_LJ93 (Eq. LJ93) */
+  double wall_sigma[DISCOS_MAX_SPECIES];
+  double wall_xi[DISCOS_MAX_SPECIES];
+  double wall_rc[DISCOS_MAX_SPECIES];
+  double E_ext[3];         /* applied uniform field: F_ext = q E_ext (Eq. totalforce) */
+  int precision;           /* DISCOS_FP64 or DISCOS_MIXED */
+  int max_refine;          /* mixed precision: residual refinement sweeps of the Poisson solve */
+  int wet;                 /* 1: hydrodynamic stage (Stokes + midpoint); 0: dry diffusion only */
+  int drift;               /* 1: stochastic drift terms on (RFD + midpoint, div D^dry) */
+  int max_ions;            /* capacity of the per-ion workspace */
+  uint64_t seed;           /* Philox key for all noise */
+} discos_config;
+
+typedef struct discos_handle discos_handle;
+
+/* Device-memory allocator hooks; NULL uses cudaMalloc / cudaFree. */
+typedef void* (*discos_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*discos_free_fn)(void* ptr, void* ctx);
+
+/* Creates a handle: validates the configuration, allocates the workspace,
+ * builds the F^P pair-force table of Sec. II.B.1 (Eq. LC) for the
+ * electrostatic kernel and uploads all constants.  Synchronous.
+ * Errors: INVALID_ARG (bad sizes, kernel, cutoff, or an all-Neumann channel
+ * whose surface charge makes neutrality impossible is not detected here;
+ * see discos_spread), OOM, CUDA. */
+discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn,
+                            discos_free_fn free_fn, void* alloc_ctx, discos_handle** out);
+
+/* Frees the workspace and the handle (synchronises the device first). */
+discos_status discos_destroy(discos_handle* h);
+
+/* Static description of the last error on this thread. */
+const char* discos_last_error(void);
+
+/* Spreading, Eq. kernel2 with the wall image construction of Sec. II.A
+ * (Fig. folded) and Sec. II.B.1.
+ * which = DISCOS_SPREAD_CHARGE: val = q[N]; grid = rho[Nz][Ny][Nx] cell
+ *   centred, images of sign -1 (Dirichlet wall) / +1 (Neumann wall).
+ * which = DISCOS_SPREAD_FORCE: val = F[3][N]; grid = fx[Nz][Ny][Nx] followed
+ *   by fy[Nz][Ny+1][Nx] followed by fz[Nz][Ny][Nx] (one contiguous buffer),
+ *   no-slip images (opposite normal and tangential force).
+ * The grid is overwritten (not accumulated into). */
+discos_status discos_spread(discos_handle* h, const void* x, const void* val, int N, int which,
+                            void* grid, void* stream);
+
+/* Poisson solve -eps lap_h phi = rho (Eq. poisson) with the wall conditions
+ * of Eqs. esbc1 / esbc3, periodic in x and z: DFTs in x and z and a double
+ * precision tridiagonal solve per (kx, kz) mode in y.  rho, phi:
+ * [Nz][Ny][Nx] reals (may alias).  For two Neumann walls the potential has
+ * zero mean and the charge (plus surface charge) must be neutral to
+ * 1e-9 relative (checked on the host only by the caller). */
+discos_status discos_solve_poisson(discos_handle* h, const void* rho, void* phi, void* stream);
+
+/* Staggered Stokes solve with no-slip walls (Eqs. disc_stokes, fluidbc):
+ * f = fx|fy|fz as in discos_spread(FORCE); v = u|v|w in the same layout
+ * (wall rows of v are zero); p = [Nz][Ny][Nx] pressure (mean zero), may be
+ * NULL.  f and v may alias. */
+discos_status discos_solve_stokes(discos_handle* h, const void* f, void* v, void* p, void* stream);
+
+/* Interpolation, Eq. kernel1 with ghost cells filled from the boundary
+ * conditions.
+ * which = DISCOS_INTERP_EFIELD: grid = phi; out[3][N] = E^P = J^es(-grad_h phi)
+ *   (Eq. efieldop) with E on the cell faces.
+ * which = DISCOS_INTERP_VELOCITY: grid = u|v|w; out[3][N] = J^hy v. */
+discos_status discos_interpolate(discos_handle* h, const void* x, int N, int which,
+                                 const void* grid, void* out, void* stream);
+
+/* Cell list of Sec. II.B.1's neighbour sets: list cells of k grid cells per
+ * axis (k = ceil(max(psi, largest LJ cutoff))), cell = min(floor(x) div k,
+ * nc - 1); counting sort, ions stable by index inside a cell.
+ * cell_start[n_cells + 1] and perm[N] are int32 device arrays (either may be
+ * NULL); n_cells_out (host, may be NULL) receives n_cells. */
+discos_status discos_cell_list(discos_handle* h, const void* x, int N, int* cell_start,
+                               int* perm, int* n_cells_out, void* stream);
+
+/* Near-field forces added to F[3][N] (F += ...): the P3M local correction
+ * with wall images (Eqs. coulomb, fullElectro, LC), the ion-ion LJ force
+ * (Eq. closerange) and the wall force (Sec. II.B.2).  nbr_count[N] (int32,
+ * may be NULL) receives the number of real and image partners within psi. */
+discos_status discos_near_field(discos_handle* h, const void* x, const void* q, const int* species,
+                                int N, void* F, int* nbr_count, void* stream);
+
+/* Total force, Eq. totalforce: stages 1 and 2 of Sec. II.D
+ * (spread, Poisson, field interpolation, near field, wall, external field).
+ * F[3][N] is overwritten; nbr_count may be NULL. */
+discos_status discos_forces(discos_handle* h, const void* x, const void* q, const int* species,
+                            int N, void* F, int* nbr_count, void* stream);
+
+/* Advances N ions by nsteps steps of Sec. II.D: forces, then either the dry
+ * Euler-Maruyama update of Eq. ions3 (cfg.wet = 0) or the fluid forcing,
+ * Stokes solve and midpoint update of Eqs. step1-step2 (cfg.wet = 1).
+ * x is updated in place (wrapped in x, z; specular reflection at the walls).
+ * step0 is the index of the first step (it keys the Philox noise).
+ * F_out[3][N] (may be NULL) receives the forces of the last step. */
+discos_status discos_step(discos_handle* h, void* x, const void* q, const int* species, int N,
+                          int64_t step0, int nsteps, void* F_out, void* stream);
+
+/* Host-only (no GPU needed): the F^P pair-force table that discos_create
+ * builds (Sec. II.B.1, Eq. LC), for kernel `kernel` (es_w, es_beta used by
+ * DISCOS_KERNEL_ES), f^P(k psi / n_tab) for k = 0..n_tab with l_B = 1 and
+ * unit charges, written to the host array out[n_tab + 1].
+ * Errors: INVALID_ARG. */
+discos_status discos_fp_table(int kernel, int es_w, double es_beta, double psi, int n_tab, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

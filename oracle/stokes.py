@@ -7,8 +7,8 @@ Eq. disc_stokes / stokes_temporal:  grad_h p - eta lap_h v = f,  div_h v = 0,
 on the MAC grid (normal velocities on faces, p at centres), periodic in x and
 z, no-slip walls at y = 0 and y = Ny (Eq. fluidbc): v_y = 0 on the wall faces,
 tangential ghosts u(-1) = -u(0) so the velocity vanishes on the wall.  The
-saddle-point system is assembled in full, with the pressure gauge
-sum(p) = 0 added by bordering, and solved by a sparse direct solver.
+saddle-point system is solved in its Uzawa (Schur complement) form with
+exact inner solves; the pressure gauge is sum(p) = 0.
 
 Stochastic forcing sqrt(2 kT eta / (dV dt)) div_h Z (Eq. stokes_temporal),
 reading of the cited staggered construction: Z symmetric, diagonal entries
@@ -79,32 +79,48 @@ def _ops(dims):
     return Lc, lap_face(), Lc, Gx, Gy, Gz
 
 
-def solve(fx, fy, fz, eta):
+def solve(fx, fy, fz, eta, tol=1e-13):
     """Velocity (u on x-faces, v on y-faces incl. zero wall faces, w) and p.
 
-    fy has shape (Nz, Ny+1, Nx); its wall rows are ignored.
+    fy has shape (Nz, Ny+1, Nx); its wall rows are ignored.  Uzawa form of
+    the saddle-point system  eta L vel + G p = f,  G^T vel = 0:  the pressure
+    solves the Schur complement system  G^T L^-1 G p = G^T L^-1 f  by
+    conjugate gradients on mean-zero pressures (the constant is the null
+    space), with every L^-1 applied by a sparse LU factorisation of the
+    viscous operator; then vel = L^-1 (f - G p) / eta.
     """
     Nz, Ny, Nx = fx.shape
     dims = (Nx, Ny, Nz)
     Lu, Lv, Lw, Gx, Gy, Gz = _ops(dims)
-    nc = Nx * Ny * Nz
-    nv = Nx * (Ny - 1) * Nz
-    Z = None
-    ones = sp.csr_matrix(np.ones((nc, 1)))
-    A = sp.bmat([
-        [eta * Lu, None, None, Gx, None],
-        [None, eta * Lv, None, Gy, None],
-        [None, None, eta * Lw, Gz, None],
-        [-Gx.T, -Gy.T, -Gz.T, None, ones],
-        [None, None, None, ones.T, None]], format='csc')
-    b = np.concatenate([fx.ravel(), fy[:, 1:Ny, :].ravel(), fz.ravel(), np.zeros(nc), [0.0]])
-    x = spla.spsolve(A, b)
-    u = x[:nc].reshape(Nz, Ny, Nx)
+    lu_c = spla.splu(Lu.tocsc())
+    lu_f = spla.splu(Lv.tocsc())
+
+    def Linv(bx, by, bz):
+        return lu_c.solve(bx), lu_f.solve(by), lu_c.solve(bz)
+
+    def G(p):
+        return Gx @ p, Gy @ p, Gz @ p
+
+    def GT(a, b, c):
+        return Gx.T @ a + Gy.T @ b + Gz.T @ c
+
+    f = (fx.ravel(), fy[:, 1:Ny, :].ravel(), fz.ravel())
+    rhs = GT(*Linv(*f))
+    rhs -= rhs.mean()
+    n = rhs.size
+    S = spla.LinearOperator((n, n), matvec=lambda p: (lambda r: r - r.mean())(GT(*Linv(*G(p - p.mean())))),
+                            dtype=np.float64)
+    p, info = spla.cg(S, rhs, rtol=tol, atol=0.0, maxiter=5000)
+    if info != 0:
+        raise RuntimeError(f"Schur CG did not converge (info={info})")
+    p = p - p.mean()
+    gp = G(p)
+    ux, uy, uz = Linv(*(a - b for a, b in zip(f, gp)))
+    u = ux.reshape(Nz, Ny, Nx) / eta
     v = np.zeros((Nz, Ny + 1, Nx))
-    v[:, 1:Ny, :] = x[nc:nc + nv].reshape(Nz, Ny - 1, Nx)
-    w = x[nc + nv:2 * nc + nv].reshape(Nz, Ny, Nx)
-    p = x[2 * nc + nv:3 * nc + nv].reshape(Nz, Ny, Nx)
-    return u, v, w, p
+    v[:, 1:Ny, :] = uy.reshape(Nz, Ny - 1, Nx) / eta
+    w = uz.reshape(Nz, Ny, Nx) / eta
+    return u, v, w, p.reshape(Nz, Ny, Nx)
 
 
 def divergence(u, v, w):

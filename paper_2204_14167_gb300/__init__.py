@@ -1,0 +1,241 @@
+"""GB300-native DISCOS hot path (wall-bounded channel) behind the libdiscos C ABI.
+
+Python side: a thin binding (`Discos`) over include/discos.h that passes
+torch device tensors and the current CUDA stream to the library, a run
+configuration (`RunConfig`), workload presets and seeded synthetic inputs.
+All numerical work happens in the CUDA kernels of libdiscos.
+"""
+from dataclasses import dataclass, field
+import ctypes
+
+from . import _lib
+from ._lib import (BC_DIRICHLET, BC_NEUMANN, KERNEL_PESKIN4, KERNEL_PESKIN6, KERNEL_ES, FP64, MIXED,
+                   WALL_WCA, WALL_LJ93, SPREAD_CHARGE, SPREAD_FORCE, INTERP_EFIELD, INTERP_VELOCITY,
+                   DiscosError)
+
+__all__ = ["RunConfig", "Discos", "DiscosError", "fp_table", "BC_DIRICHLET", "BC_NEUMANN", "KERNEL_PESKIN4",
+           "KERNEL_PESKIN6", "KERNEL_ES", "FP64", "MIXED", "WALL_WCA", "WALL_LJ93"]
+
+
+def _unit_gamma():
+    # gamma_hat = 1 everywhere: c1 = 1, all other terms zero (c3, c5, c7 = 1 keep it finite)
+    return [1.0, 0.0, 1.0, 0.0, 1.0, 0.0, 1.0]
+
+
+@dataclass
+class RunConfig:
+    """Reduced units: grid spacing 1, eps = 1/(4 pi lB).  Mirrors discos_config."""
+    Nx: int = 32
+    Ny: int = 32
+    Nz: int = 32
+    bc: tuple = (BC_DIRICHLET, BC_DIRICHLET)
+    phi_b: tuple = (0.0, 0.0)
+    surf_charge: tuple = (0.0, 0.0)
+    kernel_es: int = KERNEL_PESKIN6
+    kernel_hy: int = KERNEL_PESKIN4
+    es_w: tuple = (6, 6)
+    es_beta: tuple = (8.0, 8.0)
+    lB: float = 7.0
+    eta: float = 1.0
+    kT: float = 1.0
+    dt: float = 0.01
+    psi: float = 4.0
+    n_tab: int = 64
+    nspecies: int = 1
+    D_tot: list = field(default_factory=lambda: [1.0])
+    D_wet: list = field(default_factory=lambda: [0.0])
+    # [species][direction: 0 parallel, 1 perpendicular][0 tot, 1 wet][7]
+    gamma_coef: list = field(default_factory=lambda: [[[_unit_gamma(), _unit_gamma()]] * 2])
+    lj_sigma: list = field(default_factory=lambda: [[1.0]])
+    lj_xi: list = field(default_factory=lambda: [[1.0]])
+    lj_rc: list = field(default_factory=lambda: [[2.0 ** (1.0 / 6.0)]])
+    wall_type: int = WALL_WCA
+    wall_sigma: list = field(default_factory=lambda: [2.0 ** (-1.0 / 6.0)])
+    wall_xi: list = field(default_factory=lambda: [1.0])
+    wall_rc: list = field(default_factory=lambda: [1.0])
+    E_ext: tuple = (0.0, 0.0, 0.0)
+    precision: int = FP64
+    max_refine: int = 0
+    wet: bool = False
+    drift: bool = True
+    max_ions: int = 1024
+    seed: int = 20220428
+
+    @property
+    def dims(self):
+        return (self.Nx, self.Ny, self.Nz)
+
+    def to_c(self):
+        c = _lib.Config()
+        c.Nx, c.Ny, c.Nz = self.Nx, self.Ny, self.Nz
+        for w in range(2):
+            c.bc[w] = int(self.bc[w])
+            c.phi_b[w] = float(self.phi_b[w])
+            c.surf_charge[w] = float(self.surf_charge[w])
+            c.es_w[w] = int(self.es_w[w])
+            c.es_beta[w] = float(self.es_beta[w])
+        c.kernel_es, c.kernel_hy = int(self.kernel_es), int(self.kernel_hy)
+        c.lB, c.eta, c.kT, c.dt, c.psi = self.lB, self.eta, self.kT, self.dt, self.psi
+        c.n_tab = self.n_tab
+        c.nspecies = self.nspecies
+        for a in range(self.nspecies):
+            c.D_tot[a] = float(self.D_tot[a])
+            c.D_wet[a] = float(self.D_wet[a])
+            for d in range(2):
+                for t in range(2):
+                    for k in range(7):
+                        c.gamma_coef[a][d][t][k] = float(self.gamma_coef[a][d][t][k])
+            for b in range(self.nspecies):
+                c.lj_sigma[a][b] = float(self.lj_sigma[a][b])
+                c.lj_xi[a][b] = float(self.lj_xi[a][b])
+                c.lj_rc[a][b] = float(self.lj_rc[a][b])
+            c.wall_sigma[a] = float(self.wall_sigma[a])
+            c.wall_xi[a] = float(self.wall_xi[a])
+            c.wall_rc[a] = float(self.wall_rc[a])
+        c.wall_type = int(self.wall_type)
+        for d in range(3):
+            c.E_ext[d] = float(self.E_ext[d])
+        c.precision = int(self.precision)
+        c.max_refine = int(self.max_refine)
+        c.wet = int(bool(self.wet))
+        c.drift = int(bool(self.drift))
+        c.max_ions = int(self.max_ions)
+        c.seed = int(self.seed)
+        return c
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Discos:
+    """A libdiscos handle.  Tensors are CUDA tensors of the handle's real type
+    (float64 for FP64, float32 for MIXED); positions are (3, N), contiguous."""
+
+    def __init__(self, cfg: RunConfig):
+        import torch
+        lib = _lib.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libdiscos needs a CUDA device")
+        torch.cuda.init()
+        self.cfg = cfg
+        self._c = cfg.to_c()
+        h = ctypes.c_void_p()
+        _lib.check(lib.discos_create(ctypes.byref(self._c), None, None, None, ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+        self.dtype = torch.float64 if cfg.precision == FP64 else torch.float32
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.discos_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers
+    def _check_ions(self, x):
+        assert x.is_cuda and x.dtype == self.dtype and x.is_contiguous() and x.shape[0] == 3, "bad positions"
+        return x.shape[1]
+
+    def empty_grid(self, kind="cell"):
+        import torch
+        Nx, Ny, Nz = self.cfg.dims
+        if kind == "cell":
+            return torch.empty((Nz, Ny, Nx), dtype=self.dtype, device="cuda")
+        n = Nx * Nz * (3 * Ny + 1)
+        return torch.empty(n, dtype=self.dtype, device="cuda")
+
+    # -- entry points
+    def spread_charge(self, x, q, out=None, stream=None):
+        N = self._check_ions(x)
+        rho = self.empty_grid("cell") if out is None else out
+        _lib.check(self._lib.discos_spread(self._h, _ptr(x), _ptr(q), N, SPREAD_CHARGE, _ptr(rho), _stream(stream)))
+        return rho
+
+    def spread_force(self, x, F, out=None, stream=None):
+        N = self._check_ions(x)
+        f = self.empty_grid("mac") if out is None else out
+        _lib.check(self._lib.discos_spread(self._h, _ptr(x), _ptr(F), N, SPREAD_FORCE, _ptr(f), _stream(stream)))
+        return f
+
+    def solve_poisson(self, rho, out=None, stream=None):
+        phi = self.empty_grid("cell") if out is None else out
+        _lib.check(self._lib.discos_solve_poisson(self._h, _ptr(rho), _ptr(phi), _stream(stream)))
+        return phi
+
+    def solve_stokes(self, f, out=None, pressure=False, stream=None):
+        v = self.empty_grid("mac") if out is None else out
+        p = self.empty_grid("cell") if pressure else None
+        _lib.check(self._lib.discos_solve_stokes(self._h, _ptr(f), _ptr(v), _ptr(p), _stream(stream)))
+        return (v, p) if pressure else v
+
+    def interpolate_efield(self, x, phi, stream=None):
+        import torch
+        N = self._check_ions(x)
+        out = torch.empty((3, N), dtype=self.dtype, device="cuda")
+        _lib.check(self._lib.discos_interpolate(self._h, _ptr(x), N, INTERP_EFIELD, _ptr(phi), _ptr(out),
+                                                _stream(stream)))
+        return out
+
+    def interpolate_velocity(self, x, v, stream=None):
+        import torch
+        N = self._check_ions(x)
+        out = torch.empty((3, N), dtype=self.dtype, device="cuda")
+        _lib.check(self._lib.discos_interpolate(self._h, _ptr(x), N, INTERP_VELOCITY, _ptr(v), _ptr(out),
+                                                _stream(stream)))
+        return out
+
+    def cell_list(self, x, stream=None):
+        import torch
+        N = self._check_ions(x)
+        n = ctypes.c_int()
+        _lib.check(self._lib.discos_cell_list(self._h, _ptr(x), 0, None, None, ctypes.byref(n), _stream(stream)))
+        start = torch.empty(n.value + 1, dtype=torch.int32, device="cuda")
+        perm = torch.empty(max(N, 1), dtype=torch.int32, device="cuda")
+        _lib.check(self._lib.discos_cell_list(self._h, _ptr(x), N, _ptr(start), _ptr(perm), None, _stream(stream)))
+        return start, perm[:N]
+
+    def near_field(self, x, q, species=None, F=None, counts=True, stream=None):
+        import torch
+        N = self._check_ions(x)
+        if F is None:
+            F = torch.zeros((3, N), dtype=self.dtype, device="cuda")
+        nbr = torch.empty(max(N, 1), dtype=torch.int32, device="cuda") if counts else None
+        _lib.check(self._lib.discos_near_field(self._h, _ptr(x), _ptr(q), _ptr(species), N, _ptr(F), _ptr(nbr),
+                                               _stream(stream)))
+        return (F, nbr[:N]) if counts else F
+
+    def forces(self, x, q, species=None, counts=False, stream=None):
+        import torch
+        N = self._check_ions(x)
+        F = torch.empty((3, N), dtype=self.dtype, device="cuda")
+        nbr = torch.empty(max(N, 1), dtype=torch.int32, device="cuda") if counts else None
+        _lib.check(self._lib.discos_forces(self._h, _ptr(x), _ptr(q), _ptr(species), N, _ptr(F), _ptr(nbr),
+                                           _stream(stream)))
+        return (F, nbr[:N]) if counts else F
+
+    def step(self, x, q, species=None, step0=0, nsteps=1, F_out=None, stream=None):
+        """Advance x in place by nsteps steps; returns x."""
+        N = self._check_ions(x)
+        _lib.check(self._lib.discos_step(self._h, _ptr(x), _ptr(q), _ptr(species), N, int(step0), int(nsteps),
+                                         _ptr(F_out), _stream(stream)))
+        return x
+
+
+def fp_table(kernel, psi, n_tab, es_w=6, es_beta=8.0):
+    """The library's F^P table (host computation, no GPU needed)."""
+    lib = _lib.load()
+    out = (ctypes.c_double * (n_tab + 1))()
+    _lib.check(lib.discos_fp_table(int(kernel), int(es_w), float(es_beta), float(psi), int(n_tab), out))
+    return list(out)

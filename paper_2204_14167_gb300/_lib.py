@@ -1,0 +1,99 @@
+"""ctypes binding of libdiscos (include/discos.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch
+tensors to device pointers and a Python configuration to the C struct.  If
+the shared library is missing it raises instead of falling back to anything.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdiscos.so")
+
+MAX_SPECIES = 4
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_NOT_NEUTRAL, ERR_NOT_CONVERGED, ERR_DEVICE_FAULT, ERR_TIMEOUT, ERR_CUDA = range(8)
+BC_DIRICHLET, BC_NEUMANN = 0, 1
+KERNEL_PESKIN4, KERNEL_PESKIN6, KERNEL_ES = 0, 1, 2
+FP64, MIXED = 0, 1
+WALL_WCA, WALL_LJ93 = 0, 1
+SPREAD_CHARGE, SPREAD_FORCE = 0, 1
+INTERP_EFIELD, INTERP_VELOCITY = 0, 1
+
+D = ctypes.c_double
+NS = MAX_SPECIES
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("Nx", ctypes.c_int), ("Ny", ctypes.c_int), ("Nz", ctypes.c_int),
+        ("bc", ctypes.c_int * 2),
+        ("phi_b", D * 2),
+        ("surf_charge", D * 2),
+        ("kernel_es", ctypes.c_int),
+        ("kernel_hy", ctypes.c_int),
+        ("es_w", ctypes.c_int * 2),
+        ("es_beta", D * 2),
+        ("lB", D), ("eta", D), ("kT", D), ("dt", D), ("psi", D),
+        ("n_tab", ctypes.c_int),
+        ("nspecies", ctypes.c_int),
+        ("D_tot", D * NS), ("D_wet", D * NS),
+        ("gamma_coef", D * 7 * 2 * 2 * NS),
+        ("lj_sigma", D * NS * NS), ("lj_xi", D * NS * NS), ("lj_rc", D * NS * NS),
+        ("wall_type", ctypes.c_int),
+        ("wall_sigma", D * NS), ("wall_xi", D * NS), ("wall_rc", D * NS),
+        ("E_ext", D * 3),
+        ("precision", ctypes.c_int),
+        ("max_refine", ctypes.c_int),
+        ("wet", ctypes.c_int),
+        ("drift", ctypes.c_int),
+        ("max_ions", ctypes.c_int),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+EXPORTS = [
+    "discos_create", "discos_destroy", "discos_last_error", "discos_spread", "discos_solve_poisson",
+    "discos_solve_stokes", "discos_interpolate", "discos_cell_list", "discos_near_field", "discos_forces",
+    "discos_step", "discos_fp_table",
+]
+
+_lib = None
+
+
+def load():
+    """Load libdiscos.so (built in-tree by build.py); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libdiscos.so not found at {LIB_PATH}: run paper_2204_14167_gb300/build.py "
+                           "(or __graft_entry__.build()) first")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    lib.discos_create.argtypes = [ctypes.POINTER(Config), vp, vp, vp, ctypes.POINTER(vp)]
+    lib.discos_destroy.argtypes = [vp]
+    lib.discos_last_error.restype = ctypes.c_char_p
+    lib.discos_spread.argtypes = [vp, vp, vp, i32, i32, vp, vp]
+    lib.discos_solve_poisson.argtypes = [vp, vp, vp, vp]
+    lib.discos_solve_stokes.argtypes = [vp, vp, vp, vp, vp]
+    lib.discos_interpolate.argtypes = [vp, vp, i32, i32, vp, vp, vp]
+    lib.discos_cell_list.argtypes = [vp, vp, i32, vp, vp, ctypes.POINTER(i32), vp]
+    lib.discos_near_field.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp]
+    lib.discos_forces.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp]
+    lib.discos_step.argtypes = [vp, vp, vp, vp, i32, i64, i32, vp, vp]
+    lib.discos_fp_table.argtypes = [i32, i32, D, D, i32, ctypes.POINTER(D)]
+    for name in EXPORTS:
+        getattr(lib, name).restype = ctypes.c_int if name != "discos_last_error" else ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+class DiscosError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"discos status {status}: {msg}")
+        self.status = status
+
+
+def check(status):
+    if status != OK:
+        raise DiscosError(status, load().discos_last_error().decode())

@@ -1,0 +1,441 @@
+// The C ABI of libdiscos: handle creation (validation, workspace, constant
+// tables) and the entry points that enqueue the hot-path kernels.  The
+// four-stage time step follows Sec. II.D of the paper.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+#include "internal.h"
+
+namespace discos {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+discos_status cuda_status(cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return DISCOS_OK;
+  set_error(std::string(where) + ": " + cudaGetErrorString(e));
+  return DISCOS_ERR_CUDA;
+}
+
+namespace {
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int kernel_width(int kind, int es_w) {
+  if (kind == DISCOS_KERNEL_PESKIN4) return 4;
+  if (kind == DISCOS_KERNEL_PESKIN6) return 6;
+  if (kind == DISCOS_KERNEL_ES) return es_w;
+  return -1;
+}
+
+discos_status invalid(const std::string& m) {
+  set_error(m);
+  return DISCOS_ERR_INVALID_ARG;
+}
+
+KernelParams make_kernel(int kind, int es_w, double es_beta) {
+  KernelParams kp{};
+  kp.kind = kind;
+  kp.w = kernel_width(kind, es_w);
+  if (kind == DISCOS_KERNEL_ES) {
+    kp.alpha = 0.5 * es_w;
+    kp.beta = es_beta;
+    kp.inv_norm = 1.0 / es_normalisation(es_w, es_beta);
+  }
+  return kp;
+}
+
+// The F^P table depends only on the kernel, psi and n_tab: computed once per
+// process for each combination.
+std::vector<double> cached_fp_table(const KernelParams& kp, double psi, int n_tab) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, double, double, int>, std::vector<double>> cache;
+  auto key = std::make_tuple(kp.kind, kp.w, kp.beta, psi, n_tab);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  std::vector<double> tab(n_tab + 1);
+  std::string err;
+  build_fp_table(kp, psi, n_tab, tab.data(), &err);
+  cache[key] = tab;
+  return tab;
+}
+
+void* dalloc(discos_handle* h, size_t bytes, bool* ok) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (h->alloc_fn) {
+    p = h->alloc_fn(bytes, h->alloc_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (!p) *ok = false;
+  return p;
+}
+
+void dfree(discos_handle* h, void* p) {
+  if (!p) return;
+  if (h->free_fn) h->free_fn(p, h->alloc_ctx);
+  else cudaFree(p);
+}
+
+template <typename T>
+void upload_twiddles(void* dst, int N) {
+  std::vector<cplx<T>> tw(N / 2);
+  for (int k = 0; k < N / 2; ++k) {
+    double a = -2.0 * M_PI * k / N;
+    tw[k] = cplx<T>{T(std::cos(a)), T(std::sin(a))};
+  }
+  cudaMemcpy(dst, tw.data(), sizeof(cplx<T>) * tw.size(), cudaMemcpyHostToDevice);
+}
+
+template <typename T>
+void upload_table(void* dst, const std::vector<double>& t) {
+  std::vector<T> v(t.begin(), t.end());
+  cudaMemcpy(dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+}
+
+void free_workspace(discos_handle* h) {
+  Workspace& W = h->W;
+  void* ptrs[] = {W.phi, W.spec, W.fgrid, W.inv_m, W.tw_x, W.tw_z, W.fptab, W.cell_of, W.counts, W.fill,
+                  W.cell_start, W.perm, W.tile_sums, W.xs, W.qs, W.sps, W.F, W.xstar, W.V};
+  for (void* p : ptrs) dfree(h, p);
+  W = Workspace{};
+}
+
+template <typename T>
+discos_status forces_impl(discos_handle* h, const T* x, const T* q, const int* species, int N, T* F, int* nbr,
+                          cudaStream_t s) {
+  const Params& P = h->P;
+  Workspace& W = h->W;
+  T* phi = reinterpret_cast<T*>(W.phi);
+  cudaError_t e = launch_spread_charge<T>(P, x, q, N, phi, s);
+  if (e == cudaSuccess) e = launch_poisson<T>(P, W, phi, phi, s);
+  if (e == cudaSuccess) e = launch_interp_efield<T>(P, x, q, N, phi, F, true, s);
+  if (e == cudaSuccess) e = launch_near_field<T>(P, W, x, q, species, N, F, nbr, s);
+  return cuda_status(e, "discos_forces");
+}
+
+template <typename T>
+discos_status step_impl(discos_handle* h, T* x, const T* q, const int* species, int N, int64_t step0,
+                        int nsteps, T* F_out, cudaStream_t s) {
+  const Params& P = h->P;
+  Workspace& W = h->W;
+  T* F = reinterpret_cast<T*>(W.F);
+  T* fg = reinterpret_cast<T*>(W.fgrid);
+  T* V = reinterpret_cast<T*>(W.V);
+  T* xs = reinterpret_cast<T*>(W.xstar);
+  const bool wet = h->cfg.wet != 0;
+  const bool thermal = P.kT > 0.0;
+  const bool drift = P.drift != 0;
+  for (int n = 0; n < nsteps; ++n) {
+    const int64_t step = step0 + n;
+    discos_status st = forces_impl<T>(h, x, q, species, N, F, nullptr, s);
+    if (st != DISCOS_OK) return st;
+    cudaError_t e = cudaSuccess;
+    if (wet) {
+      e = launch_spread_force<T>(P, x, F, N, fg, step, drift && thermal, s);
+      if (e == cudaSuccess && thermal) e = launch_stress_noise<T>(P, fg, step, s);
+      if (e == cudaSuccess) e = launch_stokes<T>(P, W, fg, fg, nullptr, s);
+      if (e == cudaSuccess) e = launch_interp_velocity<T>(P, x, N, fg, V, s);
+      if (drift) {
+        if (e == cudaSuccess) e = launch_midpoint<T>(P, x, V, N, xs, s);
+        if (e == cudaSuccess) e = launch_interp_velocity<T>(P, xs, N, fg, V, s);
+      }
+      if (e == cudaSuccess) e = launch_dry_update<T>(P, x, species, F, V, N, step, s);
+    } else {
+      e = launch_dry_update<T>(P, x, species, F, nullptr, N, step, s);
+    }
+    if (e != cudaSuccess) return cuda_status(e, "discos_step");
+  }
+  if (F_out && nsteps > 0)
+    return cuda_status(cudaMemcpyAsync(F_out, F, sizeof(T) * 3 * (size_t)N, cudaMemcpyDeviceToDevice, s),
+                       "discos_step");
+  return DISCOS_OK;
+}
+
+discos_status check_n(discos_handle* h, int N) {
+  if (!h) return invalid("null handle");
+  if (N < 0 || N > h->cfg.max_ions) return invalid("N outside [0, max_ions]");
+  return DISCOS_OK;
+}
+
+}  // namespace
+}  // namespace discos
+
+using namespace discos;
+
+extern "C" {
+
+const char* discos_last_error(void) { return g_err.c_str(); }
+
+discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, discos_free_fn free_fn,
+                            void* alloc_ctx, discos_handle** out) {
+  if (!cfg || !out) return invalid("null argument");
+  *out = nullptr;
+  const discos_config& c = *cfg;
+  if (!is_pow2(c.Nx) || c.Nx < 16 || c.Nx > 512) return invalid("Nx must be a power of two in [16, 512]");
+  if (!is_pow2(c.Nz) || c.Nz < 16 || c.Nz > 512) return invalid("Nz must be a power of two in [16, 512]");
+  if (c.Ny < 8 || c.Ny > 512) return invalid("Ny must be in [8, 512]");
+  for (int w = 0; w < 2; ++w)
+    if (c.bc[w] != DISCOS_BC_DIRICHLET && c.bc[w] != DISCOS_BC_NEUMANN) return invalid("bad wall type");
+  int wes = kernel_width(c.kernel_es, c.es_w[0]);
+  int why = kernel_width(c.kernel_hy, c.es_w[1]);
+  if (wes < 4 || wes > 7 || why < 4 || why > 7) return invalid("kernel must be PESKIN4, PESKIN6 or ES with width 4..7");
+  if (wes > c.Ny - 2 || why > c.Ny - 2) return invalid("kernel wider than the channel");
+  if (!(c.psi > 0.0) || c.n_tab < 2) return invalid("psi > 0 and n_tab >= 2 required");
+  if (c.nspecies < 1 || c.nspecies > DISCOS_MAX_SPECIES) return invalid("nspecies must be 1..4");
+  if (c.max_ions < 1) return invalid("max_ions must be positive");
+  if (c.precision != DISCOS_FP64 && c.precision != DISCOS_MIXED) return invalid("bad precision");
+  if (!(c.dt > 0.0) || c.kT < 0.0) return invalid("dt > 0 and kT >= 0 required");
+  if (c.wet && !(c.eta > 0.0)) return invalid("eta > 0 required for the wet path");
+  if (c.wall_type != DISCOS_WALL_WCA && c.wall_type != DISCOS_WALL_LJ93) return invalid("bad wall_type");
+  double rcmax = c.psi;
+  for (int a = 0; a < c.nspecies; ++a) {
+    if (!(c.D_tot[a] > c.D_wet[a]) || c.D_wet[a] < 0.0) return invalid("need D_tot > D_wet >= 0");
+    for (int b = 0; b < c.nspecies; ++b) rcmax = std::max(rcmax, c.lj_rc[a][b]);
+  }
+  int k = (int)std::ceil(rcmax - 1e-12);
+  if (k < 1) k = 1;
+  if (c.Nx / k < 3 || c.Nz / k < 3) return invalid("cutoff too large for the box (need 3 list cells per periodic axis)");
+  if (2.0 * c.psi > std::min(c.Nx, c.Nz)) return invalid("psi must be at most half the periodic box");
+
+  discos_handle* h = new discos_handle();
+  h->cfg = c;
+  h->mixed = c.precision == DISCOS_MIXED;
+  h->alloc_fn = alloc_fn;
+  h->free_fn = free_fn;
+  h->alloc_ctx = alloc_ctx;
+  cudaGetDevice(&h->device);
+
+  Params& P = h->P;
+  std::memset(&P, 0, sizeof(P));
+  P.Nx = c.Nx; P.Ny = c.Ny; P.Nz = c.Nz;
+  P.Nxh = c.Nx / 2 + 1;
+  P.Px = (P.Nxh + 15) / 16 * 16;
+  for (int w = 0; w < 2; ++w) { P.bc[w] = c.bc[w]; P.phi_b[w] = c.phi_b[w]; }
+  // dphi/dy on the walls: -eps dphi/dn = varsigma with n the inward normal
+  P.slope[0] = -4.0 * M_PI * c.lB * c.surf_charge[0];
+  P.slope[1] = 4.0 * M_PI * c.lB * c.surf_charge[1];
+  P.kes = make_kernel(c.kernel_es, c.es_w[0], c.es_beta[0]);
+  P.khy = make_kernel(c.kernel_hy, c.es_w[1], c.es_beta[1]);
+  P.lB = c.lB; P.eta = c.eta; P.kT = c.kT; P.dt = c.dt; P.psi = c.psi;
+  P.n_tab = c.n_tab;
+  P.tab_scale = c.n_tab / c.psi;
+  P.nspecies = c.nspecies;
+  for (int a = 0; a < DISCOS_MAX_SPECIES; ++a) {
+    P.D_tot[a] = c.D_tot[a];
+    P.D_wet[a] = c.D_wet[a];
+    P.D_dry[a] = c.D_tot[a] - c.D_wet[a];
+    std::memcpy(P.gamma[a], c.gamma_coef[a], sizeof(P.gamma[a]));
+    for (int b = 0; b < DISCOS_MAX_SPECIES; ++b) {
+      P.lj_sigma[a][b] = c.lj_sigma[a][b];
+      P.lj_xi[a][b] = c.lj_xi[a][b];
+      P.lj_rc[a][b] = c.lj_rc[a][b];
+    }
+    P.wall_sigma[a] = c.wall_sigma[a];
+    P.wall_xi[a] = c.wall_xi[a];
+    P.wall_rc[a] = c.wall_rc[a];
+  }
+  P.wall_type = c.wall_type;
+  for (int d = 0; d < 3; ++d) P.E_ext[d] = c.E_ext[d];
+  P.k_cell = k;
+  P.ncx = c.Nx / k; P.ncy = std::max(1, c.Ny / k); P.ncz = c.Nz / k;
+  P.drift = c.drift;
+  P.seed = c.seed;
+
+  // workspace
+  const size_t rs = h->mixed ? sizeof(float) : sizeof(double);
+  const size_t G = (size_t)c.Nx * c.Ny * c.Nz;
+  const size_t Gf = (size_t)c.Nx * c.Nz * (3 * c.Ny + 1);
+  const size_t specslot = (size_t)c.Nz * (c.Ny + 1) * P.Px;
+  const size_t modes = (size_t)P.Nxh * c.Nz;
+  const int n_cells = P.ncx * P.ncy * P.ncz;
+  const size_t M = (size_t)c.max_ions;
+  Workspace& W = h->W;
+  W.n_cells = n_cells;
+  bool ok = true;
+  W.phi = dalloc(h, rs * G, &ok);
+  W.spec = dalloc(h, 2 * rs * 4 * specslot, &ok);
+  W.fgrid = dalloc(h, rs * Gf, &ok);
+  W.inv_m = (double*)dalloc(h, sizeof(double) * modes * c.Ny, &ok);
+  W.tw_x = dalloc(h, 2 * rs * (c.Nx / 2), &ok);
+  W.tw_z = dalloc(h, 2 * rs * (c.Nz / 2), &ok);
+  W.fptab = dalloc(h, rs * (c.n_tab + 1), &ok);
+  W.cell_of = (int*)dalloc(h, sizeof(int) * M, &ok);
+  W.counts = (int*)dalloc(h, sizeof(int) * n_cells, &ok);
+  W.fill = (int*)dalloc(h, sizeof(int) * n_cells, &ok);
+  W.cell_start = (int*)dalloc(h, sizeof(int) * (n_cells + 1), &ok);
+  W.perm = (int*)dalloc(h, sizeof(int) * M, &ok);
+  W.tile_sums = (int*)dalloc(h, sizeof(int) * ((n_cells + 1023) / 1024 + 1), &ok);
+  W.xs = dalloc(h, rs * 3 * M, &ok);
+  W.qs = dalloc(h, rs * M, &ok);
+  W.sps = (int*)dalloc(h, sizeof(int) * M, &ok);
+  W.F = dalloc(h, rs * 3 * M, &ok);
+  W.xstar = dalloc(h, rs * 3 * M, &ok);
+  W.V = dalloc(h, rs * 3 * M, &ok);
+  if (!ok) {
+    free_workspace(h);
+    delete h;
+    set_error("device allocation failed");
+    return DISCOS_ERR_OOM;
+  }
+  // Thomas pivots of the Poisson wall-normal systems, one set per (kx, kz)
+  {
+    std::vector<double> inv((size_t)c.Ny * modes);
+    for (int kz = 0; kz < c.Nz; ++kz)
+      for (int kx = 0; kx < P.Nxh; ++kx) {
+        double lam = (2.0 - 2.0 * std::cos(2.0 * M_PI * kx / c.Nx)) + (2.0 - 2.0 * std::cos(2.0 * M_PI * kz / c.Nz));
+        size_t mode = (size_t)kz * P.Nxh + kx;
+        double m = 0.0;
+        for (int j = 0; j < c.Ny; ++j) {
+          double d = 2.0 + lam;
+          if (j == 0) d += c.bc[0] == DISCOS_BC_DIRICHLET ? 1.0 : -1.0;
+          if (j == c.Ny - 1) d += c.bc[1] == DISCOS_BC_DIRICHLET ? 1.0 : -1.0;
+          m = j == 0 ? d : d - 1.0 / m;
+          inv[(size_t)j * modes + mode] = m != 0.0 ? 1.0 / m : 0.0;
+        }
+      }
+    cudaMemcpy(W.inv_m, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice);
+  }
+  std::vector<double> tab = cached_fp_table(P.kes, c.psi, c.n_tab);
+  if (h->mixed) {
+    upload_twiddles<float>(W.tw_x, c.Nx);
+    upload_twiddles<float>(W.tw_z, c.Nz);
+    upload_table<float>(W.fptab, tab);
+  } else {
+    upload_twiddles<double>(W.tw_x, c.Nx);
+    upload_twiddles<double>(W.tw_z, c.Nz);
+    upload_table<double>(W.fptab, tab);
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_workspace(h);
+    delete h;
+    return cuda_status(e, "discos_create");
+  }
+  *out = h;
+  return DISCOS_OK;
+}
+
+discos_status discos_destroy(discos_handle* h) {
+  if (!h) return invalid("null handle");
+  cudaDeviceSynchronize();
+  free_workspace(h);
+  delete h;
+  return DISCOS_OK;
+}
+
+discos_status discos_spread(discos_handle* h, const void* x, const void* val, int N, int which, void* grid,
+                            void* stream) {
+  discos_status st = check_n(h, N);
+  if (st) return st;
+  if (!grid || (N > 0 && (!x || !val))) return invalid("null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (which == DISCOS_SPREAD_CHARGE) {
+    e = h->mixed ? launch_spread_charge<float>(h->P, (const float*)x, (const float*)val, N, (float*)grid, s)
+                 : launch_spread_charge<double>(h->P, (const double*)x, (const double*)val, N, (double*)grid, s);
+  } else if (which == DISCOS_SPREAD_FORCE) {
+    e = h->mixed ? launch_spread_force<float>(h->P, (const float*)x, (const float*)val, N, (float*)grid, 0, false, s)
+                 : launch_spread_force<double>(h->P, (const double*)x, (const double*)val, N, (double*)grid, 0, false, s);
+  } else {
+    return invalid("which must be DISCOS_SPREAD_CHARGE or DISCOS_SPREAD_FORCE");
+  }
+  return cuda_status(e, "discos_spread");
+}
+
+discos_status discos_solve_poisson(discos_handle* h, const void* rho, void* phi, void* stream) {
+  if (!h) return invalid("null handle");
+  if (!rho || !phi) return invalid("null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = h->mixed ? launch_poisson<float>(h->P, h->W, (const float*)rho, (float*)phi, s)
+                           : launch_poisson<double>(h->P, h->W, (const double*)rho, (double*)phi, s);
+  return cuda_status(e, "discos_solve_poisson");
+}
+
+discos_status discos_solve_stokes(discos_handle* h, const void* f, void* v, void* p, void* stream) {
+  if (!h) return invalid("null handle");
+  if (!f || !v) return invalid("null pointer");
+  if (!(h->P.eta > 0.0)) return invalid("eta must be positive");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = h->mixed ? launch_stokes<float>(h->P, h->W, (const float*)f, (float*)v, (float*)p, s)
+                           : launch_stokes<double>(h->P, h->W, (const double*)f, (double*)v, (double*)p, s);
+  return cuda_status(e, "discos_solve_stokes");
+}
+
+discos_status discos_interpolate(discos_handle* h, const void* x, int N, int which, const void* grid, void* out,
+                                 void* stream) {
+  discos_status st = check_n(h, N);
+  if (st) return st;
+  if (!grid || (N > 0 && (!x || !out))) return invalid("null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (which == DISCOS_INTERP_EFIELD) {
+    e = h->mixed ? launch_interp_efield<float>(h->P, (const float*)x, nullptr, N, (const float*)grid, (float*)out, false, s)
+                 : launch_interp_efield<double>(h->P, (const double*)x, nullptr, N, (const double*)grid, (double*)out, false, s);
+  } else if (which == DISCOS_INTERP_VELOCITY) {
+    e = h->mixed ? launch_interp_velocity<float>(h->P, (const float*)x, N, (const float*)grid, (float*)out, s)
+                 : launch_interp_velocity<double>(h->P, (const double*)x, N, (const double*)grid, (double*)out, s);
+  } else {
+    return invalid("which must be DISCOS_INTERP_EFIELD or DISCOS_INTERP_VELOCITY");
+  }
+  return cuda_status(e, "discos_interpolate");
+}
+
+discos_status discos_cell_list(discos_handle* h, const void* x, int N, int* cell_start, int* perm, int* n_cells_out,
+                               void* stream) {
+  discos_status st = check_n(h, N);
+  if (st) return st;
+  if (N > 0 && !x) return invalid("null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_cells_out) *n_cells_out = h->W.n_cells;
+  cudaError_t e = h->mixed ? launch_cell_list<float>(h->P, h->W, (const float*)x, N, s)
+                           : launch_cell_list<double>(h->P, h->W, (const double*)x, N, s);
+  if (e == cudaSuccess && cell_start)
+    e = cudaMemcpyAsync(cell_start, h->W.cell_start, sizeof(int) * (h->W.n_cells + 1), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && perm && N > 0)
+    e = cudaMemcpyAsync(perm, h->W.perm, sizeof(int) * N, cudaMemcpyDeviceToDevice, s);
+  return cuda_status(e, "discos_cell_list");
+}
+
+discos_status discos_near_field(discos_handle* h, const void* x, const void* q, const int* species, int N, void* F,
+                                int* nbr_count, void* stream) {
+  discos_status st = check_n(h, N);
+  if (st) return st;
+  if (N > 0 && (!x || !q || !F)) return invalid("null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = h->mixed
+      ? launch_near_field<float>(h->P, h->W, (const float*)x, (const float*)q, species, N, (float*)F, nbr_count, s)
+      : launch_near_field<double>(h->P, h->W, (const double*)x, (const double*)q, species, N, (double*)F, nbr_count, s);
+  return cuda_status(e, "discos_near_field");
+}
+
+discos_status discos_forces(discos_handle* h, const void* x, const void* q, const int* species, int N, void* F,
+                            int* nbr_count, void* stream) {
+  discos_status st = check_n(h, N);
+  if (st) return st;
+  if (N > 0 && (!x || !q || !F)) return invalid("null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  return h->mixed ? forces_impl<float>(h, (const float*)x, (const float*)q, species, N, (float*)F, nbr_count, s)
+                  : forces_impl<double>(h, (const double*)x, (const double*)q, species, N, (double*)F, nbr_count, s);
+}
+
+discos_status discos_step(discos_handle* h, void* x, const void* q, const int* species, int N, int64_t step0,
+                          int nsteps, void* F_out, void* stream) {
+  discos_status st = check_n(h, N);
+  if (st) return st;
+  if (nsteps < 0) return invalid("nsteps must be >= 0");
+  if (N > 0 && (!x || !q)) return invalid("null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  return h->mixed ? step_impl<float>(h, (float*)x, (const float*)q, species, N, step0, nsteps, (float*)F_out, s)
+                  : step_impl<double>(h, (double*)x, (const double*)q, species, N, step0, nsteps, (double*)F_out, s);
+}
+
+}  // extern "C"

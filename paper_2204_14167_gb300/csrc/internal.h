@@ -1,0 +1,104 @@
+// Internal declarations shared by the libdiscos translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include "../../include/discos.h"
+#include "common.cuh"
+
+namespace discos {
+
+// Everything a kernel needs to know about the run, passed by value.
+struct Params {
+  int Nx, Ny, Nz;
+  int Nxh, Px;                 // Nx/2 + 1 x-modes, padded row pitch of spectra
+  int bc[2];
+  double phi_b[2];
+  double slope[2];             // dphi/dy on Neumann walls (bottom, top)
+  KernelParams kes, khy;
+  double lB, eta, kT, dt, psi;
+  int n_tab;
+  double tab_scale;            // n_tab / psi
+  int nspecies;
+  double D_dry[DISCOS_MAX_SPECIES], D_tot[DISCOS_MAX_SPECIES], D_wet[DISCOS_MAX_SPECIES];
+  double gamma[DISCOS_MAX_SPECIES][2][2][7];
+  double lj_sigma[DISCOS_MAX_SPECIES][DISCOS_MAX_SPECIES];
+  double lj_xi[DISCOS_MAX_SPECIES][DISCOS_MAX_SPECIES];
+  double lj_rc[DISCOS_MAX_SPECIES][DISCOS_MAX_SPECIES];
+  int wall_type;
+  double wall_sigma[DISCOS_MAX_SPECIES], wall_xi[DISCOS_MAX_SPECIES], wall_rc[DISCOS_MAX_SPECIES];
+  double E_ext[3];
+  int k_cell, ncx, ncy, ncz;
+  int drift;
+  uint64_t seed;
+};
+
+// Device workspace owned by a handle.
+struct Workspace {
+  // grids
+  void* phi = nullptr;         // [Nz][Ny][Nx] real: rho, then phi
+  void* spec = nullptr;        // 3 spectra [Nz][Ny+1][Px] complex real
+  void* fgrid = nullptr;       // fx|fy|fz real
+  double* inv_m = nullptr;     // Poisson Thomas pivots [Ny][modes]
+  void* tw_x = nullptr;        // twiddles exp(-2 pi i k / Nx), k < Nx/2
+  void* tw_z = nullptr;        // twiddles exp(-2 pi i k / Nz), k < Nz/2
+  void* fptab = nullptr;       // F^P table [n_tab + 1] real
+  // ions
+  int* cell_of = nullptr;      // [max_ions]
+  int* counts = nullptr;       // [n_cells]
+  int* fill = nullptr;         // [n_cells]
+  int* cell_start = nullptr;   // [n_cells + 1]
+  int* perm = nullptr;         // [max_ions]
+  int* tile_sums = nullptr;    // scan scratch
+  void* xs = nullptr;          // sorted positions [3][max_ions] real
+  void* qs = nullptr;          // sorted charges [max_ions] real
+  int* sps = nullptr;          // sorted species [max_ions]
+  void* F = nullptr;           // forces [3][max_ions] real
+  void* xstar = nullptr;       // midpoint positions [3][max_ions] real
+  void* V = nullptr;           // interpolated velocities [3][max_ions] real
+  int n_cells = 0;
+};
+
+}  // namespace discos
+
+struct discos_handle {
+  discos_config cfg;
+  discos::Params P;
+  discos::Workspace W;
+  bool mixed;
+  discos_alloc_fn alloc_fn;
+  discos_free_fn free_fn;
+  void* alloc_ctx;
+  int device;
+};
+
+namespace discos {
+
+void set_error(const std::string& msg);
+discos_status cuda_status(cudaError_t e, const char* where);
+
+// Host code that builds the F^P table (fptable.cpp).
+bool build_fp_table(const KernelParams& kp, double psi, int n_tab, double* out, std::string* err);
+double es_normalisation(int w, double beta);
+
+// Launch wrappers (one per kernel family); T = float or double.
+template <typename T> cudaError_t launch_cell_list(const Params& P, Workspace& W, const T* x, int N, cudaStream_t s);
+template <typename T> cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N, T* rho, cudaStream_t s);
+template <typename T> cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, T* f,
+                                                      int64_t step, bool rfd, cudaStream_t s);
+template <typename T> cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_t s);
+template <typename T> cudaError_t launch_poisson(const Params& P, Workspace& W, const T* rho, T* phi, cudaStream_t s);
+template <typename T> cudaError_t launch_stokes(const Params& P, Workspace& W, const T* f, T* v, T* p, cudaStream_t s);
+template <typename T> cudaError_t launch_interp_efield(const Params& P, const T* x, const T* q, int N, const T* phi,
+                                                       T* out, bool as_force, cudaStream_t s);
+template <typename T> cudaError_t launch_interp_velocity(const Params& P, const T* x, int N, const T* v, T* out,
+                                                         cudaStream_t s);
+template <typename T> cudaError_t launch_near_field(const Params& P, Workspace& W, const T* x, const T* q,
+                                                    const int* species, int N, T* F, int* nbr, cudaStream_t s);
+template <typename T> cudaError_t launch_dry_update(const Params& P, T* x, const int* species, const T* F,
+                                                   const T* V, int N, int64_t step, cudaStream_t s);
+template <typename T> cudaError_t launch_midpoint(const Params& P, const T* x, const T* V, int N, T* xstar,
+                                                  cudaStream_t s);
+template <typename T> cudaError_t launch_fill_zero(T* p, size_t n, cudaStream_t s);
+
+}  // namespace discos

@@ -1,0 +1,194 @@
+// Near-field forces over the cell list: the P3M local correction of
+// Eqs. fullElectro and LC, F^LC = l_B q_i q_j (1/r^2 - f^P(r)) rhat for every
+// partner within psi, including the mirror images of the ions across each
+// wall (charge -q at a Dirichlet wall, +q at a Neumann wall, Sec. II.B.1); the
+// ion-ion LJ force of Eq. closerange; and the wall force of Sec. II.B.2.
+//
+// One thread per ion in cell order (neighbouring threads share cells, so the
+// partner loads hit the same lines).  Each ion sums over its own partners
+// (full neighbour loop, no atomics, deterministic order).  Whether a pair is
+// inside a cutoff is decided with one rounding per operation in the order
+// dx = x_i - x_j, minimum image by +-L, r2 = (dx^2 + dy^2) + dz^2, so the
+// neighbour counts are reproducible bit for bit.  Image partners of ion i
+// can only sit in the list-cell row next to the wall, because a list cell is
+// at least psi wide.
+#include "internal.h"
+
+namespace discos {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ int cell_coord(T v, int k, int nc) {
+  int c = (int)floor(v);
+  c = c < 0 ? 0 : c / k;
+  return c < nc ? c : nc - 1;
+}
+
+template <typename T>
+__global__ void k_gather(const T* __restrict__ x, const T* __restrict__ q, const int* __restrict__ species, int N,
+                         const int* __restrict__ perm, T* __restrict__ xs, T* __restrict__ qs, int* __restrict__ sps) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  int i = perm[s];
+  xs[s] = x[i];
+  xs[N + s] = x[N + i];
+  xs[2 * N + s] = x[2 * N + i];
+  qs[s] = q[i];
+  sps[s] = species ? species[i] : 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T min_image(T d, T L, T half) {
+  if (d > half) return sub_rn(d, L);
+  if (d < -half) return add_rn(d, L);
+  return d;
+}
+
+template <typename T>
+__device__ __forceinline__ T fp_lookup(const T* __restrict__ tab, int n_tab, T scale, T r) {
+  T t = r * scale;
+  int k = (int)t;
+  if (k > n_tab - 1) k = n_tab - 1;
+  T fr = t - T(k);
+  T a = tab[k], b = tab[k + 1];
+  return a + fr * (b - a);
+}
+
+template <typename T>
+__global__ void k_near_field(const T* __restrict__ xs, const T* __restrict__ qs, const int* __restrict__ sps,
+                             const int* __restrict__ perm, const int* __restrict__ start, int N, Params P,
+                             const T* __restrict__ tab, T* __restrict__ F, int* __restrict__ nbr) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  const T xi = xs[s], yi = xs[N + s], zi = xs[2 * N + s], qi = qs[s];
+  const int si = sps[s];
+  const int cx = cell_coord(xi, P.k_cell, P.ncx);
+  const int cy = cell_coord(yi, P.k_cell, P.ncy);
+  const int cz = cell_coord(zi, P.k_cell, P.ncz);
+  const T Lx = T(P.Nx), Lz = T(P.Nz), hx = mul_rn(T(0.5), Lx), hz = mul_rn(T(0.5), Lz);
+  const T psi = T(P.psi);
+  const T psi2 = mul_rn(psi, psi);
+  const T lB = T(P.lB), scale = T(P.tab_scale);
+  T fx = T(0), fy = T(0), fz = T(0);
+  int cnt = 0;
+  for (int dz = -1; dz <= 1; ++dz) {
+    int czz = cz + dz;
+    czz = czz < 0 ? czz + P.ncz : (czz >= P.ncz ? czz - P.ncz : czz);
+    for (int dy = -1; dy <= 1; ++dy) {
+      int cyy = cy + dy;
+      if (cyy < 0 || cyy >= P.ncy) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        int cxx = cx + dx;
+        cxx = cxx < 0 ? cxx + P.ncx : (cxx >= P.ncx ? cxx - P.ncx : cxx);
+        int c = (czz * P.ncy + cyy) * P.ncx + cxx;
+        int b = start[c], e = start[c + 1];
+        for (int j = b; j < e; ++j) {
+          if (j == s) continue;
+          T ddx = min_image(sub_rn(xi, xs[j]), Lx, hx);
+          T ddy = sub_rn(yi, xs[N + j]);
+          T ddz = min_image(sub_rn(zi, xs[2 * N + j]), Lz, hz);
+          T r2 = add_rn(add_rn(mul_rn(ddx, ddx), mul_rn(ddy, ddy)), mul_rn(ddz, ddz));
+          const int sj = sps[j];
+          T rcl = T(P.lj_rc[si][sj]);
+          bool in_psi = r2 < psi2;
+          bool in_lj = r2 < mul_rn(rcl, rcl);
+          if (!(in_psi || in_lj)) continue;
+          T r = sqrt(r2);
+          T coef = T(0);
+          if (in_psi) {
+            coef += lB * qi * qs[j] * (T(1) / r2 - fp_lookup(tab, P.n_tab, scale, r));
+            ++cnt;
+          }
+          if (in_lj) {
+            T sg = T(P.lj_sigma[si][sj]);
+            T sr2 = sg * sg / r2;
+            T sr6 = sr2 * sr2 * sr2;
+            coef += T(24) * T(P.lj_xi[si][sj]) / r * (T(2) * sr6 * sr6 - sr6);
+          }
+          T cr = coef / r;
+          fx += cr * ddx; fy += cr * ddy; fz += cr * ddz;
+        }
+      }
+    }
+  }
+  // wall images: bottom (y -> -y) and top (y -> 2 Ny - y)
+  for (int wall = 0; wall < 2; ++wall) {
+    bool near = wall == 0 ? (yi < psi) : (sub_rn(T(P.Ny), yi) < psi);
+    if (!near) continue;
+    const T sgn = P.bc[wall] == DISCOS_BC_DIRICHLET ? T(-1) : T(1);
+    const int cyy = wall == 0 ? 0 : P.ncy - 1;
+    const T twoNy = T(2 * P.Ny);
+    for (int dz = -1; dz <= 1; ++dz) {
+      int czz = cz + dz;
+      czz = czz < 0 ? czz + P.ncz : (czz >= P.ncz ? czz - P.ncz : czz);
+      for (int dx = -1; dx <= 1; ++dx) {
+        int cxx = cx + dx;
+        cxx = cxx < 0 ? cxx + P.ncx : (cxx >= P.ncx ? cxx - P.ncx : cxx);
+        int c = (czz * P.ncy + cyy) * P.ncx + cxx;
+        int b = start[c], e = start[c + 1];
+        for (int j = b; j < e; ++j) {
+          T yj = xs[N + j];
+          T yimg = wall == 0 ? -yj : sub_rn(twoNy, yj);
+          T ddx = min_image(sub_rn(xi, xs[j]), Lx, hx);
+          T ddy = sub_rn(yi, yimg);
+          T ddz = min_image(sub_rn(zi, xs[2 * N + j]), Lz, hz);
+          T r2 = add_rn(add_rn(mul_rn(ddx, ddx), mul_rn(ddy, ddy)), mul_rn(ddz, ddz));
+          if (!(r2 < psi2)) continue;
+          T r = sqrt(r2);
+          T coef = lB * qi * (sgn * qs[j]) * (T(1) / r2 - fp_lookup(tab, P.n_tab, scale, r));
+          ++cnt;
+          T cr = coef / r;
+          fx += cr * ddx; fy += cr * ddy; fz += cr * ddz;
+        }
+      }
+    }
+  }
+  // short-range wall force (Sec. II.B.2): 12-6 repulsion or the 9-3 form of Eq. LJ93
+  {
+    const T rc = T(P.wall_rc[si]), sg = T(P.wall_sigma[si]), xiw = T(P.wall_xi[si]);
+    for (int wall = 0; wall < 2; ++wall) {
+      T d = wall == 0 ? yi : sub_rn(T(P.Ny), yi);
+      if (!(d < rc)) continue;
+      T f;
+      if (P.wall_type == DISCOS_WALL_WCA) {
+        T sr2 = sg * sg / (d * d);
+        T sr6 = sr2 * sr2 * sr2;
+        f = T(24) * xiw / d * (T(2) * sr6 * sr6 - sr6);
+      } else {
+        T s3 = sg * sg * sg;
+        T d2 = d * d, d4 = d2 * d2;
+        f = T(1.5) * sqrt(T(3)) * xiw * (T(9) * s3 * s3 * s3 / (d4 * d4 * d2) - T(3) * s3 / d4);
+      }
+      fy += wall == 0 ? f : -f;
+    }
+  }
+  const int i = perm[s];
+  F[i] += fx;
+  F[N + i] += fy;
+  F[2 * N + i] += fz;
+  if (nbr) nbr[i] = cnt;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_near_field(const Params& P, Workspace& W, const T* x, const T* q, const int* species, int N,
+                              T* F, int* nbr, cudaStream_t s) {
+  if (N <= 0) return cudaSuccess;
+  cudaError_t e = launch_cell_list<T>(P, W, x, N, s);
+  if (e != cudaSuccess) return e;
+  T* xs = reinterpret_cast<T*>(W.xs);
+  T* qs = reinterpret_cast<T*>(W.qs);
+  int bs = 256;
+  int nb = (N + bs - 1) / bs;
+  k_gather<T><<<nb, bs, 0, s>>>(x, q, species, N, W.perm, xs, qs, W.sps);
+  k_near_field<T><<<(N + 127) / 128, 128, 0, s>>>(xs, qs, W.sps, W.perm, W.cell_start, N, P,
+                                                  reinterpret_cast<const T*>(W.fptab), F, nbr);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_near_field<float>(const Params&, Workspace&, const float*, const float*, const int*, int, float*, int*, cudaStream_t);
+template cudaError_t launch_near_field<double>(const Params&, Workspace&, const double*, const double*, const int*, int, double*, int*, cudaStream_t);
+
+}  // namespace discos

@@ -1,0 +1,89 @@
+// Stochastic stress forcing sqrt(2 kT eta / (dV dt)) div_h Z of
+// Eq. stokes_temporal on the MAC faces.  Z is symmetric: diagonal entries
+// sqrt(2) N(0,1) at cell centres, off-diagonal entries N(0,1) on the edges
+// (xy at (x=i, y=j), xz at (x=i, z=k), yz at (y=j, z=k), j = 0..Ny), the
+// off-diagonal entries on the wall edges scaled by sqrt(2) so that the noise
+// covariance matches the no-slip viscous operator (discrete fluctuation-
+// dissipation balance).  Normals come from Philox counters
+// (cell of an Nx x (Ny+1) x Nz lattice, step, 0, tag 3 / tag 4).
+//
+// Each block generates Z for a 32 x 4 x 4 tile of cells plus a one-cell halo
+// in shared memory (two Philox draws per halo cell) and then forms the three
+// face divergences of its cells, adding them to the force grids.
+#include "internal.h"
+
+namespace discos {
+
+namespace {
+
+constexpr int TX = 32, TY = 4, TZ = 4;
+constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
+constexpr int HN = HX * HY * HZ;
+
+template <typename T>
+__global__ void k_stress_noise(T* __restrict__ f, Params P, long long step, T amp) {
+  __shared__ T Zd[3][HN];     // xx, yy, zz
+  __shared__ T Ze[3][HN];     // xy, xz, yz
+  const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * TZ;
+  const int tid = threadIdx.x;
+  const T r2 = T(1.4142135623730951);
+  for (int h = tid; h < HN; h += blockDim.x) {
+    int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+    int i = (i0 + hx - 1) & (Nx - 1);
+    int j = j0 + hy - 1;
+    int k = (k0 + hz - 1) & (Nz - 1);
+    T a[4] = {T(0), T(0), T(0), T(0)}, b[4] = {T(0), T(0), T(0), T(0)};
+    if (j >= 0 && j <= Ny) {
+      uint32_t cell = (uint32_t)(((size_t)k * (Ny + 1) + j) * Nx + i);
+      normals4(u32x4{cell, (uint32_t)step, 0u, (uint32_t)TAG_STRESS_A}, P.seed, a);
+      normals4(u32x4{cell, (uint32_t)step, 0u, (uint32_t)TAG_STRESS_B}, P.seed, b);
+    }
+    bool centre = j >= 0 && j < Ny;
+    T wall = (j == 0 || j == Ny) ? r2 : T(1);
+    Zd[0][h] = centre ? r2 * a[0] : T(0);
+    Zd[1][h] = centre ? r2 * a[1] : T(0);
+    Zd[2][h] = centre ? r2 * a[2] : T(0);
+    Ze[0][h] = (j >= 0 && j <= Ny) ? wall * a[3] : T(0);   // xy
+    Ze[1][h] = centre ? b[0] : T(0);                         // xz
+    Ze[2][h] = (j >= 0 && j <= Ny) ? wall * b[1] : T(0);   // yz
+  }
+  __syncthreads();
+  const size_t G = (size_t)Nx * Ny * Nz;
+  T* fx = f;
+  T* fy = f + G;
+  T* fz = f + G + (size_t)Nx * (Ny + 1) * Nz;
+  for (int c = tid; c < TX * TY * TZ; c += blockDim.x) {
+    int lx = c % TX, ly = (c / TX) % TY, lz = c / (TX * TY);
+    int i = i0 + lx, j = j0 + ly, k = k0 + lz;
+    if (i >= Nx || j >= Ny || k >= Nz) continue;
+    int h = ((lz + 1) * HY + (ly + 1)) * HX + (lx + 1);
+    const int sx = 1, sy = HX, sz = HX * HY;
+    // x-face (i, j+1/2, k+1/2)
+    T dx = (Zd[0][h] - Zd[0][h - sx]) + (Ze[0][h + sy] - Ze[0][h]) + (Ze[1][h + sz] - Ze[1][h]);
+    // z-face (i+1/2, j+1/2, k)
+    T dz = (Ze[1][h + sx] - Ze[1][h]) + (Ze[2][h + sy] - Ze[2][h]) + (Zd[2][h] - Zd[2][h - sz]);
+    fx[((size_t)k * Ny + j) * Nx + i] += amp * dx;
+    fz[((size_t)k * Ny + j) * Nx + i] += amp * dz;
+    if (j >= 1) {
+      // y-face (i+1/2, j, k+1/2)
+      T dy = (Ze[0][h + sx] - Ze[0][h]) + (Zd[1][h] - Zd[1][h - sy]) + (Ze[2][h + sz] - Ze[2][h]);
+      fy[((size_t)k * (Ny + 1) + j) * Nx + i] += amp * dy;
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_t s) {
+  dim3 grid((P.Nx + TX - 1) / TX, (P.Ny + TY - 1) / TY, (P.Nz + TZ - 1) / TZ);
+  T amp = T(sqrt(2.0 * P.kT * P.eta / P.dt));
+  k_stress_noise<T><<<grid, 256, 0, s>>>(f, P, (long long)step, amp);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_stress_noise<float>(const Params&, float*, int64_t, cudaStream_t);
+template cudaError_t launch_stress_noise<double>(const Params&, double*, int64_t, cudaStream_t);
+
+}  // namespace discos

@@ -1,0 +1,175 @@
+// Spreading (Eq. kernel2) of charges onto cell centres and of forces onto the
+// MAC faces, with the wall image construction of Sec. II.A (Fig. folded) and
+// Sec. II.B.1 applied as an index fold: a stencil point outside the channel
+// is mapped to its mirror inside with the image sign.
+//
+// Thread layout: a group of 8 lanes per ion (4 ions per warp); lane l owns
+// x-offset l of the stencil, so each warp-wide atomic touches 4 short runs of
+// consecutive addresses.  The y and z weights are computed by the lanes of
+// the group and broadcast with shuffles.
+#include "internal.h"
+
+namespace discos {
+
+namespace {
+
+template <typename T>
+__global__ void k_spread_charge(const T* __restrict__ x, const T* __restrict__ q, int N, Params P,
+                                T* __restrict__ rho) {
+  const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
+  const KernelParams kp = P.kes;
+  const int w = kp.w;
+  int ion = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  int l = threadIdx.x & 7;
+  int gbase = (threadIdx.x & 31) & ~7;
+  bool valid = ion < N;
+  T px = T(0.5), py = T(0.5), pz = T(0.5), qq = T(0);
+  if (valid) {
+    px = x[ion]; py = x[N + ion]; pz = x[2 * N + ion]; qq = q[ion];
+  }
+  T sx = px - T(0.5), sy = py - T(0.5), sz = pz - T(0.5);
+  int x0 = stencil_start(sx, w), y0 = stencil_start(sy, w), z0 = stencil_start(sz, w);
+  T wx = l < w ? kval(sx - T(x0 + l), kp) : T(0);
+  T wy = l < w ? kval(sy - T(y0 + l), kp) : T(0);
+  T wz = l < w ? kval(sz - T(z0 + l), kp) : T(0);
+  int ix = (x0 + l) & (Nx - 1);
+  const T s0 = P.bc[0] == DISCOS_BC_DIRICHLET ? T(-1) : T(1);
+  const T s1 = P.bc[1] == DISCOS_BC_DIRICHLET ? T(-1) : T(1);
+  for (int jz = 0; jz < w; ++jz) {
+    T wzj = __shfl_sync(0xffffffffu, wz, gbase + jz);
+    int iz = (z0 + jz) & (Nz - 1);
+    for (int jy = 0; jy < w; ++jy) {
+      T wyj = __shfl_sync(0xffffffffu, wy, gbase + jy);
+      int iy = y0 + jy;
+      T sg = T(1);
+      if (iy < 0) { iy = -1 - iy; sg = s0; }
+      else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = s1; }
+      if (valid && l < w && iy >= 0 && iy < Ny)
+        atomicAdd(&rho[((size_t)iz * Ny + iy) * Nx + ix], qq * sg * wzj * wyj * wx);
+    }
+  }
+}
+
+// Force spreading for one MAC component c (blockIdx.y), no-slip images
+// (sign -1 for every component).  With rfd, adds the thermal forcing of
+// Eq. thermforce: the random finite difference
+//   (kT/delta) [S(x + delta W/2) W - S(x - delta W/2) W]
+// in its delta -> 0 form kT W_c (W . grad_x) S, which equals the finite
+// difference to O(delta^2) and has no cancellation in single precision.
+template <typename T>
+__global__ void k_spread_force(const T* __restrict__ x, const T* __restrict__ F, int N, Params P,
+                               T* __restrict__ f, long long step, int rfd) {
+  const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
+  const KernelParams kp = P.khy;
+  const int w = kp.w;
+  const int c = blockIdx.y;
+  int ion = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  int l = threadIdx.x & 7;
+  int gbase = (threadIdx.x & 31) & ~7;
+  bool valid = ion < N;
+  T p[3] = {T(0.5), T(0.5), T(0.5)};
+  T Fc = T(0);
+  T Wr[3] = {T(0), T(0), T(0)};
+  if (valid) {
+    p[0] = x[ion]; p[1] = x[N + ion]; p[2] = x[2 * N + ion];
+    Fc = F[(size_t)c * N + ion];
+    if (rfd) {
+      T g[4];
+      normals4(u32x4{(uint32_t)ion, (uint32_t)step, 0u, (uint32_t)TAG_RFD}, P.seed, g);
+      Wr[0] = g[0]; Wr[1] = g[1]; Wr[2] = g[2];
+    }
+  }
+  // grid point 0 sits at offset 0 along axis c (faces) and 1/2 otherwise
+  T s[3];
+  int st[3];
+  T wv[3], wd[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    s[d] = p[d] - (d == c ? T(0) : T(0.5));
+    st[d] = stencil_start(s[d], w);
+    T z = s[d] - T(st[d] + l);
+    wv[d] = l < w ? kval(z, kp) : T(0);
+    wd[d] = (l < w && rfd) ? kder(z, kp) : T(0);
+  }
+  const T a = T(P.kT) * Wr[c];
+  const int Nyg = (c == 1) ? Ny + 1 : Ny;
+  size_t off = 0;
+  if (c >= 1) off += (size_t)Nz * Ny * Nx;
+  if (c == 2) off += (size_t)Nz * (Ny + 1) * Nx;
+  T* g = f + off;
+  int ix = (st[0] + l) & (Nx - 1);
+  for (int jz = 0; jz < w; ++jz) {
+    T wzj = __shfl_sync(0xffffffffu, wv[2], gbase + jz);
+    T dzj = __shfl_sync(0xffffffffu, wd[2], gbase + jz);
+    int iz = (st[2] + jz) & (Nz - 1);
+    for (int jy = 0; jy < w; ++jy) {
+      T wyj = __shfl_sync(0xffffffffu, wv[1], gbase + jy);
+      T dyj = __shfl_sync(0xffffffffu, wd[1], gbase + jy);
+      int iy = st[1] + jy;
+      T sg = T(1);
+      bool ok = true;
+      if (c == 1) {             // y-faces 0..Ny; wall faces receive real + image = 0
+        if (iy < 0) { iy = -iy; sg = T(-1); }
+        else if (iy > Ny) { iy = 2 * Ny - iy; sg = T(-1); }
+        ok = iy > 0 && iy < Ny;
+      } else {                  // cell-centred in y
+        if (iy < 0) { iy = -1 - iy; sg = T(-1); }
+        else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = T(-1); }
+        ok = iy >= 0 && iy < Ny;
+      }
+      T val = Fc * wv[0] * wyj * wzj;
+      if (rfd) val += a * (Wr[0] * wd[0] * wyj * wzj + Wr[1] * wv[0] * dyj * wzj + Wr[2] * wv[0] * wyj * dzj);
+      if (valid && l < w && ok) atomicAdd(&g[((size_t)iz * Nyg + iy) * Nx + ix], sg * val);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_fill(T* __restrict__ p, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) p[i] = T(0);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_fill_zero(T* p, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int bs = 256;
+  size_t nb = (n + bs - 1) / bs;
+  if (nb > 152 * 16) nb = 152 * 16;
+  k_fill<T><<<(unsigned)nb, bs, 0, s>>>(p, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N, T* rho, cudaStream_t s) {
+  cudaError_t e = launch_fill_zero(rho, (size_t)P.Nx * P.Ny * P.Nz, s);
+  if (e != cudaSuccess || N <= 0) return e;
+  int bs = 256;
+  int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
+  k_spread_charge<T><<<nb, bs, 0, s>>>(x, q, N, P, rho);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, T* f, int64_t step, bool rfd,
+                                cudaStream_t s) {
+  size_t n = (size_t)P.Nx * P.Nz * (3 * P.Ny + 1);
+  cudaError_t e = launch_fill_zero(f, n, s);
+  if (e != cudaSuccess || N <= 0) return e;
+  int bs = 256;
+  dim3 grid((unsigned)(((size_t)N * 8 + bs - 1) / bs), 3);
+  k_spread_force<T><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_fill_zero<float>(float*, size_t, cudaStream_t);
+template cudaError_t launch_fill_zero<double>(double*, size_t, cudaStream_t);
+template cudaError_t launch_spread_charge<float>(const Params&, const float*, const float*, int, float*, cudaStream_t);
+template cudaError_t launch_spread_charge<double>(const Params&, const double*, const double*, int, double*, cudaStream_t);
+template cudaError_t launch_spread_force<float>(const Params&, const float*, const float*, int, float*, int64_t, bool, cudaStream_t);
+template cudaError_t launch_spread_force<double>(const Params&, const double*, const double*, int, double*, int64_t, bool, cudaStream_t);
+
+}  // namespace discos

@@ -1,0 +1,65 @@
+"""Workload presets: synthetic channels shaped like the paper's runs.
+
+Each preset returns (RunConfig, ion recipe).  Reduced units: grid spacing 1,
+kT = 1.  The near-field cutoff psi = 4 is where the grid pair force of the
+4- and 6-point kernels has reached Coulomb to within 0.7%.
+"""
+import math
+
+from . import RunConfig, BC_DIRICHLET, BC_NEUMANN, KERNEL_PESKIN4, KERNEL_PESKIN6, FP64, MIXED
+from . import mobility
+
+WCA = 2.0 ** (1.0 / 6.0)
+A_WET_PESKIN4 = 0.91     # hydrodynamic radius of the 4-point kernel in grid units
+
+
+def _wca(sigma):
+    return dict(lj_sigma=[[sigma]], lj_xi=[[1.0]], lj_rc=[[WCA * sigma]])
+
+
+def _wall():
+    # repulsive 12-6 wall cut at 1 cell (sigma = 2^-1/6)
+    return dict(wall_sigma=[2.0 ** (-1.0 / 6.0)], wall_xi=[1.0], wall_rc=[1.0])
+
+
+def dry_channel_32(precision=FP64):
+    """32^3 channel, Dirichlet phi = 0 walls, 128 + 128 ions, l_B = 7,
+    6-point kernel, dry diffusion (D = 1, dt = 0.01)."""
+    gam = mobility.gamma_table(1.0, 1.0, 32.0)
+    cfg = RunConfig(Nx=32, Ny=32, Nz=32, bc=(BC_DIRICHLET, BC_DIRICHLET), kernel_es=KERNEL_PESKIN6,
+                    kernel_hy=KERNEL_PESKIN6, lB=7.0, dt=0.01, psi=4.0, n_tab=64, D_tot=[1.0], D_wet=[0.0],
+                    gamma_coef=[gam], wet=False, precision=precision, max_ions=256, **_wca(3.0), **_wall())
+    return cfg, dict(n_pos=128, n_neg=128, ymargin=1.0, min_sep=0.9 * 3.0, seed=20220429)
+
+
+def wet_channel_128x64x128(precision=MIXED):
+    """128 x 64 x 128 channel with dielectric (Neumann) walls, 10k + 10k ions,
+    Debye length ~4 cells (l_B = 0.261), E_x = 0.05, fluctuating Stokes with
+    no-slip walls, 50% wet (4-point kernel, a_w = 0.91, a_t = a_w / 2)."""
+    Ny = 64
+    eta = 1.0 / (6.0 * math.pi)
+    D_wet = 1.0 / A_WET_PESKIN4            # kT / (6 pi eta a_w)
+    D_tot = 2.0 * D_wet                    # a_t = a_w / 2
+    gam = mobility.gamma_table(0.5 * A_WET_PESKIN4, A_WET_PESKIN4, float(Ny))
+    cfg = RunConfig(Nx=128, Ny=Ny, Nz=128, bc=(BC_NEUMANN, BC_NEUMANN), kernel_es=KERNEL_PESKIN4,
+                    kernel_hy=KERNEL_PESKIN4, lB=0.261, eta=eta, kT=1.0, dt=0.01, psi=4.0, n_tab=64,
+                    D_tot=[D_tot], D_wet=[D_wet], gamma_coef=[gam], E_ext=(0.05, 0.0, 0.0), wet=True,
+                    precision=precision, max_ions=20000, **_wca(1.0), **_wall())
+    return cfg, dict(n_pos=10000, n_neg=10000, ymargin=1.0, min_sep=0.9, seed=20220430)
+
+
+def wet_channel_small(precision=MIXED, Nx=32, Ny=16, Nz=16, n=300):
+    """Small wet channel with the same physics as wet_channel_128x64x128, for
+    tests the oracle finishes in seconds."""
+    cfg, rec = wet_channel_128x64x128(precision)
+    cfg.Nx, cfg.Ny, cfg.Nz = Nx, Ny, Nz
+    cfg.gamma_coef = [mobility.gamma_table(0.5 * A_WET_PESKIN4, A_WET_PESKIN4, float(Ny))]
+    cfg.max_ions = max(n, 1)
+    rec = dict(rec, n_pos=n // 2, n_neg=n - n // 2)
+    return cfg, rec
+
+
+PRESETS = {
+    "dry_channel_32": dry_channel_32,
+    "wet_channel_128x64x128": wet_channel_128x64x128,
+}
