@@ -119,6 +119,10 @@ discos_status discos_destroy(discos_handle* h);
 /* Static description of the last error on this thread. */
 const char* discos_last_error(void);
 
+/* Number of CUDA kernels the library has enqueued since it was loaded (all
+ * handles, all threads); a diagnostic for launch accounting. */
+long long discos_launch_count(void);
+
 /* Spreading, Eq. kernel2 with the wall image construction of Sec. II.A
  * (Fig. folded) and Sec. II.B.1.
  * which = DISCOS_SPREAD_CHARGE: val = q[N]; grid = rho[Nz][Ny][Nx] cell

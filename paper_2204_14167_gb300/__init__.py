@@ -239,3 +239,8 @@ def fp_table(kernel, psi, n_tab, es_w=6, es_beta=8.0):
     out = (ctypes.c_double * (n_tab + 1))()
     _lib.check(lib.discos_fp_table(int(kernel), int(es_w), float(es_beta), float(psi), int(n_tab), out))
     return list(out)
+
+
+def launch_count():
+    """Kernels the library has enqueued since it was loaded."""
+    return int(_lib.load().discos_launch_count())

@@ -54,7 +54,7 @@ class Config(ctypes.Structure):
 EXPORTS = [
     "discos_create", "discos_destroy", "discos_last_error", "discos_spread", "discos_solve_poisson",
     "discos_solve_stokes", "discos_interpolate", "discos_cell_list", "discos_near_field", "discos_forces",
-    "discos_step", "discos_fp_table",
+    "discos_step", "discos_fp_table", "discos_launch_count",
 ]
 
 _lib = None
@@ -83,7 +83,9 @@ def load():
     lib.discos_step.argtypes = [vp, vp, vp, vp, i32, i64, i32, vp, vp]
     lib.discos_fp_table.argtypes = [i32, i32, D, D, i32, ctypes.POINTER(D)]
     for name in EXPORTS:
-        getattr(lib, name).restype = ctypes.c_int if name != "discos_last_error" else ctypes.c_char_p
+        getattr(lib, name).restype = ctypes.c_int
+    lib.discos_last_error.restype = ctypes.c_char_p
+    lib.discos_launch_count.restype = ctypes.c_longlong
     _lib = lib
     return lib
 

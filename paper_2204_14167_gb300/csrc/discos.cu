@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -14,8 +15,10 @@
 namespace discos {
 
 static thread_local std::string g_err;
+static std::atomic<long long> g_launches{0};
 
 void set_error(const std::string& msg) { g_err = msg; }
+void count_launches(long long n) { g_launches += n; }
 
 discos_status cuda_status(cudaError_t e, const char* where) {
   if (e == cudaSuccess) return DISCOS_OK;
@@ -101,10 +104,60 @@ void upload_table(void* dst, const std::vector<double>& t) {
   cudaMemcpy(dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
 }
 
+// Per-mode factors of the Stokes wall-normal systems (see k_stokes.cu):
+// the L D L^T factors of the pentadiagonal K^2 A_f + D_y^T A_c D_y
+// (diagonal K^4 + 4K^2 + 6, +1 on the first and last rows; first
+// off-diagonal -2K^2 - 4; second off-diagonal 1) and the Thomas pivots of
+// A_c (diagonal K^2 + 2, +1 on the wall rows; off-diagonals -1).
+void upload_stokes_factors(discos_handle* h) {
+  const discos_config& c = h->cfg;
+  const int Ny = c.Ny, Nxh = h->P.Nxh, Nz = c.Nz;
+  const size_t M = (size_t)Nxh * Nz;
+  const int n = Ny - 1;
+  std::vector<double> l1((size_t)n * M), l2((size_t)n * M), di((size_t)n * M), ci((size_t)Ny * M), mc(5 * M);
+  for (int kz = 0; kz < Nz; ++kz)
+    for (int kx = 0; kx < Nxh; ++kx) {
+      const size_t m = (size_t)kz * Nxh + kx;
+      const double tx = 2.0 * M_PI * kx / c.Nx, tz = 2.0 * M_PI * kz / c.Nz;
+      const double K2 = (2.0 - 2.0 * std::cos(tx)) + (2.0 - 2.0 * std::cos(tz));
+      const bool zero = kx == 0 && kz == 0;
+      mc[5 * m + 0] = std::cos(tx) - 1.0;
+      mc[5 * m + 1] = std::sin(tx);
+      mc[5 * m + 2] = std::cos(tz) - 1.0;
+      mc[5 * m + 3] = std::sin(tz);
+      mc[5 * m + 4] = zero ? 0.0 : -1.0 / K2;
+      const double e = -2.0 * K2 - 4.0, f = 1.0;
+      double Dm1 = 0.0, Dm2 = 0.0, l1m1 = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double a2 = i >= 2 ? f / Dm2 : 0.0;
+        double a1 = i >= 1 ? (e - (i >= 2 ? a2 * l1m1 * Dm2 : 0.0)) / Dm1 : 0.0;
+        double d = K2 * K2 + 4.0 * K2 + 6.0 + (i == 0 ? 1.0 : 0.0) + (i == n - 1 ? 1.0 : 0.0);
+        double D = d - a1 * a1 * Dm1 - a2 * a2 * Dm2;
+        l1[(size_t)i * M + m] = zero ? 0.0 : a1;
+        l2[(size_t)i * M + m] = zero ? 0.0 : a2;
+        di[(size_t)i * M + m] = zero ? 0.0 : 1.0 / D;
+        Dm2 = Dm1; Dm1 = D; l1m1 = a1;
+      }
+      double mm = 0.0;
+      for (int j = 0; j < Ny; ++j) {
+        double a = K2 + 2.0 + (j == 0 ? 1.0 : 0.0) + (j == Ny - 1 ? 1.0 : 0.0);
+        mm = j == 0 ? a : a - 1.0 / mm;
+        ci[(size_t)j * M + m] = 1.0 / mm;
+      }
+    }
+  Workspace& W = h->W;
+  cudaMemcpy(W.st_l1, l1.data(), sizeof(double) * l1.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(W.st_l2, l2.data(), sizeof(double) * l2.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(W.st_di, di.data(), sizeof(double) * di.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(W.st_ci, ci.data(), sizeof(double) * ci.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(W.st_mc, mc.data(), sizeof(double) * mc.size(), cudaMemcpyHostToDevice);
+}
+
 void free_workspace(discos_handle* h) {
   Workspace& W = h->W;
   void* ptrs[] = {W.phi, W.spec, W.fgrid, W.inv_m, W.tw_x, W.tw_z, W.fptab, W.cell_of, W.counts, W.fill,
-                  W.cell_start, W.perm, W.tile_sums, W.xs, W.qs, W.sps, W.F, W.xstar, W.V};
+                  W.cell_start, W.perm, W.tile_sums, W.xs, W.qs, W.sps, W.F, W.xstar, W.V,
+                  W.st_l1, W.st_l2, W.st_di, W.st_ci, W.st_mc, W.st_scratch, W.ps_scratch};
   for (void* p : ptrs) dfree(h, p);
   W = Workspace{};
 }
@@ -174,6 +227,8 @@ using namespace discos;
 extern "C" {
 
 const char* discos_last_error(void) { return g_err.c_str(); }
+
+long long discos_launch_count(void) { return g_launches.load(); }
 
 discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, discos_free_fn free_fn,
                             void* alloc_ctx, discos_handle** out) {
@@ -280,6 +335,16 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   W.F = dalloc(h, rs * 3 * M, &ok);
   W.xstar = dalloc(h, rs * 3 * M, &ok);
   W.V = dalloc(h, rs * 3 * M, &ok);
+  W.ps_scratch = (double*)dalloc(h, sizeof(double) * (size_t)c.Ny * ((2 * modes + 127) / 128 * 128), &ok);
+  if (c.wet) {
+    W.st_l1 = (double*)dalloc(h, sizeof(double) * (c.Ny - 1) * modes, &ok);
+    W.st_l2 = (double*)dalloc(h, sizeof(double) * (c.Ny - 1) * modes, &ok);
+    W.st_di = (double*)dalloc(h, sizeof(double) * (c.Ny - 1) * modes, &ok);
+    W.st_ci = (double*)dalloc(h, sizeof(double) * c.Ny * modes, &ok);
+    W.st_mc = (double*)dalloc(h, sizeof(double) * 5 * modes, &ok);
+    const size_t S2 = (2 * modes + 127) / 128 * 128;
+    W.st_scratch = (double*)dalloc(h, sizeof(double) * (2 * (size_t)c.Ny * S2 + 2 * (c.Ny + 1)), &ok);
+  }
   if (!ok) {
     free_workspace(h);
     delete h;
@@ -304,6 +369,7 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
       }
     cudaMemcpy(W.inv_m, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice);
   }
+  if (c.wet) upload_stokes_factors(h);
   std::vector<double> tab = cached_fp_table(P.kes, c.psi, c.n_tab);
   if (h->mixed) {
     upload_twiddles<float>(W.tw_x, c.Nx);
@@ -364,6 +430,7 @@ discos_status discos_solve_stokes(discos_handle* h, const void* f, void* v, void
   if (!h) return invalid("null handle");
   if (!f || !v) return invalid("null pointer");
   if (!(h->P.eta > 0.0)) return invalid("eta must be positive");
+  if (!h->cfg.wet) return invalid("the handle was created without the hydrodynamic stage (wet = 0)");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = h->mixed ? launch_stokes<float>(h->P, h->W, (const float*)f, (float*)v, (float*)p, s)
                            : launch_stokes<double>(h->P, h->W, (const double*)f, (double*)v, (double*)p, s);

@@ -56,6 +56,14 @@ struct Workspace {
   void* F = nullptr;           // forces [3][max_ions] real
   void* xstar = nullptr;       // midpoint positions [3][max_ions] real
   void* V = nullptr;           // interpolated velocities [3][max_ions] real
+  // Stokes wall-normal factors, [row][mode] in double (k_stokes.cu)
+  double* st_l1 = nullptr;     // pentadiagonal L D L^T: l1 [Ny-1][M]
+  double* st_l2 = nullptr;     // l2 [Ny-1][M]
+  double* st_di = nullptr;     // 1/D [Ny-1][M]
+  double* st_ci = nullptr;     // A_c Thomas reciprocal pivots [Ny][M]
+  double* st_mc = nullptr;     // per mode g_x, g_z, -1/K^2 [M][5]
+  double* st_scratch = nullptr;  // 2 x [Ny][2M] + 2 (Ny + 1)
+  double* ps_scratch = nullptr;  // Poisson forward values [Ny][2M rounded up to 128]
   int n_cells = 0;
 };
 
@@ -75,6 +83,8 @@ struct discos_handle {
 namespace discos {
 
 void set_error(const std::string& msg);
+// Number of kernels this library has launched since it was loaded.
+void count_launches(long long n);
 discos_status cuda_status(cudaError_t e, const char* where);
 
 // Host code that builds the F^P table (fptable.cpp).

@@ -145,13 +145,23 @@ cudaError_t launch_cell_list(const Params& P, Workspace& W, const T* x, int N, c
   cudaMemsetAsync(W.fill, 0, sizeof(int) * n, s);
   int bs = 256;
   int nb = (N + bs - 1) / bs;
-  if (nb > 0) k_bin<T><<<nb, bs, 0, s>>>(x, N, P, W.cell_of, W.counts);
+  if (nb > 0) {
+    k_bin<T><<<nb, bs, 0, s>>>(x, N, P, W.cell_of, W.counts);
+    count_launches(1);
+  }
   int ntiles = (n + kScanTile - 1) / kScanTile;
   k_tile_sums<<<ntiles, 256, 0, s>>>(W.counts, n, W.tile_sums);
+  count_launches(1);
   k_scan_tiles<<<1, 1024, 0, s>>>(W.tile_sums, ntiles);
+  count_launches(1);
   k_scan_apply<<<ntiles, kScanTile, 0, s>>>(W.counts, n, W.tile_sums, W.cell_start, N);
-  if (nb > 0) k_scatter<<<nb, bs, 0, s>>>(W.cell_of, N, W.cell_start, W.fill, W.perm);
+  count_launches(1);
+  if (nb > 0) {
+    k_scatter<<<nb, bs, 0, s>>>(W.cell_of, N, W.cell_start, W.fill, W.perm);
+    count_launches(1);
+  }
   k_sort_cells<<<(n + 255) / 256, 256, 0, s>>>(W.cell_start, n, W.perm);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -158,59 +158,53 @@ __global__ void k_fft_z(cplx<T>* __restrict__ data, int Nz, int logNz, int Nyr, 
 // Wall-normal tridiagonal solve per (kx, kz) mode, double precision.
 // Rows: (2 + lambda) phi_j - phi_{j-1} - phi_{j+1} = b_j with the wall rows
 // modified by the ghost cells (+1 on the diagonal at a Dirichlet wall, -1 at a
-// Neumann wall); inv_m holds the reciprocal Thomas pivots.  The (0, 0) mode of
-// a channel with two Neumann walls is singular: there phi_0 = 0, the last
-// equation (redundant for a neutral system) is dropped, and the mean is
-// removed afterwards.
+// Neumann wall); inv_m [Ny][M] holds the reciprocal Thomas pivots.  One
+// thread per (mode, part): the matrix is real, so the real and imaginary
+// parts are independent systems.  Forward values go to a private slot of the
+// double scratch Y [Ny][threads].  The (0, 0) mode of a channel with two
+// Neumann walls is singular: there phi_0 = 0, the last equation (redundant
+// for a neutral system) is dropped, and the mean is removed afterwards.
 template <typename T>
 __global__ void k_poisson_y(cplx<T>* __restrict__ S, const double* __restrict__ inv_m, int Ny, int Nz, int Nxh,
-                            int Px, int singular, double norm) {
-  extern __shared__ unsigned char smem_raw[];
-  double2* yb = reinterpret_cast<double2*>(smem_raw);
-  const int t = threadIdx.x;
-  const int kx = blockIdx.x * blockDim.x + t;
-  const int kz = blockIdx.y;
-  if (kx >= Nxh) return;
-  const size_t modes = (size_t)Nxh * Nz;
-  const size_t mode = (size_t)kz * Nxh + kx;
-  const size_t col = (size_t)kz * Ny * Px + kx;
-  const int B = blockDim.x;
-  if (singular && kx == 0 && kz == 0) {
-    double2 pm{0.0, 0.0}, pc{0.0, 0.0};
-    double2 sum{0.0, 0.0};
-    yb[0 * B + t] = pc;
+                            int Px, int singular, double norm, double* __restrict__ Y) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int M = Nxh * Nz;
+  const int mode = tid >> 1, part = tid & 1;
+  if (mode >= M) return;
+  const int kz = mode / Nxh, kx = mode - kz * Nxh;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  T* Sr = reinterpret_cast<T*>(S);
+  const size_t col = 2 * ((size_t)kz * Ny * Px + kx) + part;
+  const size_t rstep = 2 * (size_t)Px;
+  if (singular && mode == 0) {
+    double pm = 0.0, pc = 0.0, sum = 0.0;
+    Y[tid] = 0.0;
     for (int j = 0; j < Ny - 1; ++j) {
-      cplx<T> b = S[col + (size_t)j * Px];
-      double2 nx;
-      if (j == 0) { nx.x = pc.x - (double)b.re; nx.y = pc.y - (double)b.im; }
-      else { nx.x = 2.0 * pc.x - pm.x - (double)b.re; nx.y = 2.0 * pc.y - pm.y - (double)b.im; }
+      double b = (double)Sr[col + (size_t)j * rstep];
+      double nx = (j == 0) ? pc - b : 2.0 * pc - pm - b;
       pm = pc; pc = nx;
-      yb[(j + 1) * B + t] = nx;
+      Y[(size_t)(j + 1) * stride + tid] = nx;
     }
-    for (int j = 0; j < Ny; ++j) { sum.x += yb[j * B + t].x; sum.y += yb[j * B + t].y; }
-    sum.x /= Ny; sum.y /= Ny;
-    for (int j = 0; j < Ny; ++j) {
-      double2 v = yb[j * B + t];
-      S[col + (size_t)j * Px] = cplx<T>{T((v.x - sum.x) * norm), T((v.y - sum.y) * norm)};
-    }
+    for (int j = 0; j < Ny; ++j) sum += Y[(size_t)j * stride + tid];
+    const double mean = sum / Ny;
+    for (int j = 0; j < Ny; ++j) Sr[col + (size_t)j * rstep] = T((Y[(size_t)j * stride + tid] - mean) * norm);
     return;
   }
-  double2 prev{0.0, 0.0};
+  double prev = 0.0;
+#pragma unroll 4
   for (int j = 0; j < Ny; ++j) {
-    cplx<T> b = S[col + (size_t)j * Px];
-    double im = inv_m[(size_t)j * modes + mode];
-    prev.x = ((double)b.re + prev.x) * im;
-    prev.y = ((double)b.im + prev.y) * im;
-    yb[j * B + t] = prev;
+    double im = inv_m[(size_t)j * M + mode];
+    double b = (double)Sr[col + (size_t)j * rstep];
+    prev = fma(prev, im, b * im);
+    Y[(size_t)j * stride + tid] = prev;
   }
-  double2 xn = prev;
-  S[col + (size_t)(Ny - 1) * Px] = cplx<T>{T(xn.x * norm), T(xn.y * norm)};
+  double xn = prev;
+  Sr[col + (size_t)(Ny - 1) * rstep] = T(xn * norm);
+#pragma unroll 4
   for (int j = Ny - 2; j >= 0; --j) {
-    double im = inv_m[(size_t)j * modes + mode];
-    double2 v = yb[j * B + t];
-    xn.x = v.x + im * xn.x;
-    xn.y = v.y + im * xn.y;
-    S[col + (size_t)j * Px] = cplx<T>{T(xn.x * norm), T(xn.y * norm)};
+    double im = inv_m[(size_t)j * M + mode];
+    xn = fma(im, xn, Y[(size_t)j * stride + tid]);
+    Sr[col + (size_t)j * rstep] = T(xn * norm);
   }
 }
 
@@ -241,6 +235,7 @@ cudaError_t fft_x_forward(const Params& P, const T* in, int R, cplx<T>* out, T s
   int nb = (pairs + pp - 1) / pp;
   size_t sm = (size_t)pp * N * sizeof(cplx<T>);
   k_rfft_x<T><<<nb, 256, sm, s>>>(in, R, N, logN, P.Px, out, scale, Nyr, add0, add1, tw, pp);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -253,6 +248,7 @@ cudaError_t fft_x_inverse(const Params& P, const cplx<T>* in, int R, T* out, T s
   int nb = (pairs + pp - 1) / pp;
   size_t sm = (size_t)pp * N * sizeof(cplx<T>);
   k_irfft_x<T><<<nb, 256, sm, s>>>(in, R, N, logN, P.Px, out, scale, tw, pp);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -264,6 +260,7 @@ cudaError_t fft_z(const Params& P, cplx<T>* data, int Nyr, int nfields, size_t f
   ensure_fft_z_attr<T>();
   dim3 grid((P.Nxh + kTileZ - 1) / kTileZ, Nyr, nfields);
   k_fft_z<T><<<grid, 256, sm, s>>>(data, Nz, logNz, Nyr, P.Px, P.Nxh, inverse ? 1 : 0, tw, field_stride, 0);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -274,6 +271,7 @@ cudaError_t fft_z_mac(const Params& P, cplx<T>* data, bool inverse, const cplx<T
   ensure_fft_z_attr<T>();
   dim3 grid((P.Nxh + kTileZ - 1) / kTileZ, P.Ny + 1, 3);
   k_fft_z<T><<<grid, 256, sm, s>>>(data, Nz, logNz, P.Ny, P.Px, P.Nxh, inverse ? 1 : 0, tw, 0, 1);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -292,16 +290,11 @@ cudaError_t launch_poisson(const Params& P, Workspace& W, const T* rho, T* phi, 
   e = fft_z<T>(P, S, Ny, 1, 0, false, twz, s);
   if (e != cudaSuccess) return e;
   int singular = (P.bc[0] == DISCOS_BC_NEUMANN && P.bc[1] == DISCOS_BC_NEUMANN) ? 1 : 0;
-  int B = Ny > 128 ? 16 : 32;
-  dim3 grid((P.Nxh + B - 1) / B, Nz);
-  size_t sm = (size_t)B * Ny * sizeof(double2);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_poisson_y<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    cudaFuncSetAttribute(k_poisson_y<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    attr = true;
-  }
-  k_poisson_y<T><<<grid, B, sm, s>>>(S, W.inv_m, Ny, Nz, P.Nxh, P.Px, singular, 1.0 / ((double)Nx * Nz));
+  const int threads = 2 * P.Nxh * Nz;
+  const int nb = (threads + 127) / 128;
+  k_poisson_y<T><<<nb, 128, 0, s>>>(S, W.inv_m, Ny, Nz, P.Nxh, P.Px, singular, 1.0 / ((double)Nx * Nz),
+                                    W.ps_scratch);
+  count_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = fft_z<T>(P, S, Ny, 1, 0, true, twz, s);

@@ -159,6 +159,7 @@ cudaError_t launch_interp_efield(const Params& P, const T* x, const T* q, int N,
   int bs = 256;
   int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
   k_interp_efield<T><<<nb, bs, 0, s>>>(x, q, N, P, phi, out, as_force ? 1 : 0);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -168,6 +169,7 @@ cudaError_t launch_interp_velocity(const Params& P, const T* x, int N, const T* 
   int bs = 256;
   int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
   k_interp_velocity<T><<<nb, bs, 0, s>>>(x, N, P, v, out);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -4,9 +4,9 @@
 // wall (charge -q at a Dirichlet wall, +q at a Neumann wall, Sec. II.B.1); the
 // ion-ion LJ force of Eq. closerange; and the wall force of Sec. II.B.2.
 //
-// One thread per ion in cell order (neighbouring threads share cells, so the
+// One warp per ion in cell order (neighbouring warps share cells, so the
 // partner loads hit the same lines).  Each ion sums over its own partners
-// (full neighbour loop, no atomics, deterministic order).  Whether a pair is
+// (full neighbour loop, no atomics, fixed reduction order).  Whether a pair is
 // inside a cutoff is decided with one rounding per operation in the order
 // dx = x_i - x_j, minimum image by +-L, r2 = (dx^2 + dy^2) + dz^2, so the
 // neighbour counts are reproducible bit for bit.  Image partners of ion i
@@ -56,11 +56,49 @@ __device__ __forceinline__ T fp_lookup(const T* __restrict__ tab, int n_tab, T s
 }
 
 template <typename T>
+__device__ __forceinline__ void pair_terms(const T xi, const T yi, const T zi, const T qi, const int si,
+                                           const T xj, const T yj, const T zj, const T qj, const int sj,
+                                           bool real, const Params& P, const T* __restrict__ tab, T Lx, T hx,
+                                           T Lz, T hz, T psi2, T lB, T scale, T& fx, T& fy, T& fz, int& cnt) {
+  T ddx = min_image(sub_rn(xi, xj), Lx, hx);
+  T ddy = sub_rn(yi, yj);
+  T ddz = min_image(sub_rn(zi, zj), Lz, hz);
+  T r2 = add_rn(add_rn(mul_rn(ddx, ddx), mul_rn(ddy, ddy)), mul_rn(ddz, ddz));
+  bool in_psi = r2 < psi2;
+  bool in_lj = false;
+  T rcl = T(0);
+  if (real) {
+    rcl = T(P.lj_rc[si][sj]);
+    in_lj = r2 < mul_rn(rcl, rcl);
+  }
+  if (!(in_psi || in_lj)) return;
+  T r = sqrt(r2);
+  T coef = T(0);
+  if (in_psi) {
+    coef += lB * qi * qj * (T(1) / r2 - fp_lookup(tab, P.n_tab, scale, r));
+    ++cnt;
+  }
+  if (in_lj) {
+    T sg = T(P.lj_sigma[si][sj]);
+    T sr2 = sg * sg / r2;
+    T sr6 = sr2 * sr2 * sr2;
+    coef += T(24) * T(P.lj_xi[si][sj]) / r * (T(2) * sr6 * sr6 - sr6);
+  }
+  T cr = coef / r;
+  fx += cr * ddx; fy += cr * ddy; fz += cr * ddz;
+}
+
+// One warp per ion (cell order).  Lanes 0..26 take the 27 neighbour cells;
+// for an ion within psi of a wall, lanes 0..8 (bottom) and 9..17 (top) then
+// take the 9 wall-row cells around it for the image partners.  The partial
+// sums are reduced with a fixed shuffle tree (deterministic).
+template <typename T>
 __global__ void k_near_field(const T* __restrict__ xs, const T* __restrict__ qs, const int* __restrict__ sps,
                              const int* __restrict__ perm, const int* __restrict__ start, int N, Params P,
                              const T* __restrict__ tab, T* __restrict__ F, int* __restrict__ nbr) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= N) return;
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (s >= N) return;                       // whole warps exit together
   const T xi = xs[s], yi = xs[N + s], zi = xs[2 * N + s], qi = qs[s];
   const int si = sps[s];
   const int cx = cell_coord(xi, P.k_cell, P.ncx);
@@ -72,78 +110,52 @@ __global__ void k_near_field(const T* __restrict__ xs, const T* __restrict__ qs,
   const T lB = T(P.lB), scale = T(P.tab_scale);
   T fx = T(0), fy = T(0), fz = T(0);
   int cnt = 0;
-  for (int dz = -1; dz <= 1; ++dz) {
-    int czz = cz + dz;
-    czz = czz < 0 ? czz + P.ncz : (czz >= P.ncz ? czz - P.ncz : czz);
-    for (int dy = -1; dy <= 1; ++dy) {
-      int cyy = cy + dy;
-      if (cyy < 0 || cyy >= P.ncy) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        int cxx = cx + dx;
-        cxx = cxx < 0 ? cxx + P.ncx : (cxx >= P.ncx ? cxx - P.ncx : cxx);
-        int c = (czz * P.ncy + cyy) * P.ncx + cxx;
-        int b = start[c], e = start[c + 1];
-        for (int j = b; j < e; ++j) {
-          if (j == s) continue;
-          T ddx = min_image(sub_rn(xi, xs[j]), Lx, hx);
-          T ddy = sub_rn(yi, xs[N + j]);
-          T ddz = min_image(sub_rn(zi, xs[2 * N + j]), Lz, hz);
-          T r2 = add_rn(add_rn(mul_rn(ddx, ddx), mul_rn(ddy, ddy)), mul_rn(ddz, ddz));
-          const int sj = sps[j];
-          T rcl = T(P.lj_rc[si][sj]);
-          bool in_psi = r2 < psi2;
-          bool in_lj = r2 < mul_rn(rcl, rcl);
-          if (!(in_psi || in_lj)) continue;
-          T r = sqrt(r2);
-          T coef = T(0);
-          if (in_psi) {
-            coef += lB * qi * qs[j] * (T(1) / r2 - fp_lookup(tab, P.n_tab, scale, r));
-            ++cnt;
-          }
-          if (in_lj) {
-            T sg = T(P.lj_sigma[si][sj]);
-            T sr2 = sg * sg / r2;
-            T sr6 = sr2 * sr2 * sr2;
-            coef += T(24) * T(P.lj_xi[si][sj]) / r * (T(2) * sr6 * sr6 - sr6);
-          }
-          T cr = coef / r;
-          fx += cr * ddx; fy += cr * ddy; fz += cr * ddz;
-        }
-      }
-    }
-  }
-  // wall images: bottom (y -> -y) and top (y -> 2 Ny - y)
-  for (int wall = 0; wall < 2; ++wall) {
-    bool near = wall == 0 ? (yi < psi) : (sub_rn(T(P.Ny), yi) < psi);
-    if (!near) continue;
-    const T sgn = P.bc[wall] == DISCOS_BC_DIRICHLET ? T(-1) : T(1);
-    const int cyy = wall == 0 ? 0 : P.ncy - 1;
-    const T twoNy = T(2 * P.Ny);
-    for (int dz = -1; dz <= 1; ++dz) {
+  if (lane < 27) {
+    int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+    int cyy = cy + dy;
+    if (cyy >= 0 && cyy < P.ncy) {
       int czz = cz + dz;
       czz = czz < 0 ? czz + P.ncz : (czz >= P.ncz ? czz - P.ncz : czz);
-      for (int dx = -1; dx <= 1; ++dx) {
-        int cxx = cx + dx;
-        cxx = cxx < 0 ? cxx + P.ncx : (cxx >= P.ncx ? cxx - P.ncx : cxx);
-        int c = (czz * P.ncy + cyy) * P.ncx + cxx;
-        int b = start[c], e = start[c + 1];
-        for (int j = b; j < e; ++j) {
-          T yj = xs[N + j];
-          T yimg = wall == 0 ? -yj : sub_rn(twoNy, yj);
-          T ddx = min_image(sub_rn(xi, xs[j]), Lx, hx);
-          T ddy = sub_rn(yi, yimg);
-          T ddz = min_image(sub_rn(zi, xs[2 * N + j]), Lz, hz);
-          T r2 = add_rn(add_rn(mul_rn(ddx, ddx), mul_rn(ddy, ddy)), mul_rn(ddz, ddz));
-          if (!(r2 < psi2)) continue;
-          T r = sqrt(r2);
-          T coef = lB * qi * (sgn * qs[j]) * (T(1) / r2 - fp_lookup(tab, P.n_tab, scale, r));
-          ++cnt;
-          T cr = coef / r;
-          fx += cr * ddx; fy += cr * ddy; fz += cr * ddz;
-        }
+      int cxx = cx + dx;
+      cxx = cxx < 0 ? cxx + P.ncx : (cxx >= P.ncx ? cxx - P.ncx : cxx);
+      int c = (czz * P.ncy + cyy) * P.ncx + cxx;
+      int b = start[c], e = start[c + 1];
+      for (int j = b; j < e; ++j) {
+        if (j == s) continue;
+        pair_terms(xi, yi, zi, qi, si, xs[j], xs[N + j], xs[2 * N + j], qs[j], sps[j], true, P, tab, Lx, hx, Lz,
+                   hz, psi2, lB, scale, fx, fy, fz, cnt);
       }
     }
   }
+  // wall images: bottom (y -> -y) on lanes 0..8, top (y -> 2 Ny - y) on lanes 9..17
+  const bool near0 = yi < psi, near1 = sub_rn(T(P.Ny), yi) < psi;
+  if ((near0 && lane < 9) || (near1 && lane >= 9 && lane < 18)) {
+    const int wall = lane < 9 ? 0 : 1;
+    const int l9 = lane - 9 * wall;
+    int dx = l9 % 3 - 1, dz = l9 / 3 - 1;
+    int czz = cz + dz;
+    czz = czz < 0 ? czz + P.ncz : (czz >= P.ncz ? czz - P.ncz : czz);
+    int cxx = cx + dx;
+    cxx = cxx < 0 ? cxx + P.ncx : (cxx >= P.ncx ? cxx - P.ncx : cxx);
+    const int cyy = wall == 0 ? 0 : P.ncy - 1;
+    const T sgn = P.bc[wall] == DISCOS_BC_DIRICHLET ? T(-1) : T(1);
+    const T twoNy = T(2 * P.Ny);
+    int c = (czz * P.ncy + cyy) * P.ncx + cxx;
+    int b = start[c], e = start[c + 1];
+    for (int j = b; j < e; ++j) {
+      T yj = xs[N + j];
+      T yimg = wall == 0 ? -yj : sub_rn(twoNy, yj);
+      pair_terms(xi, yi, zi, qi, si, xs[j], yimg, xs[2 * N + j], sgn * qs[j], 0, false, P, tab, Lx, hx, Lz, hz,
+                 psi2, lB, scale, fx, fy, fz, cnt);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    fx += __shfl_xor_sync(0xffffffffu, fx, o);
+    fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  if (lane != 0) return;
   // short-range wall force (Sec. II.B.2): 12-6 repulsion or the 9-3 form of Eq. LJ93
   {
     const T rc = T(P.wall_rc[si]), sg = T(P.wall_sigma[si]), xiw = T(P.wall_xi[si]);
@@ -183,8 +195,10 @@ cudaError_t launch_near_field(const Params& P, Workspace& W, const T* x, const T
   int bs = 256;
   int nb = (N + bs - 1) / bs;
   k_gather<T><<<nb, bs, 0, s>>>(x, q, species, N, W.perm, xs, qs, W.sps);
-  k_near_field<T><<<(N + 127) / 128, 128, 0, s>>>(xs, qs, W.sps, W.perm, W.cell_start, N, P,
+  count_launches(1);
+  k_near_field<T><<<(N + 7) / 8, 256, 0, s>>>(xs, qs, W.sps, W.perm, W.cell_start, N, P,
                                                   reinterpret_cast<const T*>(W.fptab), F, nbr);
+  count_launches(1);
   return cudaGetLastError();
 }
 

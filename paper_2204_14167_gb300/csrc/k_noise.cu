@@ -80,6 +80,7 @@ cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_
   dim3 grid((P.Nx + TX - 1) / TX, (P.Ny + TY - 1) / TY, (P.Nz + TZ - 1) / TZ);
   T amp = T(sqrt(2.0 * P.kT * P.eta / P.dt));
   k_stress_noise<T><<<grid, 256, 0, s>>>(f, P, (long long)step, amp);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -140,6 +140,7 @@ cudaError_t launch_fill_zero(T* p, size_t n, cudaStream_t s) {
   size_t nb = (n + bs - 1) / bs;
   if (nb > 152 * 16) nb = 152 * 16;
   k_fill<T><<<(unsigned)nb, bs, 0, s>>>(p, n);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -150,6 +151,7 @@ cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N,
   int bs = 256;
   int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
   k_spread_charge<T><<<nb, bs, 0, s>>>(x, q, N, P, rho);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -162,6 +164,7 @@ cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, 
   int bs = 256;
   dim3 grid((unsigned)(((size_t)N * 8 + bs - 1) / bs), 3);
   k_spread_force<T><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -12,8 +12,8 @@
 //   eta A_c u = f_x + conj(g_x) p,   eta A_c w = f_z + conj(g_z) p.
 // The K = 0 mode has v = 0, eta A_c u = f_x, eta A_c w = f_z, and p from
 // p_j - p_{j-1} = f_y,j with zero mean.  All banded solves are in double
-// precision (LDL^T for the pentadiagonal, Thomas for the tridiagonals), one
-// thread per mode, work arrays in shared memory laid out [row][thread].
+// precision (LDL^T for the pentadiagonal, Thomas for the tridiagonals) with
+// the factors of every mode computed once when the handle is created.
 #include "internal.h"
 
 namespace discos {
@@ -32,167 +32,146 @@ cudaError_t fft_z_mac(const Params& P, cplx<T>* data, bool inverse, const cplx<T
 
 namespace {
 
-__device__ __forceinline__ double2 cd(double a, double b) { return make_double2(a, b); }
-
+// One thread per (mode, part): lanes 2m and 2m+1 hold the real and the
+// imaginary part of mode m (all band matrices are real, so the two parts
+// are independent except where conj(g) p mixes them: there the partner's
+// value comes by shuffle).  Factors are pre-computed per mode in double:
+//   PL1, PL2, PDI [Ny-1][M]: L D L^T of the pentadiagonal (l1, l2, 1/D),
+//   CI [Ny][M]: reciprocal Thomas pivots of A_c,
+//   MC [M][5]: (g_x re, g_x im, g_z re, g_z im, -1/K^2; 0 for K = 0).
+// Scratch SG, SY [Ny][threads] (double, one private slot per thread): g then
+// u-forward values; y then v then w-forward values.
 template <typename T>
-__global__ void k_stokes_y(cplx<T>* __restrict__ S, cplx<T>* __restrict__ Sp, Params P) {
-  extern __shared__ unsigned char smem_raw[];
-  const int B = blockDim.x, t = threadIdx.x;
-  const int Ny = P.Ny, Nz = P.Nz, Px = P.Px;
-  double2* G = reinterpret_cast<double2*>(smem_raw);       // [Ny][B]
-  double2* R = G + (size_t)Ny * B;                         // [Ny][B]
-  double* L1 = reinterpret_cast<double*>(R + (size_t)Ny * B);  // [Ny][B]
-  double* L2 = L1 + (size_t)Ny * B;
-  double* DI = L2 + (size_t)Ny * B;
-#define AT(arr, j) arr[(size_t)(j) * B + t]
-  const int kx = blockIdx.x * B + t;
-  const int kz = blockIdx.y;
-  if (kx >= P.Nxh) return;
-  const double eta = P.eta;
+__global__ void k_stokes_y(cplx<T>* __restrict__ S, cplx<T>* __restrict__ Sp, Params P,
+                           const double* __restrict__ PL1, const double* __restrict__ PL2,
+                           const double* __restrict__ PDI, const double* __restrict__ CI,
+                           const double* __restrict__ MC, double* __restrict__ SG, double* __restrict__ SY) {
+  const int Ny = P.Ny, Nz = P.Nz, Px = P.Px, Nxh = P.Nxh;
+  const int M = Nxh * Nz;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int mode_raw = tid >> 1;
+  const int part = tid & 1;
+  const bool active = mode_raw < M;
+  const int mode = active ? mode_raw : M - 1;      // idle lanes shadow the last mode, write nothing
+  const int kz = mode / Nxh, kx = mode - kz * Nxh;
+  const size_t M2 = (size_t)gridDim.x * blockDim.x;   // scratch row stride: one slot per thread
+  const size_t me = (size_t)tid;
+  const double eta = P.eta, ieta = 1.0 / P.eta;
   const double norm = 1.0 / ((double)P.Nx * P.Nz);
-  cplx<T>* Su = S;
-  cplx<T>* Sv = S + (size_t)Nz * Ny * Px;
-  cplx<T>* Sw = S + (size_t)Nz * (2 * Ny + 1) * Px;
-  const size_t cu = (size_t)kz * Ny * Px + kx;          // column in u / w / p spectra
-  const size_t cv = (size_t)kz * (Ny + 1) * Px + kx;    // column in the v spectrum
-  double sx, cxv, sz, czv;
-  sincospi(2.0 * kx / P.Nx, &sx, &cxv);
-  sincospi(2.0 * kz / P.Nz, &sz, &czv);
-  const double2 gx = cd(cxv - 1.0, sx), gz = cd(czv - 1.0, sz);
-  const double K2 = (2.0 - 2.0 * cxv) + (2.0 - 2.0 * czv);
-  auto ld = [&](const cplx<T>* a, size_t i) { cplx<T> v = a[i]; return cd((double)v.re, (double)v.im); };
-  auto st = [&](cplx<T>* a, size_t i, double2 v) { a[i] = cplx<T>{T(v.x * norm), T(v.y * norm)}; };
+  const double gxr = MC[5 * (size_t)mode + 0], gxi = MC[5 * (size_t)mode + 1];
+  const double gzr = MC[5 * (size_t)mode + 2], gzi = MC[5 * (size_t)mode + 3];
+  const double mik2 = MC[5 * (size_t)mode + 4];   // -1/K^2
+  const double K2 = mik2 != 0.0 ? -1.0 / mik2 : 0.0;
+  T* Su = reinterpret_cast<T*>(S);
+  T* Sv = reinterpret_cast<T*>(S + (size_t)Nz * Ny * Px);
+  T* Sw = reinterpret_cast<T*>(S + (size_t)Nz * (2 * Ny + 1) * Px);
+  const size_t cu = (size_t)kz * Ny * Px + kx;
+  const size_t cv = (size_t)kz * (Ny + 1) * Px + kx;
+  auto cpx = [&](const T* a, size_t e) { return make_double2((double)a[2 * e], (double)a[2 * e + 1]); };
 
-  // Thomas pivots of A_c (diag K^2 + 2, +1 on the two wall rows; off-diagonals -1)
-  auto ac_diag = [&](int j) { return K2 + 2.0 + (j == 0 ? 1.0 : 0.0) + (j == Ny - 1 ? 1.0 : 0.0); };
-  auto tridiag_ac = [&](const cplx<T>* f, double2 gc, bool with_p, cplx<T>* out) {
-    // eta A_c x = f + conj(gc) p ;  p in G
-    double2 prev = cd(0, 0);
-    for (int j = 0; j < Ny; ++j) {
-      double2 b = ld(f, cu + (size_t)j * Px);
-      if (with_p) {
-        double2 p = AT(G, j);
-        b.x += gc.x * p.x + gc.y * p.y;   // conj(gc) * p
-        b.y += gc.x * p.y - gc.y * p.x;
-      }
-      b.x /= eta; b.y /= eta;
-      double im = AT(L1, j);
-      prev.x = (b.x + prev.x) * im;
-      prev.y = (b.y + prev.y) * im;
-      AT(R, j) = prev;
-    }
-    double2 xn = prev;
-    st(out, cu + (size_t)(Ny - 1) * Px, xn);
-    for (int j = Ny - 2; j >= 0; --j) {
-      double im = AT(L1, j);
-      double2 v = AT(R, j);
-      xn.x = v.x + im * xn.x;
-      xn.y = v.y + im * xn.y;
-      st(out, cu + (size_t)j * Px, xn);
-    }
-  };
-  {
-    double m = ac_diag(0);
-    AT(L1, 0) = 1.0 / m;
-    for (int j = 1; j < Ny; ++j) {
-      m = ac_diag(j) - 1.0 / m;
-      AT(L1, j) = 1.0 / m;
-    }
-  }
-
-  if (kx == 0 && kz == 0) {
-    // K = 0: pressure from p_j - p_{j-1} = f_y,j (zero mean), v = 0
-    double2 p = cd(0, 0), sum = cd(0, 0);
-    AT(G, 0) = p;
-    for (int j = 1; j < Ny; ++j) {
-      double2 fy = ld(Sv, cv + (size_t)j * Px);
-      p.x += fy.x; p.y += fy.y;
-      AT(G, j) = p;
-      sum.x += p.x; sum.y += p.y;
-    }
-    sum.x /= Ny; sum.y /= Ny;
-    for (int j = 0; j < Ny; ++j) { AT(G, j).x -= sum.x; AT(G, j).y -= sum.y; }
-    tridiag_ac(Su, gx, false, Su);
-    tridiag_ac(Sw, gz, false, Sw);
-    for (int j = 0; j <= Ny; ++j) Sv[cv + (size_t)j * Px] = cplx<T>{T(0), T(0)};
-    if (Sp)
-      for (int j = 0; j < Ny; ++j) st(Sp, cu + (size_t)j * Px, AT(G, j));
-    return;
-  }
-
-  // g = g_x f_x + g_z f_z on cell rows
+  // pass A: g_j (this part) and the forward sweep of the pentadiagonal
+  double gprev = 0.0, y1 = 0.0, y2 = 0.0;
   for (int j = 0; j < Ny; ++j) {
-    double2 fx = ld(Su, cu + (size_t)j * Px), fz = ld(Sw, cu + (size_t)j * Px);
-    AT(G, j) = cd(gx.x * fx.x - gx.y * fx.y + gz.x * fz.x - gz.y * fz.y,
-                  gx.x * fx.y + gx.y * fx.x + gz.x * fz.y + gz.y * fz.x);
+    double2 fx = cpx(Su, cu + (size_t)j * Px), fz = cpx(Sw, cu + (size_t)j * Px);
+    double g = part == 0 ? (gxr * fx.x - gxi * fx.y + gzr * fz.x - gzi * fz.y)
+                         : (gxr * fx.y + gxi * fx.x + gzr * fz.y + gzi * fz.x);
+    SG[(size_t)j * M2 + me] = g;
+    if (j >= 1) {
+      const int i = j - 1;
+      double fy = (double)Sv[2 * (cv + (size_t)j * Px) + part];
+      double b = (K2 * fy + (g - gprev)) * ieta;
+      double y = b - PL1[(size_t)i * M + mode] * y1 - PL2[(size_t)i * M + mode] * y2;
+      SY[(size_t)i * M2 + me] = y;
+      y2 = y1; y1 = y;
+    }
+    gprev = g;
   }
-  // pentadiagonal P = K^2 A_f + D_y^T A_c D_y on faces 1..Ny-1 (unknown i = face - 1):
-  // diag K^4 + 4K^2 + 6 (+1 on the first and last rows), off-1 -2K^2 - 4, off-2 +1
-  const int n = Ny - 1;
-  const double dbase = K2 * K2 + 4.0 * K2 + 6.0, e = -2.0 * K2 - 4.0, fo = 1.0;
-  double Dm1 = 0.0, Dm2 = 0.0, l1m1 = 0.0;   // D_{i-1}, D_{i-2}, l1_{i-1}
-  double2 ym1 = cd(0, 0), ym2 = cd(0, 0);
-  for (int i = 0; i < n; ++i) {
-    const int face = i + 1;
-    double2 fy = ld(Sv, cv + (size_t)face * Px);
-    double2 g1 = AT(G, face), g0 = AT(G, face - 1);
-    // rhs = (K^2 f_y + (g_f - g_{f-1})) / eta
-    double2 b = cd((K2 * fy.x + (g1.x - g0.x)) / eta, (K2 * fy.y + (g1.y - g0.y)) / eta);
-    double l2 = i >= 2 ? fo / Dm2 : 0.0;
-    double l1 = i >= 1 ? (e - (i >= 2 ? l2 * l1m1 * Dm2 : 0.0)) / Dm1 : 0.0;
-    double d = dbase + (i == 0 ? 1.0 : 0.0) + (i == n - 1 ? 1.0 : 0.0);
-    double D = d - l1 * l1 * Dm1 - l2 * l2 * Dm2;
-    double2 y = cd(b.x - l1 * ym1.x - l2 * ym2.x, b.y - l1 * ym1.y - l2 * ym2.y);
-    AT(L1, i) = l1;  // reused below only after the A_c pivots are rebuilt
-    AT(L2, i) = l2;
-    AT(DI, i) = 1.0 / D;
-    AT(R, i) = y;
-    ym2 = ym1; ym1 = y;
-    Dm2 = Dm1; Dm1 = D; l1m1 = l1;
-  }
-  // back substitution: x_i = y_i / D_i - l1_{i+1} x_{i+1} - l2_{i+2} x_{i+2}
+  // pass B: back substitution -> v on faces 1..Ny-1 (SY[i] = v at face i+1)
   {
-    double2 x1 = cd(0, 0), x2 = cd(0, 0);
-    for (int i = n - 1; i >= 0; --i) {
-      double2 y = AT(R, i);
-      double di = AT(DI, i);
-      double a1 = i + 1 < n ? AT(L1, i + 1) : 0.0;
-      double a2 = i + 2 < n ? AT(L2, i + 2) : 0.0;
-      double2 xi = cd(y.x * di - a1 * x1.x - a2 * x2.x, y.y * di - a1 * x1.y - a2 * x2.y);
-      AT(R, i) = xi;
+    double x1 = 0.0, x2 = 0.0;
+    for (int i = Ny - 2; i >= 0; --i) {
+      double a1 = i + 1 < Ny - 1 ? PL1[(size_t)(i + 1) * M + mode] : 0.0;
+      double a2 = i + 2 < Ny - 1 ? PL2[(size_t)(i + 2) * M + mode] : 0.0;
+      double xi = SY[(size_t)i * M2 + me] * PDI[(size_t)i * M + mode] - a1 * x1 - a2 * x2;
+      SY[(size_t)i * M2 + me] = xi;
+      if (active) Sv[2 * (cv + (size_t)(i + 1) * Px) + part] = T(xi * norm);
       x2 = x1; x1 = xi;
     }
-  }
-  // v on the faces (walls zero)
-  Sv[cv] = cplx<T>{T(0), T(0)};
-  Sv[cv + (size_t)Ny * Px] = cplx<T>{T(0), T(0)};
-  for (int f = 1; f < Ny; ++f) st(Sv, cv + (size_t)f * Px, AT(R, f - 1));
-  // p_j = -(g_j + eta (A_c D_y v)_j) / K^2,  (D_y v)_j = v_{j+1} - v_j
-  auto vface = [&](int f) { return (f >= 1 && f <= Ny - 1) ? AT(R, f - 1) : cd(0, 0); };
-  auto dyv = [&](int j) { double2 a = vface(j + 1), b = vface(j); return cd(a.x - b.x, a.y - b.y); };
-  for (int j = 0; j < Ny; ++j) {
-    double a = ac_diag(j);
-    double2 c = dyv(j);
-    double2 acd = cd(a * c.x, a * c.y);
-    if (j >= 1) { double2 m = dyv(j - 1); acd.x -= m.x; acd.y -= m.y; }
-    if (j <= Ny - 2) { double2 m = dyv(j + 1); acd.x -= m.x; acd.y -= m.y; }
-    double2 g = AT(G, j);
-    AT(G, j) = cd(-(g.x + eta * acd.x) / K2, -(g.y + eta * acd.y) / K2);
-  }
-  // rebuild the A_c pivots (L1 was used by the pentadiagonal factors)
-  {
-    double m = ac_diag(0);
-    AT(L1, 0) = 1.0 / m;
-    for (int j = 1; j < Ny; ++j) {
-      m = ac_diag(j) - 1.0 / m;
-      AT(L1, j) = 1.0 / m;
+    if (active) {
+      Sv[2 * cv + part] = T(0);
+      Sv[2 * (cv + (size_t)Ny * Px) + part] = T(0);
     }
   }
-  tridiag_ac(Su, gx, true, Su);
-  tridiag_ac(Sw, gz, true, Sw);
-  if (Sp)
-    for (int j = 0; j < Ny; ++j) st(Sp, cu + (size_t)j * Px, AT(G, j));
-#undef AT
+  // pass C: p_j = -(g_j + eta (A_c D_y v)_j) / K^2 and the forward sweeps of
+  // eta A_c u = f_x + conj(g_x) p, eta A_c w = f_z + conj(g_z) p
+  {
+    auto vf = [&](int f) { return (f >= 1 && f <= Ny - 1) ? SY[(size_t)(f - 1) * M2 + me] : 0.0; };
+    double vm1 = 0.0, v0 = 0.0, v1 = vf(1), v2 = vf(2);   // faces j-1, j, j+1, j+2 at j = 0
+    double yu = 0.0, yw = 0.0;
+    for (int j = 0; j < Ny; ++j) {
+      double em = v0 - vm1, e0 = v1 - v0, ep = v2 - v1;
+      double a = K2 + 2.0 + (j == 0 ? 1.0 : 0.0) + (j == Ny - 1 ? 1.0 : 0.0);
+      double acd = a * e0 - (j >= 1 ? em : 0.0) - (j <= Ny - 2 ? ep : 0.0);
+      double g = SG[(size_t)j * M2 + me];
+      double p = (g + eta * acd) * mik2;
+      double pq = __shfl_xor_sync(0xffffffffu, p, 1);      // partner part of p
+      double pre = part == 0 ? p : pq, pim = part == 0 ? pq : p;
+      double2 fx = cpx(Su, cu + (size_t)j * Px), fz = cpx(Sw, cu + (size_t)j * Px);
+      // conj(g) p = (gr pr + gi pi) + i (gr pi - gi pr)
+      double bu = part == 0 ? fx.x + (gxr * pre + gxi * pim) : fx.y + (gxr * pim - gxi * pre);
+      double bw = part == 0 ? fz.x + (gzr * pre + gzi * pim) : fz.y + (gzr * pim - gzi * pre);
+      double ci = CI[(size_t)j * M + mode];
+      yu = (bu * ieta + yu) * ci;
+      yw = (bw * ieta + yw) * ci;
+      if (Sp && active) reinterpret_cast<T*>(Sp)[2 * (cu + (size_t)j * Px) + part] = T(p * norm);
+      SG[(size_t)j * M2 + me] = yu;
+      // slide the v window before SY[j] (= v at face j+1, already held) is reused
+      vm1 = v0; v0 = v1; v1 = v2; v2 = vf(j + 3);
+      SY[(size_t)j * M2 + me] = yw;
+    }
+  }
+  // pass D: back substitution of the two tridiagonal systems
+  {
+    double xu = 0.0, xw = 0.0;
+    for (int j = Ny - 1; j >= 0; --j) {
+      double ci = CI[(size_t)j * M + mode];
+      xu = SG[(size_t)j * M2 + me] + (j < Ny - 1 ? ci * xu : 0.0);
+      xw = SY[(size_t)j * M2 + me] + (j < Ny - 1 ? ci * xw : 0.0);
+      if (active) {
+        Su[2 * (cu + (size_t)j * Px) + part] = T(xu * norm);
+        Sw[2 * (cu + (size_t)j * Px) + part] = T(xw * norm);
+      }
+    }
+  }
+}
+
+// The pressure of the K = 0 mode (kx = kz = 0) from the saved f_y column.
+template <typename T>
+__global__ void k_stokes_p0(cplx<T>* __restrict__ Sp, const double* __restrict__ fy0, Params P) {
+  const int part = threadIdx.x;
+  if (part > 1) return;
+  const int Ny = P.Ny;
+  const double norm = 1.0 / ((double)P.Nx * P.Nz);
+  double p = 0.0, sum = 0.0;
+  for (int j = 1; j < Ny; ++j) { p += fy0[2 * j + part]; sum += p; }
+  double mean = sum / Ny;
+  p = 0.0;
+  T* sp = reinterpret_cast<T*>(Sp);
+  sp[part] = T((0.0 - mean) * norm);
+  for (int j = 1; j < Ny; ++j) {
+    p += fy0[2 * j + part];
+    sp[2 * ((size_t)j * P.Px) + part] = T((p - mean) * norm);
+  }
+}
+
+template <typename T>
+__global__ void k_save_fy0(const cplx<T>* __restrict__ S, double* __restrict__ fy0, Params P) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > P.Ny) return;
+  const cplx<T>* Sv = S + (size_t)P.Nz * P.Ny * P.Px;
+  cplx<T> v = Sv[(size_t)j * P.Px];
+  fy0[2 * j] = (double)v.re;
+  fy0[2 * j + 1] = (double)v.im;
 }
 
 }  // namespace
@@ -206,23 +185,26 @@ cudaError_t launch_stokes(const Params& P, Workspace& W, const T* f, T* v, T* p,
   const cplx<T>* twx = reinterpret_cast<const cplx<T>*>(W.tw_x);
   const cplx<T>* twz = reinterpret_cast<const cplx<T>*>(W.tw_z);
   const int R = Nz * (3 * Ny + 1);
+  const size_t M = (size_t)P.Nxh * Nz;
   cudaError_t e = fft_x_forward<T>(P, f, R, S, T(1), 1 << 30, T(0), T(0), twx, s);
   if (e != cudaSuccess) return e;
   e = fft_z_mac<T>(P, S, false, twz, s);
   if (e != cudaSuccess) return e;
-  int B = 32;
-  while (B > 1 && (size_t)B * Ny * 56 > 150 * 1024) B >>= 1;
-  size_t sm = (size_t)B * Ny * 56;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_stokes_y<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    cudaFuncSetAttribute(k_stokes_y<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    attr = true;
+  const size_t S2 = (2 * M + 127) / 128 * 128;               // threads launched = scratch row stride
+  double* fy0 = W.st_scratch + 2 * (size_t)Ny * S2;         // K = 0 column of f_y, 2 (Ny + 1) doubles
+  if (p) {
+    k_save_fy0<T><<<(Ny + 1 + 127) / 128, 128, 0, s>>>(S, fy0, P);
+    count_launches(1);
   }
-  dim3 grid((P.Nxh + B - 1) / B, Nz);
-  k_stokes_y<T><<<grid, B, sm, s>>>(S, Sp, P);
+  k_stokes_y<T><<<(unsigned)(S2 / 128), 128, 0, s>>>(S, Sp, P, W.st_l1, W.st_l2, W.st_di, W.st_ci, W.st_mc,
+                                                     W.st_scratch, W.st_scratch + (size_t)Ny * S2);
+  count_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (p) {
+    k_stokes_p0<T><<<1, 32, 0, s>>>(Sp, fy0, P);
+    count_launches(1);
+  }
   e = fft_z_mac<T>(P, S, true, twz, s);
   if (e != cudaSuccess) return e;
   e = fft_x_inverse<T>(P, S, R, v, T(1), twx, s);

@@ -77,6 +77,7 @@ cudaError_t launch_dry_update(const Params& P, T* x, const int* species, const T
                               int64_t step, cudaStream_t s) {
   if (N <= 0) return cudaSuccess;
   k_dry_update<T><<<(N + 127) / 128, 128, 0, s>>>(x, species, F, V, N, P, (long long)step);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -84,6 +85,7 @@ template <typename T>
 cudaError_t launch_midpoint(const Params& P, const T* x, const T* V, int N, T* xstar, cudaStream_t s) {
   if (N <= 0) return cudaSuccess;
   k_midpoint<T><<<(3 * N + 255) / 256, 256, 0, s>>>(x, V, N, T(0.5 * P.dt), xstar);
+  count_launches(1);
   return cudaGetLastError();
 }
 

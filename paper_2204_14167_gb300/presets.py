@@ -35,14 +35,16 @@ def dry_channel_32(precision=FP64):
 def wet_channel_128x64x128(precision=MIXED):
     """128 x 64 x 128 channel with dielectric (Neumann) walls, 10k + 10k ions,
     Debye length ~4 cells (l_B = 0.261), E_x = 0.05, fluctuating Stokes with
-    no-slip walls, 50% wet (4-point kernel, a_w = 0.91, a_t = a_w / 2)."""
+    no-slip walls, 50% wet (4-point kernel, a_w = 0.91, a_t = a_w / 2).
+    dt = 0.001 keeps D_tot dt / a_t^2 ~ 0.01, the paper's ratio of time step
+    to diffusive time (Sec. III.C)."""
     Ny = 64
     eta = 1.0 / (6.0 * math.pi)
     D_wet = 1.0 / A_WET_PESKIN4            # kT / (6 pi eta a_w)
     D_tot = 2.0 * D_wet                    # a_t = a_w / 2
     gam = mobility.gamma_table(0.5 * A_WET_PESKIN4, A_WET_PESKIN4, float(Ny))
     cfg = RunConfig(Nx=128, Ny=Ny, Nz=128, bc=(BC_NEUMANN, BC_NEUMANN), kernel_es=KERNEL_PESKIN4,
-                    kernel_hy=KERNEL_PESKIN4, lB=0.261, eta=eta, kT=1.0, dt=0.01, psi=4.0, n_tab=64,
+                    kernel_hy=KERNEL_PESKIN4, lB=0.261, eta=eta, kT=1.0, dt=0.001, psi=4.0, n_tab=64,
                     D_tot=[D_tot], D_wet=[D_wet], gamma_coef=[gam], E_ext=(0.05, 0.0, 0.0), wet=True,
                     precision=precision, max_ions=20000, **_wca(1.0), **_wall())
     return cfg, dict(n_pos=10000, n_neg=10000, ymargin=1.0, min_sep=0.9, seed=20220430)

@@ -178,6 +178,7 @@ def test_stokes(prec):
     cfg, rec = _small_dry((0, 0), kernel=dg.KERNEL_PESKIN4)
     cfg.Nx, cfg.Ny, cfg.Nz = 16, 8, 16
     cfg.eta = 0.7
+    cfg.wet = True
     cfg.precision = prec
     rng = np.random.default_rng(14)
     Nx, Ny, Nz = cfg.dims
