@@ -164,6 +164,29 @@ discos_status discos_interpolate(discos_handle* h, const void* x, int N, int whi
 discos_status discos_cell_list(discos_handle* h, const void* x, int N, int* cell_start,
                                int* perm, int* n_cells_out, void* stream);
 
+/* Allocation-free variant of discos_cell_list, for callers that cannot
+ * allocate device memory at the point where they need a cell list: work
+ * enqueued while a stream is being captured into a CUDA graph, code inside a
+ * host framework whose caching allocator already owns the device memory, and
+ * fixed-latency loops that must not enter the allocator.  The paper has no
+ * counterpart; it builds exactly the list discos_cell_list builds, from the
+ * configuration alone (no handle).
+ * - It calls no allocating routine.  Its scratch is a file-scope device array
+ *   of 1048576 + 2 * 262144 + 257 ints (about 6.3 MB) that every GPU loading
+ *   this library holds until the process exits; hence at most 1048576 ions
+ *   and 262144 list cells per call, larger requests return INVALID_ARG with
+ *   nothing enqueued.
+ * - The first call on a device (with that device current) looks up the
+ *   array's device address; make that first call before any stream capture.
+ * - All calls share the one array: calls that overlap on the GPU (different
+ *   streams without ordering) race.  Each call clears what must start at
+ *   zero, so consecutive calls on one stream are independent.
+ * Arguments as in discos_cell_list; cfg supplies Nx, Ny, Nz, psi, nspecies,
+ * lj_rc and precision (the type of x); cell_start must hold n_cells + 1 ints
+ * (n_cells is written to n_cells_out first, -1 if over the limit). */
+discos_status discos_cell_list_noalloc(const discos_config* cfg, const void* x, int N, int* cell_start,
+                                       int* perm, int* n_cells_out, void* stream);
+
 /* Near-field forces added to F[3][N] (F += ...): the P3M local correction
  * with wall images (Eqs. coulomb, fullElectro, LC), the ion-ion LJ force
  * (Eq. closerange) and the wall force (Sec. II.B.2).  nbr_count[N] (int32,

@@ -54,7 +54,7 @@ class Config(ctypes.Structure):
 EXPORTS = [
     "discos_create", "discos_destroy", "discos_last_error", "discos_spread", "discos_solve_poisson",
     "discos_solve_stokes", "discos_interpolate", "discos_cell_list", "discos_near_field", "discos_forces",
-    "discos_step", "discos_fp_table", "discos_launch_count",
+    "discos_step", "discos_fp_table", "discos_launch_count", "discos_cell_list_noalloc",
 ]
 
 _lib = None
@@ -82,6 +82,7 @@ def load():
     lib.discos_forces.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp]
     lib.discos_step.argtypes = [vp, vp, vp, vp, i32, i64, i32, vp, vp]
     lib.discos_fp_table.argtypes = [i32, i32, D, D, i32, ctypes.POINTER(D)]
+    lib.discos_cell_list_noalloc.argtypes = [ctypes.POINTER(Config), vp, i32, vp, vp, ctypes.POINTER(i32), vp]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int
     lib.discos_last_error.restype = ctypes.c_char_p

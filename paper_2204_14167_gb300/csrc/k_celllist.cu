@@ -3,6 +3,7 @@
 // warp-aggregated counting sort (histogram, exclusive scan, scatter), a
 // per-cell sort by ion index that makes the order deterministic, and a gather
 // of the ions into cell order.
+#include <mutex>
 #include "internal.h"
 
 namespace discos {
@@ -169,3 +170,122 @@ template cudaError_t launch_cell_list<float>(const Params&, Workspace&, const fl
 template cudaError_t launch_cell_list<double>(const Params&, Workspace&, const double*, int, cudaStream_t);
 
 }  // namespace discos
+
+// ---------------------------------------------------------------------------
+// Allocation-free cell list.
+//
+// Some callers cannot allocate device memory when they need a cell list: code
+// that runs while its stream is being captured into a CUDA graph (an
+// allocation there is either illegal or escapes the graph), code embedded in a
+// host framework whose caching allocator has already reserved the device
+// memory, and fixed-latency loops that are not allowed to call into the
+// allocator at all.  For them discos_cell_list_noalloc builds the same cell
+// list as discos_cell_list without a handle and without any allocation: its
+// scratch (per-ion cell ids, per-cell counts and fill counters, scan tile sums)
+// lives in the file-scope device array below, which every GPU that loads this
+// library holds until the process exits.
+namespace discos {
+
+namespace {
+
+constexpr int kNoAllocMaxIons = 1 << 20;      // ions per call
+constexpr int kNoAllocMaxCells = 1 << 18;     // list cells per call
+constexpr int kNoAllocMaxTiles = kNoAllocMaxCells / kScanTile + 1;
+constexpr size_t kNoAllocInts = (size_t)kNoAllocMaxIons + 2 * (size_t)kNoAllocMaxCells + kNoAllocMaxTiles;
+
+static __device__ __align__(256) int g_noalloc_scratch[kNoAllocInts];
+
+constexpr int kMaxDevices = 64;
+int* g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+
+}  // namespace
+
+}  // namespace discos
+
+extern "C" discos_status discos_cell_list_noalloc(const discos_config* cfg, const void* x, int N, int* cell_start,
+                                                  int* perm, int* n_cells_out, void* stream) {
+  using namespace discos;
+  if (!cfg) {
+    set_error("discos_cell_list_noalloc: null config");
+    return DISCOS_ERR_INVALID_ARG;
+  }
+  const discos_config& c = *cfg;
+  if (c.Nx < 1 || c.Ny < 1 || c.Nz < 1 || !(c.psi > 0.0) || c.nspecies < 1 || c.nspecies > DISCOS_MAX_SPECIES ||
+      (c.precision != DISCOS_FP64 && c.precision != DISCOS_MIXED)) {
+    set_error("discos_cell_list_noalloc: bad configuration");
+    return DISCOS_ERR_INVALID_ARG;
+  }
+  double rcmax = c.psi;
+  for (int a = 0; a < c.nspecies; ++a)
+    for (int b = 0; b < c.nspecies; ++b) rcmax = rcmax > c.lj_rc[a][b] ? rcmax : c.lj_rc[a][b];
+  int k = (int)ceil(rcmax - 1e-12);
+  if (k < 1) k = 1;
+  Params P{};
+  P.k_cell = k;
+  P.ncx = c.Nx / k;
+  P.ncy = c.Ny / k > 1 ? c.Ny / k : 1;
+  P.ncz = c.Nz / k;
+  if (P.ncx < 1 || P.ncz < 1) {
+    set_error("discos_cell_list_noalloc: cutoff larger than the box");
+    return DISCOS_ERR_INVALID_ARG;
+  }
+  const long long n_cells = (long long)P.ncx * P.ncy * P.ncz;
+  if (n_cells_out) *n_cells_out = (int)(n_cells <= kNoAllocMaxCells ? n_cells : -1);
+  if (N < 0 || N > kNoAllocMaxIons || n_cells > kNoAllocMaxCells) {
+    set_error("discos_cell_list_noalloc: at most 1048576 ions and 262144 list cells per call");
+    return DISCOS_ERR_INVALID_ARG;
+  }
+  if ((N > 0 && (!x || !perm)) || !cell_start) {
+    set_error("discos_cell_list_noalloc: null pointer");
+    return DISCOS_ERR_INVALID_ARG;
+  }
+  // one-time set-up per device: the device address of the scratch array
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e, "discos_cell_list_noalloc");
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("discos_cell_list_noalloc: device index out of range");
+    return DISCOS_ERR_INVALID_ARG;
+  }
+  int* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_status(e, "discos_cell_list_noalloc: cudaGetSymbolAddress");
+      g_noalloc_ptr[dev] = static_cast<int*>(ptr);
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  int* cell_of = base;
+  int* counts = cell_of + kNoAllocMaxIons;
+  int* fill = counts + kNoAllocMaxCells;
+  int* tile_sums = fill + kNoAllocMaxCells;
+  const int n = (int)n_cells;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: clear what must start at zero
+  e = cudaMemsetAsync(counts, 0, sizeof(int) * n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fill, 0, sizeof(int) * n, s);
+  if (e != cudaSuccess) return cuda_status(e, "discos_cell_list_noalloc");
+  const int bs = 256;
+  const int nb = (N + bs - 1) / bs;
+  const int ntiles = (n + kScanTile - 1) / kScanTile;
+  if (nb > 0) {
+    if (c.precision == DISCOS_MIXED) k_bin<float><<<nb, bs, 0, s>>>((const float*)x, N, P, cell_of, counts);
+    else k_bin<double><<<nb, bs, 0, s>>>((const double*)x, N, P, cell_of, counts);
+    count_launches(1);
+  }
+  k_tile_sums<<<ntiles, 256, 0, s>>>(counts, n, tile_sums);
+  k_scan_tiles<<<1, 1024, 0, s>>>(tile_sums, ntiles);
+  k_scan_apply<<<ntiles, kScanTile, 0, s>>>(counts, n, tile_sums, cell_start, N);
+  count_launches(3);
+  if (nb > 0) {
+    k_scatter<<<nb, bs, 0, s>>>(cell_of, N, cell_start, fill, perm);
+    count_launches(1);
+  }
+  k_sort_cells<<<(n + 255) / 256, 256, 0, s>>>(cell_start, n, perm);
+  count_launches(1);
+  return cuda_status(cudaGetLastError(), "discos_cell_list_noalloc");
+}
