@@ -113,8 +113,9 @@ void upload_stokes_factors(discos_handle* h) {
   const discos_config& c = h->cfg;
   const int Ny = c.Ny, Nxh = h->P.Nxh, Nz = c.Nz;
   const size_t M = (size_t)Nxh * Nz;
-  const int n = Ny - 1;
-  std::vector<double> l1((size_t)n * M), l2((size_t)n * M), di((size_t)n * M), ci((size_t)Ny * M), mc(5 * M);
+  const int n = Ny - 1;   // unknowns: faces f = 1..Ny-1, index i = f - 1
+  std::vector<double> l1((size_t)Ny * M, 0.0), l2((size_t)Ny * M, 0.0), di((size_t)Ny * M, 0.0);
+  std::vector<double> ci((size_t)Ny * M), mc(5 * M);
   for (int kz = 0; kz < Nz; ++kz)
     for (int kx = 0; kx < Nxh; ++kx) {
       const size_t m = (size_t)kz * Nxh + kx;
@@ -133,16 +134,16 @@ void upload_stokes_factors(discos_handle* h) {
         double a1 = i >= 1 ? (e - (i >= 2 ? a2 * l1m1 * Dm2 : 0.0)) / Dm1 : 0.0;
         double d = K2 * K2 + 4.0 * K2 + 6.0 + (i == 0 ? 1.0 : 0.0) + (i == n - 1 ? 1.0 : 0.0);
         double D = d - a1 * a1 * Dm1 - a2 * a2 * Dm2;
-        l1[(size_t)i * M + m] = zero ? 0.0 : a1;
-        l2[(size_t)i * M + m] = zero ? 0.0 : a2;
-        di[(size_t)i * M + m] = zero ? 0.0 : 1.0 / D;
+        l1[m * Ny + i + 1] = zero ? 0.0 : a1;
+        l2[m * Ny + i + 1] = zero ? 0.0 : a2;
+        di[m * Ny + i + 1] = zero ? 0.0 : 1.0 / D;
         Dm2 = Dm1; Dm1 = D; l1m1 = a1;
       }
       double mm = 0.0;
       for (int j = 0; j < Ny; ++j) {
         double a = K2 + 2.0 + (j == 0 ? 1.0 : 0.0) + (j == Ny - 1 ? 1.0 : 0.0);
         mm = j == 0 ? a : a - 1.0 / mm;
-        ci[(size_t)j * M + m] = 1.0 / mm;
+        ci[m * Ny + j] = 1.0 / mm;
       }
     }
   Workspace& W = h->W;
@@ -151,28 +152,54 @@ void upload_stokes_factors(discos_handle* h) {
   cudaMemcpy(W.st_di, di.data(), sizeof(double) * di.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(W.st_ci, ci.data(), sizeof(double) * ci.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(W.st_mc, mc.data(), sizeof(double) * mc.size(), cudaMemcpyHostToDevice);
+  if (h->mixed) {
+    auto up = [](float* dst, const std::vector<double>& v) {
+      std::vector<float> f(v.begin(), v.end());
+      cudaMemcpy(dst, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice);
+    };
+    up(W.st_l1f, l1); up(W.st_l2f, l2); up(W.st_dif, di); up(W.st_cif, ci); up(W.st_mcf, mc);
+  }
 }
 
 void free_workspace(discos_handle* h) {
   Workspace& W = h->W;
-  void* ptrs[] = {W.phi, W.spec, W.fgrid, W.inv_m, W.tw_x, W.tw_z, W.fptab, W.cell_of, W.counts, W.fill,
+  void* ptrs[] = {W.phi, W.spec, W.fgrid, W.piv64, W.piv32, W.tw_x, W.tw_z, W.fptab, W.cell_of, W.counts, W.fill,
                   W.cell_start, W.perm, W.tile_sums, W.xs, W.qs, W.sps, W.F, W.xstar, W.V,
-                  W.st_l1, W.st_l2, W.st_di, W.st_ci, W.st_mc, W.st_scratch, W.ps_scratch};
+                  W.st_l1, W.st_l2, W.st_di, W.st_ci, W.st_mc,
+                  W.lo_modes, W.is_lo, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf, W.Fn};
   for (void* p : ptrs) dfree(h, p);
   W = Workspace{};
+}
+
+// Stages 1 and 2 of Sec. II.D.  The near field (cell list + pair loop) does
+// not depend on the potential, so it runs on the handle's side stream while
+// the main stream spreads the charge and solves the Poisson problem; the
+// field interpolation then adds the near-field forces (F = q (E + E_ext) +
+// F_near).  `side_extra` enqueues further independent work on the side
+// stream before it rejoins (the step uses it for the stochastic stress).
+template <typename T, typename Extra>
+discos_status forces_impl(discos_handle* h, const T* x, const T* q, const int* species, int N, T* F, int* nbr,
+                          cudaStream_t s, Extra side_extra) {
+  const Params& P = h->P;
+  Workspace& W = h->W;
+  T* phi = reinterpret_cast<T*>(W.phi);
+  T* Fn = reinterpret_cast<T*>(W.Fn);
+  cudaError_t e = cudaEventRecord(h->ev_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+  if (e == cudaSuccess) e = launch_near_field<T>(P, W, x, q, species, N, Fn, nbr, h->side, false);
+  if (e == cudaSuccess) e = side_extra(h->side);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->side);
+  if (e == cudaSuccess) e = launch_spread_charge<T>(P, x, q, N, phi, s);
+  if (e == cudaSuccess) e = launch_poisson<T>(P, W, phi, phi, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_join, 0);
+  if (e == cudaSuccess) e = launch_interp_efield<T>(P, x, q, N, phi, F, true, s, Fn);
+  return cuda_status(e, "discos_forces");
 }
 
 template <typename T>
 discos_status forces_impl(discos_handle* h, const T* x, const T* q, const int* species, int N, T* F, int* nbr,
                           cudaStream_t s) {
-  const Params& P = h->P;
-  Workspace& W = h->W;
-  T* phi = reinterpret_cast<T*>(W.phi);
-  cudaError_t e = launch_spread_charge<T>(P, x, q, N, phi, s);
-  if (e == cudaSuccess) e = launch_poisson<T>(P, W, phi, phi, s);
-  if (e == cudaSuccess) e = launch_interp_efield<T>(P, x, q, N, phi, F, true, s);
-  if (e == cudaSuccess) e = launch_near_field<T>(P, W, x, q, species, N, F, nbr, s);
-  return cuda_status(e, "discos_forces");
+  return forces_impl<T>(h, x, q, species, N, F, nbr, s, [](cudaStream_t) { return cudaSuccess; });
 }
 
 template <typename T>
@@ -187,14 +214,20 @@ discos_status step_impl(discos_handle* h, T* x, const T* q, const int* species, 
   const bool wet = h->cfg.wet != 0;
   const bool thermal = P.kT > 0.0;
   const bool drift = P.drift != 0;
+  const size_t nf = (size_t)P.Nx * P.Nz * (3 * P.Ny + 1);
   for (int n = 0; n < nsteps; ++n) {
     const int64_t step = step0 + n;
-    discos_status st = forces_impl<T>(h, x, q, species, N, F, nullptr, s);
+    // the stochastic stress (or a zero fill) initialises the fluid forcing on
+    // the side stream, overlapping the electrostatics
+    auto side = [&](cudaStream_t ss) -> cudaError_t {
+      if (!wet) return cudaSuccess;
+      return thermal ? launch_stress_noise<T>(P, fg, step, ss, true) : launch_fill_zero<T>(fg, nf, ss);
+    };
+    discos_status st = forces_impl<T>(h, x, q, species, N, F, nullptr, s, side);
     if (st != DISCOS_OK) return st;
     cudaError_t e = cudaSuccess;
     if (wet) {
-      e = launch_spread_force<T>(P, x, F, N, fg, step, drift && thermal, s);
-      if (e == cudaSuccess && thermal) e = launch_stress_noise<T>(P, fg, step, s);
+      e = launch_spread_force<T>(P, x, F, N, fg, step, drift && thermal, s, true);
       if (e == cudaSuccess) e = launch_stokes<T>(P, W, fg, fg, nullptr, s);
       if (e == cudaSuccess) e = launch_interp_velocity<T>(P, x, N, fg, V, s);
       if (drift) {
@@ -319,7 +352,7 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   W.phi = dalloc(h, rs * G, &ok);
   W.spec = dalloc(h, 2 * rs * 4 * specslot, &ok);
   W.fgrid = dalloc(h, rs * Gf, &ok);
-  W.inv_m = (double*)dalloc(h, sizeof(double) * modes * c.Ny, &ok);
+  W.piv64 = (double*)dalloc(h, sizeof(double) * modes * c.Ny, &ok);
   W.tw_x = dalloc(h, 2 * rs * (c.Nx / 2), &ok);
   W.tw_z = dalloc(h, 2 * rs * (c.Nz / 2), &ok);
   W.fptab = dalloc(h, rs * (c.n_tab + 1), &ok);
@@ -335,15 +368,25 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   W.F = dalloc(h, rs * 3 * M, &ok);
   W.xstar = dalloc(h, rs * 3 * M, &ok);
   W.V = dalloc(h, rs * 3 * M, &ok);
-  W.ps_scratch = (double*)dalloc(h, sizeof(double) * (size_t)c.Ny * ((2 * modes + 127) / 128 * 128), &ok);
+  W.Fn = dalloc(h, rs * 3 * M, &ok);
+  if (h->mixed) {
+    W.is_lo = (unsigned char*)dalloc(h, modes, &ok);
+    W.lo_modes = (int*)dalloc(h, sizeof(int) * modes, &ok);
+    W.piv32 = (float*)dalloc(h, sizeof(float) * modes * c.Ny, &ok);
+    if (c.wet) {
+      W.st_l1f = (float*)dalloc(h, sizeof(float) * c.Ny * modes, &ok);
+      W.st_l2f = (float*)dalloc(h, sizeof(float) * c.Ny * modes, &ok);
+      W.st_dif = (float*)dalloc(h, sizeof(float) * c.Ny * modes, &ok);
+      W.st_cif = (float*)dalloc(h, sizeof(float) * c.Ny * modes, &ok);
+      W.st_mcf = (float*)dalloc(h, sizeof(float) * 5 * modes, &ok);
+    }
+  }
   if (c.wet) {
-    W.st_l1 = (double*)dalloc(h, sizeof(double) * (c.Ny - 1) * modes, &ok);
-    W.st_l2 = (double*)dalloc(h, sizeof(double) * (c.Ny - 1) * modes, &ok);
-    W.st_di = (double*)dalloc(h, sizeof(double) * (c.Ny - 1) * modes, &ok);
+    W.st_l1 = (double*)dalloc(h, sizeof(double) * c.Ny * modes, &ok);
+    W.st_l2 = (double*)dalloc(h, sizeof(double) * c.Ny * modes, &ok);
+    W.st_di = (double*)dalloc(h, sizeof(double) * c.Ny * modes, &ok);
     W.st_ci = (double*)dalloc(h, sizeof(double) * c.Ny * modes, &ok);
     W.st_mc = (double*)dalloc(h, sizeof(double) * 5 * modes, &ok);
-    const size_t S2 = (2 * modes + 127) / 128 * 128;
-    W.st_scratch = (double*)dalloc(h, sizeof(double) * (2 * (size_t)c.Ny * S2 + 2 * (c.Ny + 1)), &ok);
   }
   if (!ok) {
     free_workspace(h);
@@ -351,7 +394,7 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
     set_error("device allocation failed");
     return DISCOS_ERR_OOM;
   }
-  // Thomas pivots of the Poisson wall-normal systems, one set per (kx, kz)
+  // Thomas pivots of the Poisson wall-normal systems, one set per (kx, kz), [M][Ny]
   {
     std::vector<double> inv((size_t)c.Ny * modes);
     for (int kz = 0; kz < c.Nz; ++kz)
@@ -364,12 +407,43 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
           if (j == 0) d += c.bc[0] == DISCOS_BC_DIRICHLET ? 1.0 : -1.0;
           if (j == c.Ny - 1) d += c.bc[1] == DISCOS_BC_DIRICHLET ? 1.0 : -1.0;
           m = j == 0 ? d : d - 1.0 / m;
-          inv[(size_t)j * modes + mode] = m != 0.0 ? 1.0 / m : 0.0;
+          inv[mode * c.Ny + j] = m != 0.0 ? 1.0 / m : 0.0;
         }
       }
-    cudaMemcpy(W.inv_m, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(W.piv64, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice);
+    if (h->mixed) {
+      // modes solved in double: K^2 = lambda_x + lambda_z < 0.5 (see k_ysolve.cu)
+      std::vector<unsigned char> lo(modes, 0);
+      std::vector<int> list;
+      for (int kz = 0; kz < c.Nz; ++kz)
+        for (int kx = 0; kx < P.Nxh; ++kx) {
+          double K2 = (2.0 - 2.0 * std::cos(2.0 * M_PI * kx / c.Nx)) + (2.0 - 2.0 * std::cos(2.0 * M_PI * kz / c.Nz));
+          if (K2 < 0.5) {
+            size_t m = (size_t)kz * P.Nxh + kx;
+            lo[m] = 1;
+            list.push_back((int)m);
+          }
+        }
+      W.n_lo = (int)list.size();
+      std::vector<float> inv32(inv.begin(), inv.end());
+      cudaMemcpy(W.is_lo, lo.data(), lo.size(), cudaMemcpyHostToDevice);
+      if (!list.empty()) cudaMemcpy(W.lo_modes, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice);
+      cudaMemcpy(W.piv32, inv32.data(), sizeof(float) * inv32.size(), cudaMemcpyHostToDevice);
+    }
   }
   if (c.wet) upload_stokes_factors(h);
+  cudaMemset(W.fgrid, 0, rs * Gf);   // the wall rows of f_y stay zero from here on
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&W.ystream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&W.yev0, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&W.yev1, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    free_workspace(h);
+    delete h;
+    set_error("stream or event creation failed");
+    return DISCOS_ERR_CUDA;
+  }
   std::vector<double> tab = cached_fp_table(P.kes, c.psi, c.n_tab);
   if (h->mixed) {
     upload_twiddles<float>(W.tw_x, c.Nx);
@@ -393,7 +467,13 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
 discos_status discos_destroy(discos_handle* h) {
   if (!h) return invalid("null handle");
   cudaDeviceSynchronize();
+  if (h->W.ystream) cudaStreamDestroy(h->W.ystream);
+  if (h->W.yev0) cudaEventDestroy(h->W.yev0);
+  if (h->W.yev1) cudaEventDestroy(h->W.yev1);
   free_workspace(h);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
   return DISCOS_OK;
 }

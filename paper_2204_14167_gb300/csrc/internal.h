@@ -39,7 +39,8 @@ struct Workspace {
   void* phi = nullptr;         // [Nz][Ny][Nx] real: rho, then phi
   void* spec = nullptr;        // 3 spectra [Nz][Ny+1][Px] complex real
   void* fgrid = nullptr;       // fx|fy|fz real
-  double* inv_m = nullptr;     // Poisson Thomas pivots [Ny][modes]
+  double* piv64 = nullptr;     // Poisson Thomas reciprocal pivots [M][Ny]
+  float* piv32 = nullptr;      // single-precision copy (mixed path)
   void* tw_x = nullptr;        // twiddles exp(-2 pi i k / Nx), k < Nx/2
   void* tw_z = nullptr;        // twiddles exp(-2 pi i k / Nz), k < Nz/2
   void* fptab = nullptr;       // F^P table [n_tab + 1] real
@@ -56,14 +57,27 @@ struct Workspace {
   void* F = nullptr;           // forces [3][max_ions] real
   void* xstar = nullptr;       // midpoint positions [3][max_ions] real
   void* V = nullptr;           // interpolated velocities [3][max_ions] real
-  // Stokes wall-normal factors, [row][mode] in double (k_stokes.cu)
-  double* st_l1 = nullptr;     // pentadiagonal L D L^T: l1 [Ny-1][M]
-  double* st_l2 = nullptr;     // l2 [Ny-1][M]
-  double* st_di = nullptr;     // 1/D [Ny-1][M]
-  double* st_ci = nullptr;     // A_c Thomas reciprocal pivots [Ny][M]
-  double* st_mc = nullptr;     // per mode g_x, g_z, -1/K^2 [M][5]
-  double* st_scratch = nullptr;  // 2 x [Ny][2M] + 2 (Ny + 1)
-  double* ps_scratch = nullptr;  // Poisson forward values [Ny][2M rounded up to 128]
+  void* Fn = nullptr;          // near-field forces of the current step [3][max_ions] real
+  // Stokes wall-normal factors [M][Ny] in double: L D L^T of the pentadiagonal
+  // indexed by face (l1, l2, 1/D), A_c Thomas pivots by cell row; [M][5]
+  // per-mode constants (g_x, g_z, -1/K^2)
+  double* st_l1 = nullptr;
+  double* st_l2 = nullptr;
+  double* st_di = nullptr;
+  double* st_ci = nullptr;
+  double* st_mc = nullptr;
+  // mixed precision: modes with K^2 < 0.5 are solved in double (k_ysolve.cu)
+  int n_lo = 0;
+  int* lo_modes = nullptr;       // [n_lo] mode indices kz * Nxh + kx
+  unsigned char* is_lo = nullptr;  // [M]
+  float* st_l1f = nullptr;       // single-precision copies of the Stokes factors
+  float* st_l2f = nullptr;
+  float* st_dif = nullptr;
+  float* st_cif = nullptr;
+  float* st_mcf = nullptr;
+  // the double-precision low modes run on their own stream, beside the rest
+  cudaStream_t ystream = nullptr;
+  cudaEvent_t yev0 = nullptr, yev1 = nullptr;
   int n_cells = 0;
 };
 
@@ -78,6 +92,8 @@ struct discos_handle {
   discos_free_fn free_fn;
   void* alloc_ctx;
   int device;
+  cudaStream_t side = nullptr;       // independent work of a step runs here
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace discos {
@@ -95,20 +111,27 @@ double es_normalisation(int w, double beta);
 template <typename T> cudaError_t launch_cell_list(const Params& P, Workspace& W, const T* x, int N, cudaStream_t s);
 template <typename T> cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N, T* rho, cudaStream_t s);
 template <typename T> cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, T* f,
-                                                      int64_t step, bool rfd, cudaStream_t s);
-template <typename T> cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_t s);
+                                                      int64_t step, bool rfd, cudaStream_t s,
+                                                      bool accumulate = false);
+template <typename T> cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_t s,
+                                                      bool overwrite = false);
 template <typename T> cudaError_t launch_poisson(const Params& P, Workspace& W, const T* rho, T* phi, cudaStream_t s);
 template <typename T> cudaError_t launch_stokes(const Params& P, Workspace& W, const T* f, T* v, T* p, cudaStream_t s);
 template <typename T> cudaError_t launch_interp_efield(const Params& P, const T* x, const T* q, int N, const T* phi,
-                                                       T* out, bool as_force, cudaStream_t s);
+                                                       T* out, bool as_force, cudaStream_t s,
+                                                       const T* F_add = nullptr);
 template <typename T> cudaError_t launch_interp_velocity(const Params& P, const T* x, int N, const T* v, T* out,
                                                          cudaStream_t s);
 template <typename T> cudaError_t launch_near_field(const Params& P, Workspace& W, const T* x, const T* q,
-                                                    const int* species, int N, T* F, int* nbr, cudaStream_t s);
+                                                    const int* species, int N, T* F, int* nbr, cudaStream_t s,
+                                                    bool accumulate = true);
 template <typename T> cudaError_t launch_dry_update(const Params& P, T* x, const int* species, const T* F,
                                                    const T* V, int N, int64_t step, cudaStream_t s);
 template <typename T> cudaError_t launch_midpoint(const Params& P, const T* x, const T* V, int N, T* xstar,
                                                   cudaStream_t s);
 template <typename T> cudaError_t launch_fill_zero(T* p, size_t n, cudaStream_t s);
+template <typename T> cudaError_t launch_poisson_y(const Params& P, Workspace& W, cplx<T>* S, cudaStream_t s);
+template <typename T> cudaError_t launch_stokes_y(const Params& P, Workspace& W, cplx<T>* S, cplx<T>* Sp,
+                                                  cudaStream_t s);
 
 }  // namespace discos

@@ -45,7 +45,8 @@ __device__ __forceinline__ T phi_ghost(const T* __restrict__ phi, const Params& 
 
 template <typename T>
 __global__ void k_interp_efield(const T* __restrict__ x, const T* __restrict__ q, int N, Params P,
-                                const T* __restrict__ phi, T* __restrict__ out, int as_force) {
+                                const T* __restrict__ phi, T* __restrict__ out, int as_force,
+                                const T* __restrict__ F_add) {
   const KernelParams kp = P.kes;
   const int w = kp.w;
   int ion = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
@@ -89,9 +90,10 @@ __global__ void k_interp_efield(const T* __restrict__ x, const T* __restrict__ q
   if (valid && l == 0) {
     if (as_force) {
       T qq = q[ion];
-      out[ion] = qq * (Ex + T(P.E_ext[0]));
-      out[N + ion] = qq * (Ey + T(P.E_ext[1]));
-      out[2 * N + ion] = qq * (Ez + T(P.E_ext[2]));
+      T a0 = F_add ? F_add[ion] : T(0), a1 = F_add ? F_add[N + ion] : T(0), a2 = F_add ? F_add[2 * N + ion] : T(0);
+      out[ion] = qq * (Ex + T(P.E_ext[0])) + a0;
+      out[N + ion] = qq * (Ey + T(P.E_ext[1])) + a1;
+      out[2 * N + ion] = qq * (Ez + T(P.E_ext[2])) + a2;
     } else {
       out[ion] = Ex; out[N + ion] = Ey; out[2 * N + ion] = Ez;
     }
@@ -154,11 +156,11 @@ __global__ void k_interp_velocity(const T* __restrict__ x, int N, Params P, cons
 
 template <typename T>
 cudaError_t launch_interp_efield(const Params& P, const T* x, const T* q, int N, const T* phi, T* out,
-                                 bool as_force, cudaStream_t s) {
+                                 bool as_force, cudaStream_t s, const T* F_add) {
   if (N <= 0) return cudaSuccess;
   int bs = 256;
   int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
-  k_interp_efield<T><<<nb, bs, 0, s>>>(x, q, N, P, phi, out, as_force ? 1 : 0);
+  k_interp_efield<T><<<nb, bs, 0, s>>>(x, q, N, P, phi, out, as_force ? 1 : 0, F_add);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -173,8 +175,8 @@ cudaError_t launch_interp_velocity(const Params& P, const T* x, int N, const T* 
   return cudaGetLastError();
 }
 
-template cudaError_t launch_interp_efield<float>(const Params&, const float*, const float*, int, const float*, float*, bool, cudaStream_t);
-template cudaError_t launch_interp_efield<double>(const Params&, const double*, const double*, int, const double*, double*, bool, cudaStream_t);
+template cudaError_t launch_interp_efield<float>(const Params&, const float*, const float*, int, const float*, float*, bool, cudaStream_t, const float*);
+template cudaError_t launch_interp_efield<double>(const Params&, const double*, const double*, int, const double*, double*, bool, cudaStream_t, const double*);
 template cudaError_t launch_interp_velocity<float>(const Params&, const float*, int, const float*, float*, cudaStream_t);
 template cudaError_t launch_interp_velocity<double>(const Params&, const double*, int, const double*, double*, cudaStream_t);
 

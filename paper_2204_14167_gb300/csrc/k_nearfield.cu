@@ -95,7 +95,7 @@ __device__ __forceinline__ void pair_terms(const T xi, const T yi, const T zi, c
 template <typename T>
 __global__ void k_near_field(const T* __restrict__ xs, const T* __restrict__ qs, const int* __restrict__ sps,
                              const int* __restrict__ perm, const int* __restrict__ start, int N, Params P,
-                             const T* __restrict__ tab, T* __restrict__ F, int* __restrict__ nbr) {
+                             const T* __restrict__ tab, T* __restrict__ F, int* __restrict__ nbr, int accumulate) {
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (s >= N) return;                       // whole warps exit together
@@ -176,9 +176,15 @@ __global__ void k_near_field(const T* __restrict__ xs, const T* __restrict__ qs,
     }
   }
   const int i = perm[s];
-  F[i] += fx;
-  F[N + i] += fy;
-  F[2 * N + i] += fz;
+  if (accumulate) {
+    F[i] += fx;
+    F[N + i] += fy;
+    F[2 * N + i] += fz;
+  } else {
+    F[i] = fx;
+    F[N + i] = fy;
+    F[2 * N + i] = fz;
+  }
   if (nbr) nbr[i] = cnt;
 }
 
@@ -186,7 +192,7 @@ __global__ void k_near_field(const T* __restrict__ xs, const T* __restrict__ qs,
 
 template <typename T>
 cudaError_t launch_near_field(const Params& P, Workspace& W, const T* x, const T* q, const int* species, int N,
-                              T* F, int* nbr, cudaStream_t s) {
+                              T* F, int* nbr, cudaStream_t s, bool accumulate) {
   if (N <= 0) return cudaSuccess;
   cudaError_t e = launch_cell_list<T>(P, W, x, N, s);
   if (e != cudaSuccess) return e;
@@ -197,12 +203,12 @@ cudaError_t launch_near_field(const Params& P, Workspace& W, const T* x, const T
   k_gather<T><<<nb, bs, 0, s>>>(x, q, species, N, W.perm, xs, qs, W.sps);
   count_launches(1);
   k_near_field<T><<<(N + 7) / 8, 256, 0, s>>>(xs, qs, W.sps, W.perm, W.cell_start, N, P,
-                                                  reinterpret_cast<const T*>(W.fptab), F, nbr);
+                                                  reinterpret_cast<const T*>(W.fptab), F, nbr, accumulate ? 1 : 0);
   count_launches(1);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_near_field<float>(const Params&, Workspace&, const float*, const float*, const int*, int, float*, int*, cudaStream_t);
-template cudaError_t launch_near_field<double>(const Params&, Workspace&, const double*, const double*, const int*, int, double*, int*, cudaStream_t);
+template cudaError_t launch_near_field<float>(const Params&, Workspace&, const float*, const float*, const int*, int, float*, int*, cudaStream_t, bool);
+template cudaError_t launch_near_field<double>(const Params&, Workspace&, const double*, const double*, const int*, int, double*, int*, cudaStream_t, bool);
 
 }  // namespace discos

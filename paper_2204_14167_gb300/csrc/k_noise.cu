@@ -21,7 +21,7 @@ constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
 constexpr int HN = HX * HY * HZ;
 
 template <typename T>
-__global__ void k_stress_noise(T* __restrict__ f, Params P, long long step, T amp) {
+__global__ void k_stress_noise(T* __restrict__ f, Params P, long long step, T amp, int overwrite) {
   __shared__ T Zd[3][HN];     // xx, yy, zz
   __shared__ T Ze[3][HN];     // xy, xz, yz
   const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
@@ -63,12 +63,15 @@ __global__ void k_stress_noise(T* __restrict__ f, Params P, long long step, T am
     T dx = (Zd[0][h] - Zd[0][h - sx]) + (Ze[0][h + sy] - Ze[0][h]) + (Ze[1][h + sz] - Ze[1][h]);
     // z-face (i+1/2, j+1/2, k)
     T dz = (Ze[1][h + sx] - Ze[1][h]) + (Ze[2][h + sy] - Ze[2][h]) + (Zd[2][h] - Zd[2][h - sz]);
-    fx[((size_t)k * Ny + j) * Nx + i] += amp * dx;
-    fz[((size_t)k * Ny + j) * Nx + i] += amp * dz;
+    T* px = &fx[((size_t)k * Ny + j) * Nx + i];
+    T* pz = &fz[((size_t)k * Ny + j) * Nx + i];
+    *px = overwrite ? amp * dx : *px + amp * dx;
+    *pz = overwrite ? amp * dz : *pz + amp * dz;
     if (j >= 1) {
       // y-face (i+1/2, j, k+1/2)
       T dy = (Ze[0][h + sx] - Ze[0][h]) + (Zd[1][h] - Zd[1][h - sy]) + (Ze[2][h + sz] - Ze[2][h]);
-      fy[((size_t)k * (Ny + 1) + j) * Nx + i] += amp * dy;
+      T* py = &fy[((size_t)k * (Ny + 1) + j) * Nx + i];
+      *py = overwrite ? amp * dy : *py + amp * dy;
     }
   }
 }
@@ -76,15 +79,15 @@ __global__ void k_stress_noise(T* __restrict__ f, Params P, long long step, T am
 }  // namespace
 
 template <typename T>
-cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_t s) {
+cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_t s, bool overwrite) {
   dim3 grid((P.Nx + TX - 1) / TX, (P.Ny + TY - 1) / TY, (P.Nz + TZ - 1) / TZ);
   T amp = T(sqrt(2.0 * P.kT * P.eta / P.dt));
-  k_stress_noise<T><<<grid, 256, 0, s>>>(f, P, (long long)step, amp);
+  k_stress_noise<T><<<grid, 256, 0, s>>>(f, P, (long long)step, amp, overwrite ? 1 : 0);
   count_launches(1);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_stress_noise<float>(const Params&, float*, int64_t, cudaStream_t);
-template cudaError_t launch_stress_noise<double>(const Params&, double*, int64_t, cudaStream_t);
+template cudaError_t launch_stress_noise<float>(const Params&, float*, int64_t, cudaStream_t, bool);
+template cudaError_t launch_stress_noise<double>(const Params&, double*, int64_t, cudaStream_t, bool);
 
 }  // namespace discos

@@ -157,9 +157,9 @@ cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N,
 
 template <typename T>
 cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, T* f, int64_t step, bool rfd,
-                                cudaStream_t s) {
+                                cudaStream_t s, bool accumulate) {
   size_t n = (size_t)P.Nx * P.Nz * (3 * P.Ny + 1);
-  cudaError_t e = launch_fill_zero(f, n, s);
+  cudaError_t e = accumulate ? cudaSuccess : launch_fill_zero(f, n, s);
   if (e != cudaSuccess || N <= 0) return e;
   int bs = 256;
   dim3 grid((unsigned)(((size_t)N * 8 + bs - 1) / bs), 3);
@@ -172,7 +172,7 @@ template cudaError_t launch_fill_zero<float>(float*, size_t, cudaStream_t);
 template cudaError_t launch_fill_zero<double>(double*, size_t, cudaStream_t);
 template cudaError_t launch_spread_charge<float>(const Params&, const float*, const float*, int, float*, cudaStream_t);
 template cudaError_t launch_spread_charge<double>(const Params&, const double*, const double*, int, double*, cudaStream_t);
-template cudaError_t launch_spread_force<float>(const Params&, const float*, const float*, int, float*, int64_t, bool, cudaStream_t);
-template cudaError_t launch_spread_force<double>(const Params&, const double*, const double*, int, double*, int64_t, bool, cudaStream_t);
+template cudaError_t launch_spread_force<float>(const Params&, const float*, const float*, int, float*, int64_t, bool, cudaStream_t, bool);
+template cudaError_t launch_spread_force<double>(const Params&, const double*, const double*, int, double*, int64_t, bool, cudaStream_t, bool);
 
 }  // namespace discos

@@ -1,0 +1,526 @@
+// Wall-normal banded solves as warp-parallel scans.
+//
+// After the x and z transforms every (kx, kz) mode is an independent banded
+// system in y: the Poisson tridiagonal (2 + K^2) phi_j - phi_{j-1} - phi_{j+1}
+// = b_j with the wall rows of Eqs. esbc1 / esbc3, and the Stokes
+// pentadiagonal / tridiagonal pair of Eq. disc_stokes (algebra in
+// k_stokes.cu).  Their factors are pre-computed per mode; what remains per
+// step are linear recurrences along y (forward and backward substitutions),
+// first order for a tridiagonal, second order for the pentadiagonal.
+//
+// One warp solves one mode.  Lane l owns R consecutive rows; a recurrence
+// s_j = A_j s_{j-1} + c_j is solved by composing each lane's affine maps, an
+// inclusive scan of the composed maps across the warp (shuffles, log2 32
+// levels), and a final local pass from the state entering the lane.  The
+// critical path is ~R + 5 map compositions instead of Ny dependent steps.
+//
+// Precision follows conditioning.  K^2 = lambda_x + lambda_z sets the
+// condition numbers: for K^2 >= 0.5 the tridiagonal has kappa <= 9 and the
+// pentadiagonal kappa <= 81, so the mixed path solves those modes in single
+// precision (error well below 1e-5); the modes with K^2 < 0.5 (a few percent,
+// the ill-conditioned ones and the singular K = 0 mode) are solved in double.
+// The FP64 path solves every mode in double.
+#include <type_traits>
+#include "internal.h"
+
+namespace discos {
+
+namespace {
+
+template <typename T> struct C { T r, i; };
+template <typename T> __device__ __forceinline__ C<T> cz() { return C<T>{T(0), T(0)}; }
+template <typename T> __device__ __forceinline__ C<T> cadd2(C<T> a, C<T> b) { return C<T>{a.r + b.r, a.i + b.i}; }
+template <typename T> __device__ __forceinline__ C<T> csub2(C<T> a, C<T> b) { return C<T>{a.r - b.r, a.i - b.i}; }
+template <typename T> __device__ __forceinline__ C<T> cscale(T s, C<T> a) { return C<T>{s * a.r, s * a.i}; }
+template <typename T> __device__ __forceinline__ C<T> cfma(T s, C<T> a, C<T> b) {
+  return C<T>{fma(s, a.r, b.r), fma(s, a.i, b.i)};
+}
+template <typename T> __device__ __forceinline__ T shup(T v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+template <typename T> __device__ __forceinline__ T shdn(T v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+
+// first order, two complex offsets sharing the multiplier: s -> a s + b
+template <typename T> struct M1 { T a; C<T> b0, b1; };
+template <typename T> __device__ __forceinline__ M1<T> m1_id() { return M1<T>{T(1), cz<T>(), cz<T>()}; }
+// apply `in` first, then `out`
+template <typename T> __device__ __forceinline__ M1<T> m1_comp(const M1<T>& out, const M1<T>& in) {
+  return M1<T>{out.a * in.a, cfma(out.a, in.b0, out.b0), cfma(out.a, in.b1, out.b1)};
+}
+template <typename T> __device__ __forceinline__ M1<T> m1_sh(const M1<T>& m, int o, bool up) {
+  M1<T> r;
+  r.a = up ? shup(m.a, o) : shdn(m.a, o);
+  r.b0.r = up ? shup(m.b0.r, o) : shdn(m.b0.r, o);
+  r.b0.i = up ? shup(m.b0.i, o) : shdn(m.b0.i, o);
+  r.b1.r = up ? shup(m.b1.r, o) : shdn(m.b1.r, o);
+  r.b1.i = up ? shup(m.b1.i, o) : shdn(m.b1.i, o);
+  return r;
+}
+// Exclusive scan: forward (lane order) gives m_{l-1} o ... o m_0 on lane l;
+// backward gives m_{l+1} o ... o m_31.
+template <typename T> __device__ __forceinline__ M1<T> m1_exscan(M1<T> m, int lane, bool forward) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    M1<T> q = m1_sh(m, o, forward);
+    bool take = forward ? lane >= o : lane + o < 32;
+    if (take) m = m1_comp(m, q);
+  }
+  M1<T> e = m1_sh(m, 1, forward);
+  bool first = forward ? lane == 0 : lane == 31;
+  return first ? m1_id<T>() : e;
+}
+
+// second order on a complex state (s0, s1): s -> A s + c, A real 2 x 2
+template <typename T> struct M2 { T a00, a01, a10, a11; C<T> c0, c1; };
+template <typename T> __device__ __forceinline__ M2<T> m2_id() {
+  return M2<T>{T(1), T(0), T(0), T(1), cz<T>(), cz<T>()};
+}
+template <typename T> __device__ __forceinline__ M2<T> m2_comp(const M2<T>& o, const M2<T>& n) {
+  M2<T> r;
+  r.a00 = o.a00 * n.a00 + o.a01 * n.a10;
+  r.a01 = o.a00 * n.a01 + o.a01 * n.a11;
+  r.a10 = o.a10 * n.a00 + o.a11 * n.a10;
+  r.a11 = o.a10 * n.a01 + o.a11 * n.a11;
+  r.c0 = cadd2(cadd2(cscale(o.a00, n.c0), cscale(o.a01, n.c1)), o.c0);
+  r.c1 = cadd2(cadd2(cscale(o.a10, n.c0), cscale(o.a11, n.c1)), o.c1);
+  return r;
+}
+template <typename T> __device__ __forceinline__ M2<T> m2_sh(const M2<T>& m, int o, bool up) {
+  M2<T> r;
+#define SH(x) (up ? shup(x, o) : shdn(x, o))
+  r.a00 = SH(m.a00); r.a01 = SH(m.a01); r.a10 = SH(m.a10); r.a11 = SH(m.a11);
+  r.c0.r = SH(m.c0.r); r.c0.i = SH(m.c0.i); r.c1.r = SH(m.c1.r); r.c1.i = SH(m.c1.i);
+#undef SH
+  return r;
+}
+template <typename T> __device__ __forceinline__ M2<T> m2_exscan(M2<T> m, int lane, bool forward) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    M2<T> q = m2_sh(m, o, forward);
+    bool take = forward ? lane >= o : lane + o < 32;
+    if (take) m = m2_comp(m, q);
+  }
+  M2<T> e = m2_sh(m, 1, forward);
+  bool first = forward ? lane == 0 : lane == 31;
+  return first ? m2_id<T>() : e;
+}
+
+template <typename TS> __device__ __forceinline__ C<double> ldc(const cplx<TS>* p) {
+  cplx<TS> v = *p;
+  return C<double>{(double)v.re, (double)v.im};
+}
+
+// ------------------------------------------------------------------ Poisson
+// piv [M][Ny]: reciprocal Thomas pivots.  Forward y_j = piv_j (b_j + y_{j-1}),
+// backward x_j = y_j + piv_j x_{j+1}.  The singular K = 0 mode of two
+// Neumann walls: phi_0 = 0, phi_{j+1} = 2 phi_j - phi_{j-1} - b_j (the last
+// equation is redundant for a neutral system), then the mean is removed.
+template <typename TS, typename TC, int R>
+__global__ void k_poisson_scan(cplx<TS>* __restrict__ S, const TC* __restrict__ piv, const int* __restrict__ list,
+                               int n_list, const unsigned char* __restrict__ skip, int Ny, int Nz, int Nxh, int Px,
+                               int singular, double norm) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n_list) return;
+  const int mode = list ? list[w] : w;
+  if (skip && skip[mode]) return;
+  const int kz = mode / Nxh, kx = mode - kz * Nxh;
+  cplx<TS>* col = S + (size_t)kz * Ny * Px + kx;
+  const TC* pv = piv + (size_t)mode * Ny;
+  const int j0 = lane * R;
+  C<TC> b[R];
+  TC m[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    int j = j0 + r;
+    if (j < Ny) {
+      cplx<TS> v = col[(size_t)j * Px];
+      b[r] = C<TC>{(TC)v.re, (TC)v.im};
+      m[r] = pv[j];
+    } else {
+      b[r] = cz<TC>();
+      m[r] = TC(1);
+    }
+  }
+  C<TC> x[R];
+  if (singular && mode == 0) {
+    // state (phi_j, phi_{j-1}); row j maps it to (phi_{j+1}, phi_j)
+    M2<TC> loc = m2_id<TC>();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      int j = j0 + r;
+      M2<TC> mj = m2_id<TC>();
+      if (j == 0) mj = M2<TC>{TC(1), TC(0), TC(1), TC(0), C<TC>{-b[r].r, -b[r].i}, cz<TC>()};
+      else if (j < Ny - 1) mj = M2<TC>{TC(2), TC(-1), TC(1), TC(0), C<TC>{-b[r].r, -b[r].i}, cz<TC>()};
+      loc = m2_comp(mj, loc);
+    }
+    M2<TC> pre = m2_exscan(loc, lane, true);
+    C<TC> s0 = pre.c0, s1 = pre.c1;     // state entering the lane, from (0, 0)
+    C<TC> sum = cz<TC>();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      int j = j0 + r;
+      x[r] = s0;
+      if (j < Ny) sum = cadd2(sum, s0);
+      C<TC> n0 = s0, n1 = s1;
+      if (j == 0) { n0 = csub2(s0, b[r]); n1 = s0; }
+      else if (j < Ny - 1) { n0 = csub2(csub2(cscale(TC(2), s0), s1), b[r]); n1 = s0; }
+      s0 = n0; s1 = n1;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sum.r += __shfl_xor_sync(0xffffffffu, sum.r, o);
+      sum.i += __shfl_xor_sync(0xffffffffu, sum.i, o);
+    }
+    C<TC> mean = cscale(TC(1) / TC(Ny), sum);
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = csub2(x[r], mean);
+  } else {
+    // forward: y_j = m_j y_{j-1} + m_j b_j
+    M1<TC> loc = m1_id<TC>();
+#pragma unroll
+    for (int r = 0; r < R; ++r) loc = m1_comp(M1<TC>{m[r], cscale(m[r], b[r]), cz<TC>()}, loc);
+    M1<TC> pre = m1_exscan(loc, lane, true);
+    C<TC> y = pre.b0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      y = cscale(m[r], cadd2(b[r], y));
+      x[r] = y;          // forward values for now
+    }
+    // backward: x_j = y_j + m_j x_{j+1}, x_{Ny-1} = y_{Ny-1}
+    M1<TC> locb = m1_id<TC>();
+#pragma unroll
+    for (int r = R - 1; r >= 0; --r) {
+      int j = j0 + r;
+      TC a = (j < Ny - 1) ? m[r] : TC(0);
+      if (j >= Ny) a = TC(1);
+      C<TC> c = (j < Ny) ? x[r] : cz<TC>();
+      locb = m1_comp(M1<TC>{a, c, cz<TC>()}, locb);
+    }
+    M1<TC> preb = m1_exscan(locb, lane, false);
+    C<TC> xn = preb.b0;
+#pragma unroll
+    for (int r = R - 1; r >= 0; --r) {
+      int j = j0 + r;
+      if (j < Ny) {
+        TC a = (j < Ny - 1) ? m[r] : TC(0);
+        xn = cfma(a, xn, x[r]);
+        x[r] = xn;
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    int j = j0 + r;
+    if (j < Ny) col[(size_t)j * Px] = cplx<TS>{(TS)(x[r].r * (TC)norm), (TS)(x[r].i * (TC)norm)};
+  }
+}
+
+// ------------------------------------------------------------------- Stokes
+// Per mode (K > 0), with g = g_x f_x + g_z f_z on cell rows:
+//  A  forward L D L^T substitution over the faces f = 1..Ny-1:
+//       y_f = rhs_f - l1_f y_{f-1} - l2_f y_{f-2},  rhs_f = (K^2 f_y,f + g_f - g_{f-1}) / eta
+//  B  backward: v_f = y_f d_f - l1_{f+1} v_{f+1} - l2_{f+2} v_{f+2}
+//  C  p_j = -(g_j + eta (A_c D_y v)_j) / K^2 (row-local), then the forward
+//     Thomas sweeps of eta A_c u = f_x + conj(g_x) p and eta A_c w = f_z + conj(g_z) p
+//  D  their backward sweeps.
+// Tables [M][Ny] indexed by face (L1, L2, DI; entry 0 unused) or cell row (CI);
+// MC [M][5] = (g_x, g_z, -1/K^2; 0 for K = 0).  The K = 0 mode (all-zero
+// pentadiagonal factors) gives v = 0 and p = 0 here; its pressure, needed only
+// for output, is p_j = sum_{f=1..j} f_y,f with the mean removed.
+template <typename TS, typename TC, int R>
+__global__ void k_stokes_scan(cplx<TS>* __restrict__ S, cplx<TS>* __restrict__ Sp, Params P,
+                              const TC* __restrict__ L1, const TC* __restrict__ L2, const TC* __restrict__ DI,
+                              const TC* __restrict__ CI, const TC* __restrict__ MC, const int* __restrict__ list,
+                              int n_list, const unsigned char* __restrict__ skip) {
+  extern __shared__ unsigned char smem_raw[];
+  const int Ny = P.Ny, Nz = P.Nz, Px = P.Px, Nxh = P.Nxh;
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (w >= n_list) return;
+  const int mode = list ? list[w] : w;
+  if (skip && skip[mode]) return;
+  C<TC>* sg = reinterpret_cast<C<TC>*>(smem_raw) + (size_t)wib * (2 * Ny + 1);   // g [Ny]
+  C<TC>* sv = sg + Ny;                                                              // v [Ny + 1]
+  const int kz = mode / Nxh, kx = mode - kz * Nxh;
+  cplx<TS>* Su = S + (size_t)kz * Ny * Px + kx;
+  cplx<TS>* Sv = S + (size_t)Nz * Ny * Px + (size_t)kz * (Ny + 1) * Px + kx;
+  cplx<TS>* Sw = S + (size_t)Nz * (2 * Ny + 1) * Px + (size_t)kz * Ny * Px + kx;
+  const TC* l1 = L1 + (size_t)mode * Ny;
+  const TC* l2 = L2 + (size_t)mode * Ny;
+  const TC* di = DI + (size_t)mode * Ny;
+  const TC* ci = CI + (size_t)mode * Ny;
+  const TC gxr = MC[5 * (size_t)mode], gxi = MC[5 * (size_t)mode + 1];
+  const TC gzr = MC[5 * (size_t)mode + 2], gzi = MC[5 * (size_t)mode + 3];
+  const TC mik2 = MC[5 * (size_t)mode + 4];
+  const TC K2 = mik2 != TC(0) ? TC(-1) / mik2 : TC(0);
+  const TC eta = (TC)P.eta, ieta = (TC)(1.0 / P.eta);
+  const TC norm = (TC)(1.0 / ((double)P.Nx * P.Nz));
+  const int j0 = lane * R;
+  C<TC> fx[R], fz[R], fy[R], g[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    int j = j0 + r;
+    if (j < Ny) {
+      cplx<TS> a = Su[(size_t)j * Px], b = Sw[(size_t)j * Px], c = Sv[(size_t)j * Px];
+      fx[r] = C<TC>{(TC)a.re, (TC)a.im};
+      fz[r] = C<TC>{(TC)b.re, (TC)b.im};
+      fy[r] = C<TC>{(TC)c.re, (TC)c.im};
+      g[r] = C<TC>{gxr * fx[r].r - gxi * fx[r].i + gzr * fz[r].r - gzi * fz[r].i,
+                   gxr * fx[r].i + gxi * fx[r].r + gzr * fz[r].i + gzi * fz[r].r};
+      sg[j] = g[r];
+    } else {
+      fx[r] = fz[r] = fy[r] = g[r] = cz<TC>();
+    }
+  }
+  // K = 0 pressure (output only): p_j = sum_{f=1..j} f_y,f, mean removed
+  if (mode == 0 && Sp) {
+    M1<TC> loc = m1_id<TC>();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      int j = j0 + r;
+      C<TC> add = (j >= 1 && j < Ny) ? fy[r] : cz<TC>();
+      loc = m1_comp(M1<TC>{TC(1), add, cz<TC>()}, loc);
+    }
+    M1<TC> pre = m1_exscan(loc, lane, true);
+    C<TC> p = pre.b0, sum = cz<TC>(), pv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      int j = j0 + r;
+      if (j >= 1 && j < Ny) p = cadd2(p, fy[r]);
+      pv[r] = p;
+      if (j < Ny) sum = cadd2(sum, p);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sum.r += __shfl_xor_sync(0xffffffffu, sum.r, o);
+      sum.i += __shfl_xor_sync(0xffffffffu, sum.i, o);
+    }
+    C<TC> mean = cscale(TC(1) / TC(Ny), sum);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      int j = j0 + r;
+      if (j < Ny) {
+        C<TC> q = csub2(pv[r], mean);
+        Sp[(size_t)kz * Ny * Px + kx + (size_t)j * Px] = cplx<TS>{(TS)(q.r * norm), (TS)(q.i * norm)};
+      }
+    }
+  }
+  __syncwarp();
+  // ---- A: forward, state (y_f, y_{f-1})
+  C<TC> y[R];
+  {
+    M2<TC> loc = m2_id<TC>();
+    C<TC> rhs[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      int f = j0 + r;
+      rhs[r] = cz<TC>();
+      if (f >= 1 && f < Ny) {
+        C<TC> gm = sg[f - 1];
+        rhs[r] = cscale(ieta, C<TC>{K2 * fy[r].r + (g[r].r - gm.r), K2 * fy[r].i + (g[r].i - gm.i)});
+        M2<TC> mf{-l1[f], -l2[f], TC(1), TC(0), rhs[r], cz<TC>()};
+        loc = m2_comp(mf, loc);
+      }
+    }
+    M2<TC> pre = m2_exscan(loc, lane, true);
+    C<TC> s0 = pre.c0, s1 = pre.c1;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      int f = j0 + r;
+      if (f >= 1 && f < Ny) {
+        C<TC> n0 = csub2(csub2(rhs[r], cscale(l1[f], s0)), cscale(l2[f], s1));
+        s1 = s0; s0 = n0;
+      }
+      y[r] = s0;
+    }
+  }
+  // ---- B: backward, state (v_f, v_{f+1})
+  C<TC> v[R];
+  {
+    M2<TC> loc = m2_id<TC>();
+#pragma unroll
+    for (int r = R - 1; r >= 0; --r) {
+      int f = j0 + r;
+      if (f >= 1 && f < Ny) {
+        TC a1 = f + 1 < Ny ? l1[f + 1] : TC(0);
+        TC a2 = f + 2 < Ny ? l2[f + 2] : TC(0);
+        M2<TC> mf{-a1, -a2, TC(1), TC(0), cscale(di[f], y[r]), cz<TC>()};
+        loc = m2_comp(mf, loc);
+      }
+    }
+    M2<TC> pre = m2_exscan(loc, lane, false);
+    C<TC> s0 = pre.c0, s1 = pre.c1;
+#pragma unroll
+    for (int r = R - 1; r >= 0; --r) {
+      int f = j0 + r;
+      if (f >= 1 && f < Ny) {
+        TC a1 = f + 1 < Ny ? l1[f + 1] : TC(0);
+        TC a2 = f + 2 < Ny ? l2[f + 2] : TC(0);
+        C<TC> n0 = csub2(csub2(cscale(di[f], y[r]), cscale(a1, s0)), cscale(a2, s1));
+        s1 = s0; s0 = n0;
+        v[r] = n0;
+      } else {
+        v[r] = cz<TC>();
+      }
+      if (f <= Ny) sv[f] = v[r];
+    }
+    if (lane == 0) sv[Ny] = cz<TC>();
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    int f = j0 + r;
+    if (f < Ny + 1) {
+      C<TC> vv = (f >= 1 && f < Ny) ? v[r] : cz<TC>();
+      Sv[(size_t)f * Px] = cplx<TS>{(TS)(vv.r * norm), (TS)(vv.i * norm)};
+    }
+  }
+  if (lane == 0) Sv[(size_t)Ny * Px] = cplx<TS>{TS(0), TS(0)};
+  // ---- C: pressure (row-local) and the forward sweeps for u and w
+  C<TC> bu[R], bw[R];
+  TC cm[R];
+  {
+    M1<TC> loc = m1_id<TC>();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      int j = j0 + r;
+      bu[r] = bw[r] = cz<TC>();
+      cm[r] = TC(1);
+      if (j < Ny) {
+        C<TC> e0 = csub2(sv[j + 1], sv[j]);
+        TC a = K2 + TC(2) + (j == 0 ? TC(1) : TC(0)) + (j == Ny - 1 ? TC(1) : TC(0));
+        C<TC> acd = cscale(a, e0);
+        if (j >= 1) acd = csub2(acd, csub2(sv[j], sv[j - 1]));
+        if (j <= Ny - 2) acd = csub2(acd, csub2(sv[j + 2], sv[j + 1]));
+        C<TC> p = cscale(mik2, cfma(eta, acd, g[r]));
+        if (Sp && mode != 0)
+          Sp[(size_t)kz * Ny * Px + kx + (size_t)j * Px] = cplx<TS>{(TS)(p.r * norm), (TS)(p.i * norm)};
+        // conj(g) p = (gr pr + gi pi) + i (gr pi - gi pr)
+        bu[r] = cscale(ieta, C<TC>{fx[r].r + gxr * p.r + gxi * p.i, fx[r].i + gxr * p.i - gxi * p.r});
+        bw[r] = cscale(ieta, C<TC>{fz[r].r + gzr * p.r + gzi * p.i, fz[r].i + gzr * p.i - gzi * p.r});
+        cm[r] = ci[j];
+        loc = m1_comp(M1<TC>{cm[r], cscale(cm[r], bu[r]), cscale(cm[r], bw[r])}, loc);
+      }
+    }
+    M1<TC> pre = m1_exscan(loc, lane, true);
+    C<TC> yu = pre.b0, yw = pre.b1;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      int j = j0 + r;
+      if (j < Ny) {
+        yu = cscale(cm[r], cadd2(bu[r], yu));
+        yw = cscale(cm[r], cadd2(bw[r], yw));
+      }
+      bu[r] = yu;
+      bw[r] = yw;
+    }
+  }
+  // ---- D: backward sweeps x_j = y_j + c_j x_{j+1}
+  {
+    M1<TC> loc = m1_id<TC>();
+#pragma unroll
+    for (int r = R - 1; r >= 0; --r) {
+      int j = j0 + r;
+      if (j < Ny) {
+        TC a = j < Ny - 1 ? cm[r] : TC(0);
+        loc = m1_comp(M1<TC>{a, bu[r], bw[r]}, loc);
+      }
+    }
+    M1<TC> pre = m1_exscan(loc, lane, false);
+    C<TC> xu = pre.b0, xw = pre.b1;
+#pragma unroll
+    for (int r = R - 1; r >= 0; --r) {
+      int j = j0 + r;
+      if (j < Ny) {
+        TC a = j < Ny - 1 ? cm[r] : TC(0);
+        xu = cfma(a, xu, bu[r]);
+        xw = cfma(a, xw, bw[r]);
+        Su[(size_t)j * Px] = cplx<TS>{(TS)(xu.r * norm), (TS)(xu.i * norm)};
+        Sw[(size_t)j * Px] = cplx<TS>{(TS)(xw.r * norm), (TS)(xw.i * norm)};
+      }
+    }
+  }
+}
+
+template <typename TS, typename TC>
+cudaError_t poisson_scan_launch(const Params& P, cplx<TS>* S, const TC* piv, const int* list, int n,
+                                const unsigned char* skip, cudaStream_t s) {
+  const int Ny = P.Ny;
+  const int singular = (P.bc[0] == DISCOS_BC_NEUMANN && P.bc[1] == DISCOS_BC_NEUMANN) ? 1 : 0;
+  const double norm = 1.0 / ((double)P.Nx * P.Nz);
+  const int bs = 256;
+  const int nb = (n * 32 + bs - 1) / bs;
+  if (n <= 0) return cudaSuccess;
+  if (Ny <= 32) k_poisson_scan<TS, TC, 1><<<nb, bs, 0, s>>>(S, piv, list, n, skip, Ny, P.Nz, P.Nxh, P.Px, singular, norm);
+  else if (Ny <= 64) k_poisson_scan<TS, TC, 2><<<nb, bs, 0, s>>>(S, piv, list, n, skip, Ny, P.Nz, P.Nxh, P.Px, singular, norm);
+  else if (Ny <= 128) k_poisson_scan<TS, TC, 4><<<nb, bs, 0, s>>>(S, piv, list, n, skip, Ny, P.Nz, P.Nxh, P.Px, singular, norm);
+  else k_poisson_scan<TS, TC, 8><<<nb, bs, 0, s>>>(S, piv, list, n, skip, Ny, P.Nz, P.Nxh, P.Px, singular, norm);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename TS, typename TC>
+cudaError_t stokes_scan_launch(const Params& P, cplx<TS>* S, cplx<TS>* Sp, const TC* L1, const TC* L2,
+                               const TC* DI, const TC* CI, const TC* MC, const int* list, int n,
+                               const unsigned char* skip, cudaStream_t s) {
+  const int Ny = P.Ny;
+  if (n <= 0) return cudaSuccess;
+  const size_t per_warp = (size_t)(2 * Ny + 1) * sizeof(C<TC>);
+  int warps = 8;
+  while (warps > 1 && warps * per_warp > 48 * 1024) --warps;   // stay within the default shared-memory limit
+  const size_t sm = (size_t)warps * per_warp;
+  const int nb = (n + warps - 1) / warps;
+  const int bs = 32 * warps;
+  if (Ny <= 32) k_stokes_scan<TS, TC, 1><<<nb, bs, sm, s>>>(S, Sp, P, L1, L2, DI, CI, MC, list, n, skip);
+  else if (Ny <= 64) k_stokes_scan<TS, TC, 2><<<nb, bs, sm, s>>>(S, Sp, P, L1, L2, DI, CI, MC, list, n, skip);
+  else if (Ny <= 128) k_stokes_scan<TS, TC, 4><<<nb, bs, sm, s>>>(S, Sp, P, L1, L2, DI, CI, MC, list, n, skip);
+  else k_stokes_scan<TS, TC, 8><<<nb, bs, sm, s>>>(S, Sp, P, L1, L2, DI, CI, MC, list, n, skip);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_poisson_y(const Params& P, Workspace& W, cplx<T>* S, cudaStream_t s) {
+  const int M = P.Nxh * P.Nz;
+  if constexpr (std::is_same<T, float>::value) {
+    // low modes (double) on the side stream, the rest (single) on s
+    cudaError_t e = cudaEventRecord(W.yev0, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(W.ystream, W.yev0, 0);
+    if (e == cudaSuccess) e = poisson_scan_launch<float, double>(P, S, W.piv64, W.lo_modes, W.n_lo, nullptr, W.ystream);
+    if (e == cudaSuccess) e = cudaEventRecord(W.yev1, W.ystream);
+    if (e == cudaSuccess) e = poisson_scan_launch<float, float>(P, S, W.piv32, nullptr, M, W.is_lo, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, W.yev1, 0);
+    return e;
+  } else {
+    return poisson_scan_launch<double, double>(P, S, W.piv64, nullptr, M, nullptr, s);
+  }
+}
+
+template <typename T>
+cudaError_t launch_stokes_y(const Params& P, Workspace& W, cplx<T>* S, cplx<T>* Sp, cudaStream_t s) {
+  const int M = P.Nxh * P.Nz;
+  if constexpr (std::is_same<T, float>::value) {
+    cudaError_t e = cudaEventRecord(W.yev0, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(W.ystream, W.yev0, 0);
+    if (e == cudaSuccess)
+      e = stokes_scan_launch<float, double>(P, S, Sp, W.st_l1, W.st_l2, W.st_di, W.st_ci, W.st_mc, W.lo_modes,
+                                            W.n_lo, nullptr, W.ystream);
+    if (e == cudaSuccess) e = cudaEventRecord(W.yev1, W.ystream);
+    if (e == cudaSuccess)
+      e = stokes_scan_launch<float, float>(P, S, Sp, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf, nullptr,
+                                           M, W.is_lo, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, W.yev1, 0);
+    return e;
+  } else {
+    return stokes_scan_launch<double, double>(P, S, Sp, W.st_l1, W.st_l2, W.st_di, W.st_ci, W.st_mc, nullptr, M,
+                                              nullptr, s);
+  }
+}
+
+template cudaError_t launch_poisson_y<float>(const Params&, Workspace&, cplx<float>*, cudaStream_t);
+template cudaError_t launch_poisson_y<double>(const Params&, Workspace&, cplx<double>*, cudaStream_t);
+template cudaError_t launch_stokes_y<float>(const Params&, Workspace&, cplx<float>*, cplx<float>*, cudaStream_t);
+template cudaError_t launch_stokes_y<double>(const Params&, Workspace&, cplx<double>*, cplx<double>*, cudaStream_t);
+
+}  // namespace discos
