@@ -153,6 +153,12 @@ def run_ours(args):
         step += 1
     torch.cuda.synchronize()
 
+    # dominant kernel family (by per-step time), then the timed region with a
+    # live event probe on that family
+    breakdown, step = kernel_breakdown(dg, h, x, qd, step)
+    dominant = max(breakdown, key=breakdown.get)
+    dg.probe(h, dominant)
+
     # device-timed region: K steps, L2 flushed between steps (outside the events)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -173,6 +179,8 @@ def run_ours(args):
         dist.barrier()
     clocks = stop_clocks(dev)
     t_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    probe_ms, probe_n = dg.probe_read(h)
+    dg.probe(h, None)
     if dist:
         tt = torch.tensor([t_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -201,11 +209,18 @@ def run_ours(args):
            "h2d_bytes_per_step": int(xh.numel() * 4 + qh.numel() * 4),
            "d2h_bytes_per_step": int(out_h.numel() * 4)}
 
-    # per-kernel-family breakdown for the roofline, timed live with CUDA events
-    rl = roofline_breakdown(h, cfg, x, qd, stream)
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    nbytes = algorithmic_bytes(dominant, cfg, N)
+    avg_s = probe_ms * 1e-3 / max(probe_n, 1)
+    achieved = nbytes / avg_s / 1e9 if nbytes else None
+    rl = {"roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                       "frac": achieved / peak if achieved else None, "traffic": None,
+                       "algorithmic_bytes_per_launch": nbytes, "avg_launch_us": avg_s * 1e6,
+                       "launches_timed": probe_n, "peak_source": "measured" if peaks else "fallback"},
+          "stages_ms": {k: round(v, 5) for k, v in breakdown.items()}}
 
     if rank == 0:
-        rl.pop("_launches_per_step", None)
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -220,6 +235,26 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile(args):
+    """The bench workload's steps alone: a short, fixed launch sequence for ncu."""
+    import torch
+    import paper_2204_14167_gb300 as dg
+    from paper_2204_14167_gb300 import presets, synth
+    cfg, rec = presets.wet_channel_128x64x128(dg.MIXED)
+    pos, q, sp = synth.ions(cfg.dims, rec["n_pos"], rec["n_neg"], rec["seed"], rec["ymargin"], rec["min_sep"])
+    h = dg.Discos(cfg)
+    x = torch.tensor(pos, dtype=torch.float32, device="cuda").contiguous()
+    qd = torch.tensor(q, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    n0 = dg.launch_count()
+    h.step(x, qd, step0=0, nsteps=args.warmup)
+    torch.cuda.synchronize()
+    n1 = dg.launch_count()
+    h.step(x, qd, step0=args.warmup, nsteps=args.steps)
+    torch.cuda.synchronize()
+    print(f"profile: {n1 - n0} warm-up launches, {dg.launch_count() - n1} measured launches")
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -227,50 +262,58 @@ def _peaks():
         return None
 
 
-def roofline_breakdown(h, cfg, x, q, stream):
-    """Time each stage of one step through the fine-grained C ABI."""
-    import torch
-    Nx, Ny, Nz = cfg.dims
-    N = x.shape[1]
+def algorithmic_bytes(family, cfg, N):
+    """Bytes one launch of a kernel family must move at minimum (float32 bulk
+    data, float64 factor tables of the low modes ignored), for the workload's
+    sizes.  G = Nx Ny Nz cells, M = (Nx/2+1) Nz transverse modes."""
+    Nx, Ny, Nz = cfg.Nx, cfg.Ny, cfg.Nz
     G = Nx * Ny * Nz
-    stages = {}
-    rho = h.empty_grid("cell")
-    F = torch.empty_like(x)
-    f = h.empty_grid("mac")
+    Gf = Nx * Nz * (3 * Ny + 1)
+    M = (Nx // 2 + 1) * Nz
+    w = 4 if cfg.kernel_hy == 0 else 6
+    we = 4 if cfg.kernel_es == 0 else 6
+    if family == "stokes_y":      # spectra in and out, 4 single-precision factor rows per mode row
+        return M * (2 * (3 * Ny + 1) * 8 + 4 * Ny * 4 + 20)
+    if family == "poisson_y":
+        return M * (2 * Ny * 8 + Ny * 4)
+    if family == "fft_z":         # per launch, averaged over the Poisson (1 field) and Stokes (3 fields) launches
+        return (Nz * Ny * M // Nz * 8 * 2 + Nz * (3 * Ny + 1) * M // Nz * 8 * 2) // 2
+    if family == "fft_x":
+        return (G * 4 + G // Nx * (Nx // 2 + 1) * 8 + Gf * 4 + Gf // Nx * (Nx // 2 + 1) * 8) // 2
+    if family == "noise":
+        return Gf * 4
+    if family == "interp_v":      # 3 components x w^3 face values + position in, velocity out
+        return N * (3 * w ** 3 * 4 + 24)
+    if family == "interp_e":
+        return N * ((we + 1) ** 3 * 4 + 28 + 12)
+    if family == "spread_force":  # zero-fill skipped in the step (noise initialises the grid)
+        return N * (3 * w ** 3 * 4 * 2 + 24)
+    if family == "spread_charge":
+        return G * 4 + N * (we ** 3 * 4 * 2 + 16)
+    if family == "near_field":
+        return N * (16 + 12 + 12)
+    if family == "cell_list":
+        return N * (12 + 4 * 4)
+    if family == "update":
+        return N * (12 * 4)
+    return None
 
-    def timed(name, fn, reps=5):
-        fn()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        stages[name] = a.elapsed_time(b) / reps
 
-    timed("spread_charge", lambda: h.spread_charge(x, q, out=rho))
-    timed("poisson", lambda: h.solve_poisson(rho, out=rho))
-    timed("interp_efield", lambda: h.interpolate_efield(x, rho))
-    timed("near_field", lambda: h.near_field(x, q, F=F, counts=False))
-    timed("spread_force", lambda: h.spread_force(x, F, out=f))
-    timed("stokes", lambda: h.solve_stokes(f, out=f))
-    timed("interp_velocity", lambda: h.interpolate_velocity(x, f))
-    # Poisson solve: algorithmic HBM bytes = rho read (4G) + 5 passes over the
-    # half spectrum (x-FFT write, z-FFT read+write twice, y-solve read+write,
-    # inverse x read) ~ 8 bytes * G/2 * 2 each, phi write (4G), pivots 8G/2
-    peaks = _peaks()
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
-    b_poisson = 4 * G + 4 * G + 6 * (8 * G // 2 * 2) // 2 + 8 * G // 2
-    b_stokes = 2 * 4 * (3 * G + Nx * Nz) + 6 * (8 * 3 * G // 2)
-    dom = max(("poisson", b_poisson), ("stokes", b_stokes), key=lambda kv: stages[kv[0]])
-    t = stages[dom[0]] * 1e-3
-    achieved = dom[1] / t / 1e9
-    return {"stages_ms": stages,
-            "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "peak_source": "measured" if peaks else "fallback"},
-            "_launches_per_step": None}
+def kernel_breakdown(dg, h, x, qd, step0, steps=3):
+    """Per-step time of every kernel family (CUDA events on the launching
+    streams), measured outside the timed region to pick the dominant one."""
+    from paper_2204_14167_gb300 import _lib
+    out = {}
+    step = step0
+    for fam in _lib.PROBE_FAMILIES:
+        dg.probe(h, fam)
+        for _ in range(steps):
+            h.step(x, qd, step0=step, nsteps=1)
+            step += 1
+        t, n = dg.probe_read(h)
+        out[fam] = t / steps
+    dg.probe(h, None)
+    return out, step
 
 
 def main():
@@ -280,8 +323,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only W warm-up steps and K steps of the workload (for ncu), no timing output")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

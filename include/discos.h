@@ -123,6 +123,19 @@ const char* discos_last_error(void);
  * handles, all threads); a diagnostic for launch accounting. */
 long long discos_launch_count(void);
 
+/* Live timing of one kernel family (measurement hook).  discos_probe
+ * synchronises the device, then records a CUDA event pair on the launching
+ * stream around every launch of `family` made through this handle (at most
+ * 4096 launches), -1 switches it off; discos_probe_read waits for the events
+ * and returns the summed duration in ms and the number of launches. */
+enum {
+  DISCOS_PROBE_CELL_LIST = 0, DISCOS_PROBE_NEAR_FIELD, DISCOS_PROBE_NOISE, DISCOS_PROBE_SPREAD_CHARGE,
+  DISCOS_PROBE_FFT_X, DISCOS_PROBE_FFT_Z, DISCOS_PROBE_POISSON_Y, DISCOS_PROBE_INTERP_E,
+  DISCOS_PROBE_SPREAD_FORCE, DISCOS_PROBE_STOKES_Y, DISCOS_PROBE_INTERP_V, DISCOS_PROBE_UPDATE
+};
+discos_status discos_probe(discos_handle* h, int family);
+discos_status discos_probe_read(discos_handle* h, double* total_ms, int* launches);
+
 /* Spreading, Eq. kernel2 with the wall image construction of Sec. II.A
  * (Fig. folded) and Sec. II.B.1.
  * which = DISCOS_SPREAD_CHARGE: val = q[N]; grid = rho[Nz][Ny][Nx] cell

@@ -233,6 +233,23 @@ class Discos:
         return x
 
 
+
+
+def probe(handle, family):
+    """Time every launch of one kernel family ('stokes_y', 'fft_z', ...) with
+    CUDA events on its stream; None switches the probe off."""
+    fam = -1 if family is None else _lib.PROBE_FAMILIES.index(family)
+    _lib.check(handle._lib.discos_probe(handle._h, fam))
+
+
+def probe_read(handle):
+    """(summed milliseconds, number of launches) since the probe was set."""
+    t = ctypes.c_double()
+    n = ctypes.c_int()
+    _lib.check(handle._lib.discos_probe_read(handle._h, ctypes.byref(t), ctypes.byref(n)))
+    return t.value, n.value
+
+
 def fp_table(kernel, psi, n_tab, es_w=6, es_beta=8.0):
     """The library's F^P table (host computation, no GPU needed)."""
     lib = _lib.load()

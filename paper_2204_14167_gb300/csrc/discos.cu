@@ -18,6 +18,27 @@ static thread_local std::string g_err;
 static std::atomic<long long> g_launches{0};
 
 void set_error(const std::string& msg) { g_err = msg; }
+
+// The probe of the handle whose entry point is running on this thread.
+static thread_local Probe* g_cur_probe = nullptr;
+
+void probe_begin(int family, cudaStream_t s) {
+  Probe* p = g_cur_probe;
+  if (p && p->family == family && p->n < Probe::kMax) cudaEventRecord(p->ev[2 * p->n], s);
+}
+
+void probe_end(int family, cudaStream_t s) {
+  Probe* p = g_cur_probe;
+  if (p && p->family == family && p->n < Probe::kMax) {
+    cudaEventRecord(p->ev[2 * p->n + 1], s);
+    ++p->n;
+  }
+}
+
+struct ProbeScope {
+  explicit ProbeScope(discos_handle* h) { g_cur_probe = h ? &h->probe : nullptr; }
+  ~ProbeScope() { g_cur_probe = nullptr; }
+};
 void count_launches(long long n) { g_launches += n; }
 
 discos_status cuda_status(cudaError_t e, const char* where) {
@@ -263,6 +284,41 @@ const char* discos_last_error(void) { return g_err.c_str(); }
 
 long long discos_launch_count(void) { return g_launches.load(); }
 
+discos_status discos_probe(discos_handle* h, int family) {
+  if (!h) return invalid("null handle");
+  if (family < -1 || family >= PROBE_COUNT) return invalid("unknown kernel family");
+  Probe& p = h->probe;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(e, "discos_probe");
+  if (!p.created && family >= 0) {
+    for (int i = 0; i < 2 * Probe::kMax; ++i) {
+      e = cudaEventCreate(&p.ev[i]);
+      if (e != cudaSuccess) return cuda_status(e, "discos_probe");
+    }
+    p.created = true;
+  }
+  p.family = family;
+  p.n = 0;
+  return DISCOS_OK;
+}
+
+discos_status discos_probe_read(discos_handle* h, double* total_ms, int* launches) {
+  if (!h || !total_ms || !launches) return invalid("null argument");
+  Probe& p = h->probe;
+  double tot = 0.0;
+  for (int i = 0; i < p.n; ++i) {
+    cudaError_t e = cudaEventSynchronize(p.ev[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_status(e, "discos_probe_read");
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_status(e, "discos_probe_read");
+    tot += ms;
+  }
+  *total_ms = tot;
+  *launches = p.n;
+  return DISCOS_OK;
+}
+
 discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, discos_free_fn free_fn,
                             void* alloc_ctx, discos_handle** out) {
   if (!cfg || !out) return invalid("null argument");
@@ -472,6 +528,8 @@ discos_status discos_destroy(discos_handle* h) {
   if (h->W.yev1) cudaEventDestroy(h->W.yev1);
   free_workspace(h);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->probe.created)
+    for (int i = 0; i < 2 * Probe::kMax; ++i) cudaEventDestroy(h->probe.ev[i]);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
@@ -480,6 +538,7 @@ discos_status discos_destroy(discos_handle* h) {
 
 discos_status discos_spread(discos_handle* h, const void* x, const void* val, int N, int which, void* grid,
                             void* stream) {
+  ProbeScope probe_scope(h);
   discos_status st = check_n(h, N);
   if (st) return st;
   if (!grid || (N > 0 && (!x || !val))) return invalid("null pointer");
@@ -498,6 +557,7 @@ discos_status discos_spread(discos_handle* h, const void* x, const void* val, in
 }
 
 discos_status discos_solve_poisson(discos_handle* h, const void* rho, void* phi, void* stream) {
+  ProbeScope probe_scope(h);
   if (!h) return invalid("null handle");
   if (!rho || !phi) return invalid("null pointer");
   cudaStream_t s = (cudaStream_t)stream;
@@ -507,6 +567,7 @@ discos_status discos_solve_poisson(discos_handle* h, const void* rho, void* phi,
 }
 
 discos_status discos_solve_stokes(discos_handle* h, const void* f, void* v, void* p, void* stream) {
+  ProbeScope probe_scope(h);
   if (!h) return invalid("null handle");
   if (!f || !v) return invalid("null pointer");
   if (!(h->P.eta > 0.0)) return invalid("eta must be positive");
@@ -519,6 +580,7 @@ discos_status discos_solve_stokes(discos_handle* h, const void* f, void* v, void
 
 discos_status discos_interpolate(discos_handle* h, const void* x, int N, int which, const void* grid, void* out,
                                  void* stream) {
+  ProbeScope probe_scope(h);
   discos_status st = check_n(h, N);
   if (st) return st;
   if (!grid || (N > 0 && (!x || !out))) return invalid("null pointer");
@@ -538,6 +600,7 @@ discos_status discos_interpolate(discos_handle* h, const void* x, int N, int whi
 
 discos_status discos_cell_list(discos_handle* h, const void* x, int N, int* cell_start, int* perm, int* n_cells_out,
                                void* stream) {
+  ProbeScope probe_scope(h);
   discos_status st = check_n(h, N);
   if (st) return st;
   if (N > 0 && !x) return invalid("null pointer");
@@ -554,6 +617,7 @@ discos_status discos_cell_list(discos_handle* h, const void* x, int N, int* cell
 
 discos_status discos_near_field(discos_handle* h, const void* x, const void* q, const int* species, int N, void* F,
                                 int* nbr_count, void* stream) {
+  ProbeScope probe_scope(h);
   discos_status st = check_n(h, N);
   if (st) return st;
   if (N > 0 && (!x || !q || !F)) return invalid("null pointer");
@@ -566,6 +630,7 @@ discos_status discos_near_field(discos_handle* h, const void* x, const void* q, 
 
 discos_status discos_forces(discos_handle* h, const void* x, const void* q, const int* species, int N, void* F,
                             int* nbr_count, void* stream) {
+  ProbeScope probe_scope(h);
   discos_status st = check_n(h, N);
   if (st) return st;
   if (N > 0 && (!x || !q || !F)) return invalid("null pointer");
@@ -576,6 +641,7 @@ discos_status discos_forces(discos_handle* h, const void* x, const void* q, cons
 
 discos_status discos_step(discos_handle* h, void* x, const void* q, const int* species, int N, int64_t step0,
                           int nsteps, void* F_out, void* stream) {
+  ProbeScope probe_scope(h);
   discos_status st = check_n(h, N);
   if (st) return st;
   if (nsteps < 0) return invalid("nsteps must be >= 0");

@@ -33,6 +33,24 @@ struct Params {
   uint64_t seed;
 };
 
+// Kernel families that can be timed live (discos_probe).
+enum ProbeFamily {
+  PROBE_NONE = -1, PROBE_CELL_LIST = 0, PROBE_NEAR_FIELD, PROBE_NOISE, PROBE_SPREAD_CHARGE, PROBE_FFT_X,
+  PROBE_FFT_Z, PROBE_POISSON_Y, PROBE_INTERP_E, PROBE_SPREAD_FORCE, PROBE_STOKES_Y, PROBE_INTERP_V,
+  PROBE_UPDATE, PROBE_COUNT
+};
+
+// CUDA events recorded around every launch of one kernel family.
+struct Probe {
+  int family = PROBE_NONE;
+  static const int kMax = 4096;
+  cudaEvent_t ev[2 * kMax];
+  int n = 0;
+  bool created = false;
+};
+void probe_begin(int family, cudaStream_t s);
+void probe_end(int family, cudaStream_t s);
+
 // Device workspace owned by a handle.
 struct Workspace {
   // grids
@@ -92,6 +110,7 @@ struct discos_handle {
   discos_free_fn free_fn;
   void* alloc_ctx;
   int device;
+  discos::Probe probe;
   cudaStream_t side = nullptr;       // independent work of a step runs here
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };

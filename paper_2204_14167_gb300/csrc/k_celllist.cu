@@ -142,6 +142,7 @@ __global__ void k_sort_cells(const int* __restrict__ start, int n_cells, int* __
 template <typename T>
 cudaError_t launch_cell_list(const Params& P, Workspace& W, const T* x, int N, cudaStream_t s) {
   int n = W.n_cells;
+  probe_begin(PROBE_CELL_LIST, s);
   cudaMemsetAsync(W.counts, 0, sizeof(int) * n, s);
   cudaMemsetAsync(W.fill, 0, sizeof(int) * n, s);
   int bs = 256;
@@ -163,6 +164,7 @@ cudaError_t launch_cell_list(const Params& P, Workspace& W, const T* x, int N, c
   }
   k_sort_cells<<<(n + 255) / 256, 256, 0, s>>>(W.cell_start, n, W.perm);
   count_launches(1);
+  probe_end(PROBE_CELL_LIST, s);
   return cudaGetLastError();
 }
 

@@ -16,33 +16,66 @@ namespace discos {
 namespace {
 
 
-// Radix-2 Stockham auto-sort FFT over `nvec` vectors of length N in shared
+// Stockham auto-sort FFT over `nvec` vectors of length N = 2^logN in shared
 // memory (vector v at in[v * vs .. v * vs + N)), natural order in and out, no
-// bit reversal.  Stage with sub-transform size Ns: butterfly j (< N/2) with
-// k = j mod Ns combines in[j] and in[j + N/2] (twiddle exp(-+2 pi i k / 2Ns))
-// into out[2j - k] and out[2j - k + Ns].  Reads are unit-stride; the two
-// buffers alternate.  Returns the buffer holding the result.  All threads of
-// the block take part; ends with the block synchronised.
+// bit reversal.  Radix-4 stages while they fit, then one radix-2 stage.  A
+// stage with sub-transform size Ns takes butterfly j (< N/R) with
+// k = j mod Ns, inputs in[j + m N/R] (m < R) twiddled by exp(-+2 pi i m k /
+// (R Ns)), and writes the R-point DFT to out[R j - (R-1) k + m Ns].  Reads
+// are unit-stride; the two buffers alternate.  Returns the buffer holding the
+// result.  All threads take part; ends with the block synchronised.
 template <typename T>
 __device__ cplx<T>* fft_stockham(cplx<T>* in, cplx<T>* out, int N, int logN, int nvec, int vs,
                                  const cplx<T>* __restrict__ tw, bool inverse) {
-  const int hN = N >> 1;
-  const int total = nvec * hN;
-  for (int Ns = 1; Ns < N; Ns <<= 1) {
-    const int twstep = N / (2 * Ns);
-    for (int b = threadIdx.x; b < total; b += blockDim.x) {
-      const int v = b >> (logN - 1);
-      const int j = b & (hN - 1);
-      const int k = j & (Ns - 1);
-      cplx<T> wv = tw[k * twstep];
-      if (inverse) wv.im = -wv.im;
-      const cplx<T>* iv = in + (size_t)v * vs;
-      cplx<T>* ov = out + (size_t)v * vs;
-      cplx<T> u = iv[j];
-      cplx<T> t = cmul(wv, iv[j + hN]);
-      const int o = 2 * j - k;
-      ov[o] = cadd(u, t);
-      ov[o + Ns] = csub(u, t);
+  int Ns = 1;
+  while (Ns < N) {
+    if (4 * Ns <= N) {
+      const int q = N >> 2;
+      const int total = nvec * q;
+      const int twstep = N / (4 * Ns);
+      for (int b = threadIdx.x; b < total; b += blockDim.x) {
+        const int v = b / q;
+        const int j = b - v * q;
+        const int k = j & (Ns - 1);
+        cplx<T> w1 = tw[k * twstep], w2 = tw[2 * k * twstep];
+        if (inverse) { w1.im = -w1.im; w2.im = -w2.im; }
+        const cplx<T> w3 = cmul(w1, w2);
+        const cplx<T>* iv = in + (size_t)v * vs;
+        cplx<T>* ov = out + (size_t)v * vs;
+        const cplx<T> a0 = iv[j];
+        const cplx<T> a1 = cmul(w1, iv[j + q]);
+        const cplx<T> a2 = cmul(w2, iv[j + 2 * q]);
+        const cplx<T> a3 = cmul(w3, iv[j + 3 * q]);
+        const cplx<T> b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3);
+        const cplx<T> d = csub(a1, a3);
+        // (a1 - a3) times -i (forward) or +i (inverse)
+        const cplx<T> b3 = inverse ? cplx<T>{-d.im, d.re} : cplx<T>{d.im, -d.re};
+        const int o = 4 * j - 3 * k;
+        ov[o] = cadd(b0, b2);
+        ov[o + Ns] = cadd(b1, b3);
+        ov[o + 2 * Ns] = csub(b0, b2);
+        ov[o + 3 * Ns] = csub(b1, b3);
+      }
+      Ns <<= 2;
+    } else {
+      const int hN = N >> 1;
+      const int total = nvec * hN;
+      const int twstep = N / (2 * Ns);
+      for (int b = threadIdx.x; b < total; b += blockDim.x) {
+        const int v = b >> (logN - 1);
+        const int j = b & (hN - 1);
+        const int k = j & (Ns - 1);
+        cplx<T> wv = tw[k * twstep];
+        if (inverse) wv.im = -wv.im;
+        const cplx<T>* iv = in + (size_t)v * vs;
+        cplx<T>* ov = out + (size_t)v * vs;
+        cplx<T> u = iv[j];
+        cplx<T> t = cmul(wv, iv[j + hN]);
+        const int o = 2 * j - k;
+        ov[o] = cadd(u, t);
+        ov[o + Ns] = csub(u, t);
+      }
+      Ns <<= 1;
     }
     __syncthreads();
     cplx<T>* tmp = in; in = out; out = tmp;
@@ -154,7 +187,8 @@ __global__ void k_fft_z(cplx<T>* __restrict__ data, int Nz, int logNz, int Nyr, 
     bufa[c * vs + z] = v;
   }
   __syncthreads();
-  cplx<T>* r = fft_stockham(bufa, bufb, Nz, logNz, TK, vs, tw, inverse != 0);
+  const int nv = Nxh - kx0 < TK ? Nxh - kx0 : TK;   // the last tile holds fewer columns
+  cplx<T>* r = fft_stockham(bufa, bufb, Nz, logNz, nv, vs, tw, inverse != 0);
   for (int idx = threadIdx.x; idx < TK * Nz; idx += blockDim.x) {
     int z = idx / TK, c = idx - z * TK;
     int kx = kx0 + c;
@@ -170,10 +204,11 @@ int pairs_per_block(int N) {
 
 }  // namespace
 
-// columns per z-transform block: 16, halved while the two buffers exceed 140 KB
+// columns per z-transform block: 8 (small blocks keep the launch within one
+// wave at typical sizes), halved while the two buffers exceed 140 KB
 template <typename T>
 int tile_z(int Nz) {
-  int tk = 16;
+  int tk = 8;
   while (tk > 2 && 2 * (size_t)tk * (Nz + 1) * sizeof(cplx<T>) > 140 * 1024) tk >>= 1;
   return tk;
 }
@@ -196,8 +231,10 @@ cudaError_t fft_x_forward(const Params& P, const T* in, int R, cplx<T>* out, T s
   int pairs = (R + 1) / 2;
   int nb = (pairs + pp - 1) / pp;
   size_t sm = 2 * (size_t)pp * N * sizeof(cplx<T>);
+  probe_begin(PROBE_FFT_X, s);
   k_rfft_x<T><<<nb, 256, sm, s>>>(in, R, N, logN, P.Px, out, scale, Nyr, add0, add1, tw, pp);
   count_launches(1);
+  probe_end(PROBE_FFT_X, s);
   return cudaGetLastError();
 }
 
@@ -209,8 +246,10 @@ cudaError_t fft_x_inverse(const Params& P, const cplx<T>* in, int R, T* out, T s
   int pairs = (R + 1) / 2;
   int nb = (pairs + pp - 1) / pp;
   size_t sm = 2 * (size_t)pp * N * sizeof(cplx<T>);
+  probe_begin(PROBE_FFT_X, s);
   k_irfft_x<T><<<nb, 256, sm, s>>>(in, R, N, logN, P.Px, out, scale, tw, pp);
   count_launches(1);
+  probe_end(PROBE_FFT_X, s);
   return cudaGetLastError();
 }
 
@@ -222,8 +261,10 @@ cudaError_t fft_z(const Params& P, cplx<T>* data, int Nyr, int nfields, size_t f
   size_t sm = 2 * (size_t)TK * (Nz + 1) * sizeof(cplx<T>);
   ensure_fft_z_attr<T>();
   dim3 grid((P.Nxh + TK - 1) / TK, Nyr, nfields);
+  probe_begin(PROBE_FFT_Z, s);
   k_fft_z<T><<<grid, 256, sm, s>>>(data, Nz, logNz, Nyr, P.Px, P.Nxh, inverse ? 1 : 0, tw, field_stride, 0, TK);
   count_launches(1);
+  probe_end(PROBE_FFT_Z, s);
   return cudaGetLastError();
 }
 
@@ -234,8 +275,10 @@ cudaError_t fft_z_mac(const Params& P, cplx<T>* data, bool inverse, const cplx<T
   size_t sm = 2 * (size_t)TK * (Nz + 1) * sizeof(cplx<T>);
   ensure_fft_z_attr<T>();
   dim3 grid((P.Nxh + TK - 1) / TK, P.Ny + 1, 3);
+  probe_begin(PROBE_FFT_Z, s);
   k_fft_z<T><<<grid, 256, sm, s>>>(data, Nz, logNz, P.Ny, P.Px, P.Nxh, inverse ? 1 : 0, tw, 0, 1, TK);
   count_launches(1);
+  probe_end(PROBE_FFT_Z, s);
   return cudaGetLastError();
 }
 

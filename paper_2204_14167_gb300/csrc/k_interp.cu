@@ -160,8 +160,10 @@ cudaError_t launch_interp_efield(const Params& P, const T* x, const T* q, int N,
   if (N <= 0) return cudaSuccess;
   int bs = 256;
   int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
+  probe_begin(PROBE_INTERP_E, s);
   k_interp_efield<T><<<nb, bs, 0, s>>>(x, q, N, P, phi, out, as_force ? 1 : 0, F_add);
   count_launches(1);
+  probe_end(PROBE_INTERP_E, s);
   return cudaGetLastError();
 }
 
@@ -170,8 +172,10 @@ cudaError_t launch_interp_velocity(const Params& P, const T* x, int N, const T* 
   if (N <= 0) return cudaSuccess;
   int bs = 256;
   int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
+  probe_begin(PROBE_INTERP_V, s);
   k_interp_velocity<T><<<nb, bs, 0, s>>>(x, N, P, v, out);
   count_launches(1);
+  probe_end(PROBE_INTERP_V, s);
   return cudaGetLastError();
 }
 

@@ -200,11 +200,13 @@ cudaError_t launch_near_field(const Params& P, Workspace& W, const T* x, const T
   T* qs = reinterpret_cast<T*>(W.qs);
   int bs = 256;
   int nb = (N + bs - 1) / bs;
+  probe_begin(PROBE_NEAR_FIELD, s);
   k_gather<T><<<nb, bs, 0, s>>>(x, q, species, N, W.perm, xs, qs, W.sps);
   count_launches(1);
   k_near_field<T><<<(N + 7) / 8, 256, 0, s>>>(xs, qs, W.sps, W.perm, W.cell_start, N, P,
                                                   reinterpret_cast<const T*>(W.fptab), F, nbr, accumulate ? 1 : 0);
   count_launches(1);
+  probe_end(PROBE_NEAR_FIELD, s);
   return cudaGetLastError();
 }
 

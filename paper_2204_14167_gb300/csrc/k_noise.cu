@@ -82,8 +82,10 @@ template <typename T>
 cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_t s, bool overwrite) {
   dim3 grid((P.Nx + TX - 1) / TX, (P.Ny + TY - 1) / TY, (P.Nz + TZ - 1) / TZ);
   T amp = T(sqrt(2.0 * P.kT * P.eta / P.dt));
+  probe_begin(PROBE_NOISE, s);
   k_stress_noise<T><<<grid, 256, 0, s>>>(f, P, (long long)step, amp, overwrite ? 1 : 0);
   count_launches(1);
+  probe_end(PROBE_NOISE, s);
   return cudaGetLastError();
 }
 

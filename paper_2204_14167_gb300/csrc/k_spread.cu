@@ -146,12 +146,17 @@ cudaError_t launch_fill_zero(T* p, size_t n, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N, T* rho, cudaStream_t s) {
+  probe_begin(PROBE_SPREAD_CHARGE, s);
   cudaError_t e = launch_fill_zero(rho, (size_t)P.Nx * P.Ny * P.Nz, s);
-  if (e != cudaSuccess || N <= 0) return e;
+  if (e != cudaSuccess || N <= 0) {
+    probe_end(PROBE_SPREAD_CHARGE, s);
+    return e;
+  }
   int bs = 256;
   int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
   k_spread_charge<T><<<nb, bs, 0, s>>>(x, q, N, P, rho);
   count_launches(1);
+  probe_end(PROBE_SPREAD_CHARGE, s);
   return cudaGetLastError();
 }
 
@@ -159,12 +164,17 @@ template <typename T>
 cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, T* f, int64_t step, bool rfd,
                                 cudaStream_t s, bool accumulate) {
   size_t n = (size_t)P.Nx * P.Nz * (3 * P.Ny + 1);
+  probe_begin(PROBE_SPREAD_FORCE, s);
   cudaError_t e = accumulate ? cudaSuccess : launch_fill_zero(f, n, s);
-  if (e != cudaSuccess || N <= 0) return e;
+  if (e != cudaSuccess || N <= 0) {
+    probe_end(PROBE_SPREAD_FORCE, s);
+    return e;
+  }
   int bs = 256;
   dim3 grid((unsigned)(((size_t)N * 8 + bs - 1) / bs), 3);
   k_spread_force<T><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0);
   count_launches(1);
+  probe_end(PROBE_SPREAD_FORCE, s);
   return cudaGetLastError();
 }
 

@@ -76,8 +76,10 @@ template <typename T>
 cudaError_t launch_dry_update(const Params& P, T* x, const int* species, const T* F, const T* V, int N,
                               int64_t step, cudaStream_t s) {
   if (N <= 0) return cudaSuccess;
+  probe_begin(PROBE_UPDATE, s);
   k_dry_update<T><<<(N + 127) / 128, 128, 0, s>>>(x, species, F, V, N, P, (long long)step);
   count_launches(1);
+  probe_end(PROBE_UPDATE, s);
   return cudaGetLastError();
 }
 

@@ -481,7 +481,7 @@ cudaError_t stokes_scan_launch(const Params& P, cplx<TS>* S, cplx<TS>* Sp, const
 }  // namespace
 
 template <typename T>
-cudaError_t launch_poisson_y(const Params& P, Workspace& W, cplx<T>* S, cudaStream_t s) {
+cudaError_t launch_poisson_y_impl(const Params& P, Workspace& W, cplx<T>* S, cudaStream_t s) {
   const int M = P.Nxh * P.Nz;
   if constexpr (std::is_same<T, float>::value) {
     // low modes (double) on the side stream, the rest (single) on s
@@ -498,7 +498,15 @@ cudaError_t launch_poisson_y(const Params& P, Workspace& W, cplx<T>* S, cudaStre
 }
 
 template <typename T>
-cudaError_t launch_stokes_y(const Params& P, Workspace& W, cplx<T>* S, cplx<T>* Sp, cudaStream_t s) {
+cudaError_t launch_poisson_y(const Params& P, Workspace& W, cplx<T>* S, cudaStream_t s) {
+  probe_begin(PROBE_POISSON_Y, s);
+  cudaError_t e = launch_poisson_y_impl<T>(P, W, S, s);
+  probe_end(PROBE_POISSON_Y, s);
+  return e;
+}
+
+template <typename T>
+cudaError_t launch_stokes_y_impl(const Params& P, Workspace& W, cplx<T>* S, cplx<T>* Sp, cudaStream_t s) {
   const int M = P.Nxh * P.Nz;
   if constexpr (std::is_same<T, float>::value) {
     cudaError_t e = cudaEventRecord(W.yev0, s);
@@ -516,6 +524,14 @@ cudaError_t launch_stokes_y(const Params& P, Workspace& W, cplx<T>* S, cplx<T>* 
     return stokes_scan_launch<double, double>(P, S, Sp, W.st_l1, W.st_l2, W.st_di, W.st_ci, W.st_mc, nullptr, M,
                                               nullptr, s);
   }
+}
+
+template <typename T>
+cudaError_t launch_stokes_y(const Params& P, Workspace& W, cplx<T>* S, cplx<T>* Sp, cudaStream_t s) {
+  probe_begin(PROBE_STOKES_Y, s);
+  cudaError_t e = launch_stokes_y_impl<T>(P, W, S, Sp, s);
+  probe_end(PROBE_STOKES_Y, s);
+  return e;
 }
 
 template cudaError_t launch_poisson_y<float>(const Params&, Workspace&, cplx<float>*, cudaStream_t);
