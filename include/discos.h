@@ -222,6 +222,34 @@ discos_status discos_forces(discos_handle* h, const void* x, const void* q, cons
 discos_status discos_step(discos_handle* h, void* x, const void* q, const int* species, int N,
                           int64_t step0, int nsteps, void* F_out, void* stream);
 
+/* Discrete electrostatic energy of the particle-mesh problem.  The paper
+ * defines no energy; this is the grid energy of its electrostatic stage
+ * (Sec. II.B.1, Eqs. poisson, esbc1, esbc3):
+ *     U = sum_j rho_j (phi^rho_j / 2 + phi^b_j) = (1/2) sum_j rho_j (phi_j + phi^b_j)
+ * with rho = S^es q (images included, cell volume 1), phi the solution of
+ * Eq. poisson with the wall data, phi^rho its part with homogeneous wall data
+ * and phi^b the discrete lift of the wall data (the solution for rho = 0).
+ * The P3M near-field pair energy is not included.
+ * phi_b: host double[2], the two wall potentials to use in place of
+ *   cfg.phi_b (NULL = cfg.phi_b); Neumann walls ignore theirs.
+ * U: device double[1], overwritten.
+ * Errors: INVALID_ARG for two Neumann walls (no potential is fixed). */
+discos_status discos_energy(discos_handle* h, const void* x, const void* q, int N, const double* phi_b,
+                            double* U, void* stream);
+
+/* Hand-written adjoint of discos_energy: given the upstream scalar dU
+ * (device double[1]), writes
+ *   dx[3][N] = dU * dU/dx_i = dU q_i sum_j phi_j grad w(x_i - r_j)   (gradient-kernel interpolation)
+ *   dq[N]    = dU * dU/dq_i = dU (J^es phi)_i                        (interpolation = adjoint of spreading)
+ *   dphi_b[2] (device double) = dU * sum_j rho_j dphi^b_j / dphi_b,w
+ * using that the discrete Poisson operator is self-adjoint (dU/drho = phi).
+ * rho and phi are recomputed, not stored.  dx, dq are reals (device) and
+ * overwritten; any of dx, dq, dphi_b may be NULL.  phi_b as in discos_energy.
+ * Errors: as discos_energy. */
+discos_status discos_energy_backward(discos_handle* h, const void* x, const void* q, int N,
+                                     const double* phi_b, const double* dU, void* dx, void* dq,
+                                     double* dphi_b, void* stream);
+
 /* Host-only (no GPU needed): the F^P pair-force table that discos_create
  * builds (Sec. II.B.1, Eq. LC), for kernel `kernel` (es_w, es_beta used by
  * DISCOS_KERNEL_ES), f^P(k psi / n_tab) for k = 0..n_tab with l_B = 1 and

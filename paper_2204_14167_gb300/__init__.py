@@ -232,7 +232,33 @@ class Discos:
                                          _ptr(F_out), _stream(stream)))
         return x
 
+    def _phi_b(self, phi_b):
+        if phi_b is None:
+            return None
+        vals = [float(v) for v in (phi_b.tolist() if hasattr(phi_b, "tolist") else phi_b)]
+        assert len(vals) == 2, "phi_b holds the two wall potentials"
+        return (ctypes.c_double * 2)(*vals)
 
+    def energy(self, x, q, phi_b=None, out=None, stream=None):
+        """Discrete electrostatic energy U as a float64 CUDA scalar."""
+        import torch
+        N = self._check_ions(x)
+        U = torch.empty((), dtype=torch.float64, device="cuda") if out is None else out
+        _lib.check(self._lib.discos_energy(self._h, _ptr(x), _ptr(q), N, self._phi_b(phi_b), _ptr(U),
+                                           _stream(stream)))
+        return U
+
+    def energy_backward(self, x, q, dU, phi_b=None, need=(True, True, True), stream=None):
+        """(dx, dq, dphi_b) = dU * gradients of U; entries not in `need` are None."""
+        import torch
+        N = self._check_ions(x)
+        dU = dU.to(device="cuda", dtype=torch.float64).contiguous()
+        dx = torch.empty((3, N), dtype=self.dtype, device="cuda") if need[0] else None
+        dq = torch.empty(N, dtype=self.dtype, device="cuda") if need[1] else None
+        db = torch.empty(2, dtype=torch.float64, device="cuda") if need[2] else None
+        _lib.check(self._lib.discos_energy_backward(self._h, _ptr(x), _ptr(q), N, self._phi_b(phi_b), _ptr(dU),
+                                                    _ptr(dx), _ptr(dq), _ptr(db), _stream(stream)))
+        return dx, dq, db
 
 
 def probe(handle, family):

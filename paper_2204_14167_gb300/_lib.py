@@ -55,7 +55,7 @@ EXPORTS = [
     "discos_create", "discos_destroy", "discos_last_error", "discos_spread", "discos_solve_poisson",
     "discos_solve_stokes", "discos_interpolate", "discos_cell_list", "discos_near_field", "discos_forces",
     "discos_step", "discos_fp_table", "discos_launch_count", "discos_cell_list_noalloc",
-    "discos_probe", "discos_probe_read",
+    "discos_probe", "discos_probe_read", "discos_energy", "discos_energy_backward",
 ]
 PROBE_FAMILIES = ["cell_list", "near_field", "noise", "spread_charge", "fft_x", "fft_z", "poisson_y", "interp_e",
                   "spread_force", "stokes_y", "interp_v", "update"]
@@ -87,6 +87,8 @@ def load():
     lib.discos_fp_table.argtypes = [i32, i32, D, D, i32, ctypes.POINTER(D)]
     lib.discos_probe.argtypes = [vp, i32]
     lib.discos_probe_read.argtypes = [vp, ctypes.POINTER(D), ctypes.POINTER(i32)]
+    lib.discos_energy.argtypes = [vp, vp, vp, i32, ctypes.POINTER(D), vp, vp]
+    lib.discos_energy_backward.argtypes = [vp, vp, vp, i32, ctypes.POINTER(D), vp, vp, vp, vp, vp]
     lib.discos_cell_list_noalloc.argtypes = [ctypes.POINTER(Config), vp, i32, vp, vp, ctypes.POINTER(i32), vp]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int

@@ -187,7 +187,7 @@ void free_workspace(discos_handle* h) {
   void* ptrs[] = {W.phi, W.spec, W.fgrid, W.piv64, W.piv32, W.tw_x, W.tw_z, W.fptab, W.cell_of, W.counts, W.fill,
                   W.cell_start, W.perm, W.tile_sums, W.xs, W.qs, W.sps, W.F, W.xstar, W.V,
                   W.st_l1, W.st_l2, W.st_di, W.st_ci, W.st_mc,
-                  W.lo_modes, W.is_lo, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf, W.Fn};
+                  W.lo_modes, W.is_lo, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf, W.Fn, W.edata};
   for (void* p : ptrs) dfree(h, p);
   W = Workspace{};
 }
@@ -264,6 +264,40 @@ discos_status step_impl(discos_handle* h, T* x, const T* q, const int* species, 
   if (F_out && nsteps > 0)
     return cuda_status(cudaMemcpyAsync(F_out, F, sizeof(T) * 3 * (size_t)N, cudaMemcpyDeviceToDevice, s),
                        "discos_step");
+  return DISCOS_OK;
+}
+
+// Electrostatic energy and its adjoint (k_energy.cu).  rho goes to the
+// force-grid buffer, phi to the potential buffer; both are recomputed by the
+// backward rather than kept from the forward.
+template <typename T>
+discos_status energy_impl(discos_handle* h, const Params& P, const T* x, const T* q, int N, double* U,
+                          const double* dU, T* dx, T* dq, double* dphi_b, cudaStream_t s) {
+  Workspace& W = h->W;
+  T* rho = reinterpret_cast<T*>(W.fgrid);
+  T* phi = reinterpret_cast<T*>(W.phi);
+  double* lift = W.edata;
+  double* sums = W.edata + 3 * P.Ny;
+  const char* where = U ? "discos_energy" : "discos_energy_backward";
+  cudaError_t e = launch_spread_charge<T>(P, x, q, N, rho, s);
+  if (e == cudaSuccess) e = launch_poisson<T>(P, W, rho, phi, s);
+  if (e == cudaSuccess && (U || dphi_b)) e = launch_lift(P, lift, s);
+  if (e == cudaSuccess && (U || dphi_b)) e = launch_energy_sums<T>(P, rho, phi, lift, sums, s);
+  if (e == cudaSuccess && U) e = cudaMemcpyAsync(U, sums, sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && dphi_b) e = launch_scale2(sums, dU, dphi_b, s);
+  if (e == cudaSuccess && (dx || dq)) e = launch_energy_grad<T>(P, x, q, N, phi, dU, dx, dq, s);
+  return cuda_status(e, where);
+}
+
+discos_status energy_args(discos_handle* h, const double* phi_b, Params* P) {
+  if (h->P.bc[0] == DISCOS_BC_NEUMANN && h->P.bc[1] == DISCOS_BC_NEUMANN)
+    return invalid("the energy needs at least one Dirichlet wall (two Neumann walls fix no potential)");
+  *P = h->P;
+  if (phi_b) {
+    if (!std::isfinite(phi_b[0]) || !std::isfinite(phi_b[1])) return invalid("phi_b must be finite");
+    P->phi_b[0] = phi_b[0];
+    P->phi_b[1] = phi_b[1];
+  }
   return DISCOS_OK;
 }
 
@@ -425,6 +459,7 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   W.xstar = dalloc(h, rs * 3 * M, &ok);
   W.V = dalloc(h, rs * 3 * M, &ok);
   W.Fn = dalloc(h, rs * 3 * M, &ok);
+  W.edata = (double*)dalloc(h, sizeof(double) * (3 * (size_t)c.Ny + 4), &ok);
   if (h->mixed) {
     W.is_lo = (unsigned char*)dalloc(h, modes, &ok);
     W.lo_modes = (int*)dalloc(h, sizeof(int) * modes, &ok);
@@ -649,6 +684,37 @@ discos_status discos_step(discos_handle* h, void* x, const void* q, const int* s
   cudaStream_t s = (cudaStream_t)stream;
   return h->mixed ? step_impl<float>(h, (float*)x, (const float*)q, species, N, step0, nsteps, (float*)F_out, s)
                   : step_impl<double>(h, (double*)x, (const double*)q, species, N, step0, nsteps, (double*)F_out, s);
+}
+
+discos_status discos_energy(discos_handle* h, const void* x, const void* q, int N, const double* phi_b, double* U,
+                            void* stream) {
+  ProbeScope probe_scope(h);
+  discos_status st = check_n(h, N);
+  if (st) return st;
+  if (!U || (N > 0 && (!x || !q))) return invalid("null pointer");
+  Params P;
+  if ((st = energy_args(h, phi_b, &P))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  return h->mixed ? energy_impl<float>(h, P, (const float*)x, (const float*)q, N, U, nullptr, nullptr, nullptr,
+                                       nullptr, s)
+                  : energy_impl<double>(h, P, (const double*)x, (const double*)q, N, U, nullptr, nullptr, nullptr,
+                                        nullptr, s);
+}
+
+discos_status discos_energy_backward(discos_handle* h, const void* x, const void* q, int N, const double* phi_b,
+                                     const double* dU, void* dx, void* dq, double* dphi_b, void* stream) {
+  ProbeScope probe_scope(h);
+  discos_status st = check_n(h, N);
+  if (st) return st;
+  if (!dU || (N > 0 && (!x || !q))) return invalid("null pointer");
+  Params P;
+  if ((st = energy_args(h, phi_b, &P))) return st;
+  if (N == 0) { dx = nullptr; dq = nullptr; }
+  cudaStream_t s = (cudaStream_t)stream;
+  return h->mixed ? energy_impl<float>(h, P, (const float*)x, (const float*)q, N, nullptr, dU, (float*)dx,
+                                       (float*)dq, dphi_b, s)
+                  : energy_impl<double>(h, P, (const double*)x, (const double*)q, N, nullptr, dU, (double*)dx,
+                                        (double*)dq, dphi_b, s);
 }
 
 }  // extern "C"

@@ -96,6 +96,7 @@ struct Workspace {
   // the double-precision low modes run on their own stream, beside the rest
   cudaStream_t ystream = nullptr;
   cudaEvent_t yev0 = nullptr, yev1 = nullptr;
+  double* edata = nullptr;      // energy: lift profiles [3][Ny], then 3 sums
   int n_cells = 0;
 };
 
@@ -149,6 +150,12 @@ template <typename T> cudaError_t launch_dry_update(const Params& P, T* x, const
 template <typename T> cudaError_t launch_midpoint(const Params& P, const T* x, const T* V, int N, T* xstar,
                                                   cudaStream_t s);
 template <typename T> cudaError_t launch_fill_zero(T* p, size_t n, cudaStream_t s);
+template <typename T> cudaError_t launch_energy_sums(const Params& P, const T* rho, const T* phi, const double* lift,
+                                                      double* sums, cudaStream_t s);
+template <typename T> cudaError_t launch_energy_grad(const Params& P, const T* x, const T* q, int N, const T* phi,
+                                                      const double* dU, T* dx, T* dq, cudaStream_t s);
+cudaError_t launch_lift(const Params& P, double* lift, cudaStream_t s);
+cudaError_t launch_scale2(const double* sums, const double* dU, double* out, cudaStream_t s);
 template <typename T> cudaError_t launch_poisson_y(const Params& P, Workspace& W, cplx<T>* S, cudaStream_t s);
 template <typename T> cudaError_t launch_stokes_y(const Params& P, Workspace& W, cplx<T>* S, cplx<T>* Sp,
                                                   cudaStream_t s);

@@ -61,7 +61,19 @@ def wet_channel_small(precision=MIXED, Nx=32, Ny=16, Nz=16, n=300):
     return cfg, rec
 
 
+def energy_channel_64(precision=FP64):
+    """64^3 channel between Dirichlet walls at phi = +0.5 and -0.5, 2048 +
+    2048 ions placed uniformly in y in [1, 63], l_B = 7, 6-point kernel:
+    the workload of the differentiable energy (forward U and its adjoint)."""
+    cfg = RunConfig(Nx=64, Ny=64, Nz=64, bc=(BC_DIRICHLET, BC_DIRICHLET), phi_b=(0.5, -0.5),
+                    kernel_es=KERNEL_PESKIN6, kernel_hy=KERNEL_PESKIN6, lB=7.0, dt=0.01, psi=4.0, n_tab=64,
+                    D_tot=[1.0], D_wet=[0.0], gamma_coef=[mobility.gamma_table(1.0, 1.0, 64.0)], wet=False,
+                    precision=precision, max_ions=4096, **_wca(1.0), **_wall())
+    return cfg, dict(n_pos=2048, n_neg=2048, ymargin=1.0, min_sep=0.0, seed=20220501)
+
+
 PRESETS = {
     "dry_channel_32": dry_channel_32,
     "wet_channel_128x64x128": wet_channel_128x64x128,
+    "energy_channel_64": energy_channel_64,
 }
