@@ -222,6 +222,59 @@ discos_status discos_forces(discos_handle* h, const void* x, const void* q, cons
 discos_status discos_step(discos_handle* h, void* x, const void* q, const int* species, int N,
                           int64_t step0, int nsteps, void* F_out, void* stream);
 
+/* Batched replicas: R independent channels that share the handle's
+ * configuration (grid, walls, kernels, physics) and differ in their ions and
+ * wall potentials, advanced together by the dry-diffusion step of Sec. II.D
+ * (forces of Eq. totalforce, update of Eq. ions3).  Each replica is worked
+ * on by one thread block with its whole grid in shared memory; the blocks
+ * take replicas longest first from a device work queue.
+ * Limits: a DISCOS_MIXED handle with Nx = Nz = 32, Ny = 16 or 32, a 4- or
+ * 6-point electrostatic kernel, cfg.wet = 0, at least one Dirichlet wall;
+ * 0..512 ions per replica.
+ * Ion arrays are packed replica after replica: replica r owns the ions
+ * offsets[r] .. offsets[r+1]-1 of x[3][Ntot] (x row, y row, z row, each Ntot
+ * floats), q[Ntot] and species[Ntot]; ion i of replica r is ion
+ * i - offsets[r] of that replica for the Philox noise, keyed (i, step, r, 1).
+ * All device arrays are borrowed and must stay valid until the stream has
+ * finished the call's work. */
+typedef struct discos_batch {
+  int R;                      /* number of replicas, >= 1 */
+  const int* offsets_host;    /* host int[R + 1], offsets[0] = 0, non-decreasing */
+  const int* offsets;         /* device copy of offsets_host */
+  void* x;                    /* device float[3][Ntot], Ntot = offsets[R]; updated in place */
+  const void* q;              /* device float[Ntot] */
+  const int* species;         /* device int[Ntot] or NULL (all species 0) */
+  const double* phi_b;        /* device double[R][2] wall potentials, or NULL (cfg.phi_b for all) */
+  unsigned int* hist;         /* device uint32[R][nspecies][Ny] or NULL: after every step, +1 in
+                                 the y cell of every ion (the equilibrium density profiles) */
+  double* sums;               /* device double[R][4] or NULL: sum q, sum F_x, sum F_y, sum F_z
+                                 over the replica's ions at the last step, accumulated in double */
+  void* F_out;                /* device float[3][Ntot] or NULL: forces of the last step */
+  int* nbr_count;             /* device int[Ntot] or NULL: near-field partners of the last step */
+} discos_batch;
+
+/* Advances every replica by nsteps steps, the first with index step0.  The
+ * launches (one per step, or per steps_per_launch steps, see below) are
+ * replayed from a CUDA graph captured on the first call with the same
+ * arguments.  A call whose offsets differ from the previous call's uploads a
+ * new replica order and waits for that copy (the only host wait).
+ * Errors: INVALID_ARG for the limits above and malformed offsets. */
+discos_status discos_step_batched(discos_handle* h, const discos_batch* b, int64_t step0, int nsteps,
+                                  void* stream);
+
+/* Launch-shape autotuner of the batched step: times every candidate number
+ * of steps per launch (1, 2, 4, 8, 16; more steps per launch keep the ions
+ * in shared memory across steps, fewer give the scheduler finer work units)
+ * on trial_steps steps of a scratch copy of b's positions (b is not
+ * modified), keeps the fastest for later discos_step_batched calls on h and
+ * returns it and its time per step (either out pointer may be NULL).
+ * Blocks until the trials are done. */
+discos_status discos_tune_batched(discos_handle* h, const discos_batch* b, int trial_steps,
+                                  int* steps_per_launch, double* ms_per_step, void* stream);
+
+/* Sets the number of steps per batched launch directly (1..1024). */
+discos_status discos_set_batched_shape(discos_handle* h, int steps_per_launch);
+
 /* Discrete electrostatic energy of the particle-mesh problem.  The paper
  * defines no energy; this is the grid energy of its electrostatic stage
  * (Sec. II.B.1, Eqs. poisson, esbc1, esbc3):

@@ -71,10 +71,11 @@ def dry_increment(p, pos, species, F, step, replica=0, first_index=0):
     return inc
 
 
-def dry_step(p, pos, q, species, step, pair_dtype=np.float64):
-    """One Euler-Maruyama step of the dry-diffusion dynamics."""
+def dry_step(p, pos, q, species, step, pair_dtype=np.float64, replica=0):
+    """One Euler-Maruyama step of the dry-diffusion dynamics (noise of the
+    given replica's Philox stream)."""
     F, counts, parts = forces(p, pos, q, species, pair_dtype)
-    new = wrap_reflect(pos + dry_increment(p, pos, species, F, step), p['dims'])
+    new = wrap_reflect(pos + dry_increment(p, pos, species, F, step, replica), p['dims'])
     return new, F, counts
 
 

@@ -232,6 +232,41 @@ class Discos:
                                          _ptr(F_out), _stream(stream)))
         return x
 
+    # -- batched replicas
+    def make_batch(self, x, q, offsets, species=None, phi_b=None, hist=None, sums=None, F_out=None,
+                   nbr=None):
+        """A discos_batch over packed replicas: x (3, Ntot) float32, q (Ntot,),
+        offsets a host sequence of R + 1 ints.  The returned object keeps the
+        tensors it references alive."""
+        import torch
+        off = [int(v) for v in offsets]
+        R = len(off) - 1
+        b = _lib.Batch()
+        b.R = R
+        b._off_host = (ctypes.c_int * (R + 1))(*off)
+        b._off_dev = torch.tensor(off, dtype=torch.int32, device="cuda")
+        b.offsets_host = ctypes.cast(b._off_host, ctypes.POINTER(ctypes.c_int))
+        b.offsets = b._off_dev.data_ptr()
+        b._keep = (x, q, species, phi_b, hist, sums, F_out, nbr)
+        for name, t in (("x", x), ("q", q), ("species", species), ("phi_b", phi_b), ("hist", hist),
+                        ("sums", sums), ("F_out", F_out), ("nbr_count", nbr)):
+            setattr(b, name, None if t is None else t.data_ptr())
+        return b
+
+    def step_batched(self, batch, step0=0, nsteps=1, stream=None):
+        _lib.check(self._lib.discos_step_batched(self._h, ctypes.byref(batch), int(step0), int(nsteps),
+                                                 _stream(stream)))
+
+    def tune_batched(self, batch, trial_steps=32, stream=None):
+        """Pick the fastest steps per launch; returns (steps_per_launch, ms_per_step)."""
+        s, ms = ctypes.c_int(), ctypes.c_double()
+        _lib.check(self._lib.discos_tune_batched(self._h, ctypes.byref(batch), int(trial_steps), ctypes.byref(s),
+                                                 ctypes.byref(ms), _stream(stream)))
+        return s.value, ms.value
+
+    def set_batched_shape(self, steps_per_launch):
+        _lib.check(self._lib.discos_set_batched_shape(self._h, int(steps_per_launch)))
+
     def _phi_b(self, phi_b):
         if phi_b is None:
             return None

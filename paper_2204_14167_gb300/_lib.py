@@ -51,11 +51,29 @@ class Config(ctypes.Structure):
     ]
 
 
+class Batch(ctypes.Structure):
+    """discos_batch (include/discos.h)."""
+    _fields_ = [
+        ("R", ctypes.c_int),
+        ("offsets_host", ctypes.POINTER(ctypes.c_int)),
+        ("offsets", ctypes.c_void_p),
+        ("x", ctypes.c_void_p),
+        ("q", ctypes.c_void_p),
+        ("species", ctypes.c_void_p),
+        ("phi_b", ctypes.c_void_p),
+        ("hist", ctypes.c_void_p),
+        ("sums", ctypes.c_void_p),
+        ("F_out", ctypes.c_void_p),
+        ("nbr_count", ctypes.c_void_p),
+    ]
+
+
 EXPORTS = [
     "discos_create", "discos_destroy", "discos_last_error", "discos_spread", "discos_solve_poisson",
     "discos_solve_stokes", "discos_interpolate", "discos_cell_list", "discos_near_field", "discos_forces",
     "discos_step", "discos_fp_table", "discos_launch_count", "discos_cell_list_noalloc",
     "discos_probe", "discos_probe_read", "discos_energy", "discos_energy_backward",
+    "discos_step_batched", "discos_tune_batched", "discos_set_batched_shape",
 ]
 PROBE_FAMILIES = ["cell_list", "near_field", "noise", "spread_charge", "fft_x", "fft_z", "poisson_y", "interp_e",
                   "spread_force", "stokes_y", "interp_v", "update"]
@@ -89,6 +107,9 @@ def load():
     lib.discos_probe_read.argtypes = [vp, ctypes.POINTER(D), ctypes.POINTER(i32)]
     lib.discos_energy.argtypes = [vp, vp, vp, i32, ctypes.POINTER(D), vp, vp]
     lib.discos_energy_backward.argtypes = [vp, vp, vp, i32, ctypes.POINTER(D), vp, vp, vp, vp, vp]
+    lib.discos_step_batched.argtypes = [vp, ctypes.POINTER(Batch), i64, i32, vp]
+    lib.discos_tune_batched.argtypes = [vp, ctypes.POINTER(Batch), i32, ctypes.POINTER(i32), ctypes.POINTER(D), vp]
+    lib.discos_set_batched_shape.argtypes = [vp, i32]
     lib.discos_cell_list_noalloc.argtypes = [ctypes.POINTER(Config), vp, i32, vp, vp, ctypes.POINTER(i32), vp]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int

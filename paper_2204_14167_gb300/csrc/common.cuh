@@ -39,7 +39,19 @@ struct KernelParams {
   double alpha;  // ES: w / 2
   double beta;   // ES: beta
   double inv_norm;  // ES: 1 / int exp(beta (sqrt(1 - (z/alpha)^2) - 1)) dz
+  double inv_alpha;
+  // single-precision copies, so that float kernels convert nothing at run time
+  float alpha_f, beta_f, inv_norm_f, inv_alpha_f;
 };
+__host__ __device__ __forceinline__ double kp_beta(const KernelParams& kp, double) { return kp.beta; }
+__host__ __device__ __forceinline__ float kp_beta(const KernelParams& kp, float) { return kp.beta_f; }
+__host__ __device__ __forceinline__ double kp_inv_norm(const KernelParams& kp, double) { return kp.inv_norm; }
+__host__ __device__ __forceinline__ float kp_inv_norm(const KernelParams& kp, float) { return kp.inv_norm_f; }
+__host__ __device__ __forceinline__ double kp_inv_alpha(const KernelParams& kp, double) { return kp.inv_alpha; }
+__host__ __device__ __forceinline__ float kp_inv_alpha(const KernelParams& kp, float) { return kp.inv_alpha_f; }
+
+// Second moment of the 6-point kernel, 59/60 - sqrt(29)/20.
+#define PESKIN6_K (59.0 / 60.0 - 5.385164807134504 / 20.0)
 
 // 4-point Peskin kernel, App. B Eq. peskin1d (grid spacing 1).
 template <typename T> __host__ __device__ __forceinline__ T peskin4(T z) {
@@ -59,36 +71,37 @@ template <typename T> __host__ __device__ __forceinline__ T peskin4(T z) {
 // p = phi(r), with p the root of the quadratic sum-of-squares condition.
 template <typename T> __host__ __device__ __forceinline__ T peskin6_p(T r, T K) {
   T r2 = r * r, r3 = r2 * r, r4 = r2 * r2, r5 = r4 * r, r6 = r3 * r3;
-  T B = -(T(84) * K * r - T(66) * K + T(28) * r3 - T(66) * r2 - T(88) * r + T(183)) / T(24);
+  T B = -(T(84) * K * r - T(66) * K + T(28) * r3 - T(66) * r2 - T(88) * r + T(183)) * T(1.0 / 24.0);
   T disc = -(T(1008) * K * K * r2 - T(1008) * K * K * r - T(108) * K * K + T(672) * K * r4 -
              T(1344) * K * r3 - T(1896) * K * r2 + T(2568) * K * r + T(324) * K + T(112) * r6 -
-             T(336) * r5 - T(500) * r4 + T(1560) * r3 + T(748) * r2 - T(1584) * r - T(243)) / T(192);
-  return (-B + sqrt(disc > T(0) ? disc : T(0))) / T(14);
+             T(336) * r5 - T(500) * r4 + T(1560) * r3 + T(748) * r2 - T(1584) * r - T(243)) * T(1.0 / 192.0);
+  return (-B + sqrt(disc > T(0) ? disc : T(0))) * T(1.0 / 14.0);
 }
 template <typename T> __host__ __device__ __forceinline__ T peskin6(T z) {
   if (!(fabs(z) < T(3))) return T(0);
-  const T K = T(59.0 / 60.0) - sqrt(T(29)) / T(20);
+  const T K = T(PESKIN6_K);
   T fl = floor(z);
   T r = z - fl;
   int m = -(int)fl;
   T p = peskin6_p(r, K);
   T r2 = r * r, r3 = r2 * r;
   switch (m) {
-    case -2: return -K * r / 4 + K / 4 + p / 2 - r3 / 12 + r2 / 4 + r / 12 - T(0.375);
-    case -1: return K * r / 2 - T(3) * K / 8 - T(1.5) * p + r3 / 6 - T(3) * r2 / 8 - T(2) * r / 3 + T(19.0 / 16.0);
+    case -2: return -K * r * T(0.25) + K * T(0.25) + p * T(0.5) - r3 * T(1.0 / 12.0) + r2 * T(0.25) + r * T(1.0 / 12.0) - T(0.375);
+    case -1: return K * r * T(0.5) - T(0.375) * K - T(1.5) * p + r3 * T(1.0 / 6.0) - T(0.375) * r2 - r * T(2.0 / 3.0) + T(19.0 / 16.0);
     case 0: return p;
-    case 1: return -K * r / 2 + K / 4 + p - r3 / 6 + r2 / 4 + T(2) * r / 3 - T(0.375);
-    case 2: return K * r / 4 - K / 4 - T(1.5) * p + r3 / 12 - r2 / 4 - r / 12 + T(0.875);
-    case 3: return K / 8 + p / 2 + r2 / 8 - T(5.0 / 16.0);
+    case 1: return -K * r * T(0.5) + K * T(0.25) + p - r3 * T(1.0 / 6.0) + r2 * T(0.25) + r * T(2.0 / 3.0) - T(0.375);
+    case 2: return K * r * T(0.25) - K * T(0.25) - T(1.5) * p + r3 * T(1.0 / 12.0) - r2 * T(0.25) - r * T(1.0 / 12.0) + T(0.875);
+    case 3: return K * T(0.125) + p * T(0.5) + r2 * T(0.125) - T(5.0 / 16.0);
   }
   return T(0);
 }
 
 // ES kernel, App. B Eq. eskernel.
 template <typename T> __host__ __device__ __forceinline__ T eskernel(T z, const KernelParams& kp) {
-  T t = T(1) - (z / T(kp.alpha)) * (z / T(kp.alpha));
+  const T za = z * kp_inv_alpha(kp, T());
+  T t = T(1) - za * za;
   if (t < T(0)) return T(0);
-  return exp(T(kp.beta) * (sqrt(t) - T(1))) * T(kp.inv_norm);
+  return exp(kp_beta(kp, T()) * (sqrt(t) - T(1))) * kp_inv_norm(kp, T());
 }
 
 template <typename T> __host__ __device__ __forceinline__ T kval(T z, const KernelParams& kp) {
@@ -114,36 +127,37 @@ template <typename T> __device__ __forceinline__ T peskin4_d(T z) {
 }
 template <typename T> __device__ __forceinline__ T peskin6_d(T z) {
   if (!(fabs(z) < T(3))) return T(0);
-  const T K = T(59.0 / 60.0) - sqrt(T(29)) / T(20);
+  const T K = T(PESKIN6_K);
   T fl = floor(z);
   T r = z - fl;
   int m = -(int)fl;
   T r2 = r * r, r3 = r2 * r, r4 = r2 * r2, r5 = r4 * r, r6 = r3 * r3;
   T disc = -(T(1008) * K * K * r2 - T(1008) * K * K * r - T(108) * K * K + T(672) * K * r4 -
              T(1344) * K * r3 - T(1896) * K * r2 + T(2568) * K * r + T(324) * K + T(112) * r6 -
-             T(336) * r5 - T(500) * r4 + T(1560) * r3 + T(748) * r2 - T(1584) * r - T(243)) / T(192);
-  T Bp = -(T(84) * K + T(84) * r2 - T(132) * r - T(88)) / T(24);
+             T(336) * r5 - T(500) * r4 + T(1560) * r3 + T(748) * r2 - T(1584) * r - T(243)) * T(1.0 / 192.0);
+  T Bp = -(T(84) * K + T(84) * r2 - T(132) * r - T(88)) * T(1.0 / 24.0);
   T dd = -(T(2016) * K * K * r - T(1008) * K * K + T(2688) * K * r3 - T(4032) * K * r2 -
            T(3792) * K * r + T(2568) * K + T(672) * r5 - T(1680) * r4 - T(2000) * r3 +
-           T(4680) * r2 + T(1496) * r - T(1584)) / T(192);
+           T(4680) * r2 + T(1496) * r - T(1584)) * T(1.0 / 192.0);
   T sq = sqrt(disc > T(0) ? disc : T(0));
-  T pp = (-Bp + dd / (T(2) * sq)) / T(14);
+  T pp = (-Bp + dd / (T(2) * sq)) * T(1.0 / 14.0);
   switch (m) {
-    case -2: return (-K / 4 - r2 / 4 + r / 2 + T(1.0 / 12.0)) + T(0.5) * pp;
-    case -1: return (K / 2 + r2 / 2 - T(0.75) * r - T(2.0 / 3.0)) - T(1.5) * pp;
+    case -2: return (-K * T(0.25) - r2 * T(0.25) + r * T(0.5) + T(1.0 / 12.0)) + T(0.5) * pp;
+    case -1: return (K * T(0.5) + r2 * T(0.5) - T(0.75) * r - T(2.0 / 3.0)) - T(1.5) * pp;
     case 0: return pp;
-    case 1: return (-K / 2 - r2 / 2 + r / 2 + T(2.0 / 3.0)) + pp;
-    case 2: return (K / 4 + r2 / 4 - r / 2 - T(1.0 / 12.0)) - T(1.5) * pp;
-    case 3: return r / 4 + T(0.5) * pp;
+    case 1: return (-K * T(0.5) - r2 * T(0.5) + r * T(0.5) + T(2.0 / 3.0)) + pp;
+    case 2: return (K * T(0.25) + r2 * T(0.25) - r * T(0.5) - T(1.0 / 12.0)) - T(1.5) * pp;
+    case 3: return r * T(0.25) + T(0.5) * pp;
   }
   return T(0);
 }
 template <typename T> __device__ __forceinline__ T eskernel_d(T z, const KernelParams& kp) {
-  T al = T(kp.alpha);
-  T t = T(1) - (z / al) * (z / al);
+  const T ia = kp_inv_alpha(kp, T()), be = kp_beta(kp, T());
+  const T za = z * ia;
+  T t = T(1) - za * za;
   if (t <= T(0)) return T(0);
   T s = sqrt(t);
-  return exp(T(kp.beta) * (s - T(1))) * T(kp.inv_norm) * T(kp.beta) * (-z / (al * al)) / s;
+  return exp(be * (s - T(1))) * kp_inv_norm(kp, T()) * be * (-za * ia) / s;
 }
 template <typename T> __device__ __forceinline__ T kder(T z, const KernelParams& kp) {
   if (kp.kind == KP4) return peskin4_d(z);

@@ -47,48 +47,9 @@ discos_status cuda_status(cudaError_t e, const char* where) {
   return DISCOS_ERR_CUDA;
 }
 
-namespace {
-
-bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
-
-int kernel_width(int kind, int es_w) {
-  if (kind == DISCOS_KERNEL_PESKIN4) return 4;
-  if (kind == DISCOS_KERNEL_PESKIN6) return 6;
-  if (kind == DISCOS_KERNEL_ES) return es_w;
-  return -1;
-}
-
 discos_status invalid(const std::string& m) {
   set_error(m);
   return DISCOS_ERR_INVALID_ARG;
-}
-
-KernelParams make_kernel(int kind, int es_w, double es_beta) {
-  KernelParams kp{};
-  kp.kind = kind;
-  kp.w = kernel_width(kind, es_w);
-  if (kind == DISCOS_KERNEL_ES) {
-    kp.alpha = 0.5 * es_w;
-    kp.beta = es_beta;
-    kp.inv_norm = 1.0 / es_normalisation(es_w, es_beta);
-  }
-  return kp;
-}
-
-// The F^P table depends only on the kernel, psi and n_tab: computed once per
-// process for each combination.
-std::vector<double> cached_fp_table(const KernelParams& kp, double psi, int n_tab) {
-  static std::mutex mu;
-  static std::map<std::tuple<int, int, double, double, int>, std::vector<double>> cache;
-  auto key = std::make_tuple(kp.kind, kp.w, kp.beta, psi, n_tab);
-  std::lock_guard<std::mutex> lock(mu);
-  auto it = cache.find(key);
-  if (it != cache.end()) return it->second;
-  std::vector<double> tab(n_tab + 1);
-  std::string err;
-  build_fp_table(kp, psi, n_tab, tab.data(), &err);
-  cache[key] = tab;
-  return tab;
 }
 
 void* dalloc(discos_handle* h, size_t bytes, bool* ok) {
@@ -107,6 +68,50 @@ void dfree(discos_handle* h, void* p) {
   if (!p) return;
   if (h->free_fn) h->free_fn(p, h->alloc_ctx);
   else cudaFree(p);
+}
+
+namespace {
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int kernel_width(int kind, int es_w) {
+  if (kind == DISCOS_KERNEL_PESKIN4) return 4;
+  if (kind == DISCOS_KERNEL_PESKIN6) return 6;
+  if (kind == DISCOS_KERNEL_ES) return es_w;
+  return -1;
+}
+
+KernelParams make_kernel(int kind, int es_w, double es_beta) {
+  KernelParams kp{};
+  kp.kind = kind;
+  kp.w = kernel_width(kind, es_w);
+  if (kind == DISCOS_KERNEL_ES) {
+    kp.alpha = 0.5 * es_w;
+    kp.beta = es_beta;
+    kp.inv_norm = 1.0 / es_normalisation(es_w, es_beta);
+    kp.inv_alpha = 1.0 / kp.alpha;
+  }
+  kp.alpha_f = (float)kp.alpha;
+  kp.beta_f = (float)kp.beta;
+  kp.inv_norm_f = (float)kp.inv_norm;
+  kp.inv_alpha_f = (float)kp.inv_alpha;
+  return kp;
+}
+
+// The F^P table depends only on the kernel, psi and n_tab: computed once per
+// process for each combination.
+std::vector<double> cached_fp_table(const KernelParams& kp, double psi, int n_tab) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, double, double, int>, std::vector<double>> cache;
+  auto key = std::make_tuple(kp.kind, kp.w, kp.beta, psi, n_tab);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  std::vector<double> tab(n_tab + 1);
+  std::string err;
+  build_fp_table(kp, psi, n_tab, tab.data(), &err);
+  cache[key] = tab;
+  return tab;
 }
 
 template <typename T>
@@ -183,6 +188,7 @@ void upload_stokes_factors(discos_handle* h) {
 }
 
 void free_workspace(discos_handle* h) {
+  free_batch(h);
   Workspace& W = h->W;
   void* ptrs[] = {W.phi, W.spec, W.fgrid, W.piv64, W.piv32, W.tw_x, W.tw_z, W.fptab, W.cell_of, W.counts, W.fill,
                   W.cell_start, W.perm, W.tile_sums, W.xs, W.qs, W.sps, W.F, W.xstar, W.V,
@@ -297,6 +303,8 @@ discos_status energy_args(discos_handle* h, const double* phi_b, Params* P) {
     if (!std::isfinite(phi_b[0]) || !std::isfinite(phi_b[1])) return invalid("phi_b must be finite");
     P->phi_b[0] = phi_b[0];
     P->phi_b[1] = phi_b[1];
+    P->f.phi_b[0] = (float)phi_b[0];
+    P->f.phi_b[1] = (float)phi_b[1];
   }
   return DISCOS_OK;
 }
@@ -423,6 +431,39 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   }
   P.wall_type = c.wall_type;
   for (int d = 0; d < 3; ++d) P.E_ext[d] = c.E_ext[d];
+  P.inv_kT = 1.0 / c.kT;
+  {
+    PhysF& f = P.f;
+    for (int a = 0; a < DISCOS_MAX_SPECIES; ++a) {
+      P.inv_D_dry[a] = P.D_dry[a] != 0.0 ? 1.0 / P.D_dry[a] : 0.0;
+      f.D_tot[a] = (float)P.D_tot[a];
+      f.D_wet[a] = (float)P.D_wet[a];
+      f.D_dry[a] = (float)P.D_dry[a];
+      f.inv_D_dry[a] = (float)P.inv_D_dry[a];
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+          for (int k = 0; k < 7; ++k) f.gamma[a][i][j][k] = (float)P.gamma[a][i][j][k];
+      for (int b = 0; b < DISCOS_MAX_SPECIES; ++b) {
+        f.lj_sigma[a][b] = (float)P.lj_sigma[a][b];
+        f.lj_xi[a][b] = (float)P.lj_xi[a][b];
+        f.lj_rc[a][b] = (float)P.lj_rc[a][b];
+      }
+      f.wall_sigma[a] = (float)P.wall_sigma[a];
+      f.wall_xi[a] = (float)P.wall_xi[a];
+      f.wall_rc[a] = (float)P.wall_rc[a];
+    }
+    for (int d = 0; d < 3; ++d) f.E_ext[d] = (float)P.E_ext[d];
+    for (int w = 0; w < 2; ++w) {
+      f.slope[w] = (float)P.slope[w];
+      f.phi_b[w] = (float)P.phi_b[w];
+    }
+    f.dt = (float)P.dt;
+    f.kT = (float)P.kT;
+    f.inv_kT = (float)P.inv_kT;
+    f.lB = (float)P.lB;
+    f.psi = (float)P.psi;
+    f.tab_scale = (float)P.tab_scale;
+  }
   P.k_cell = k;
   P.ncx = c.Nx / k; P.ncy = std::max(1, c.Ny / k); P.ncz = c.Nz / k;
   P.drift = c.drift;

@@ -3,10 +3,26 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 #include "../../include/discos.h"
 #include "common.cuh"
 
 namespace discos {
+
+// Single-precision copies of the physics constants: float kernels read these
+// (through phys()), so that they convert nothing from double at run time --
+// on this GPU a conversion from double runs on the slow double pipe.
+struct PhysF {
+  float D_tot[DISCOS_MAX_SPECIES], D_wet[DISCOS_MAX_SPECIES], D_dry[DISCOS_MAX_SPECIES];
+  float inv_D_dry[DISCOS_MAX_SPECIES];
+  float gamma[DISCOS_MAX_SPECIES][2][2][7];
+  float lj_sigma[DISCOS_MAX_SPECIES][DISCOS_MAX_SPECIES];
+  float lj_xi[DISCOS_MAX_SPECIES][DISCOS_MAX_SPECIES];
+  float lj_rc[DISCOS_MAX_SPECIES][DISCOS_MAX_SPECIES];
+  float wall_sigma[DISCOS_MAX_SPECIES], wall_xi[DISCOS_MAX_SPECIES], wall_rc[DISCOS_MAX_SPECIES];
+  float E_ext[3], slope[2], phi_b[2];
+  float dt, kT, inv_kT, lB, psi, tab_scale;
+};
 
 // Everything a kernel needs to know about the run, passed by value.
 struct Params {
@@ -31,7 +47,13 @@ struct Params {
   int k_cell, ncx, ncy, ncz;
   int drift;
   uint64_t seed;
+  double inv_D_dry[DISCOS_MAX_SPECIES], inv_kT;
+  PhysF f;
 };
+
+// The physics constants in the arithmetic type of the caller.
+__host__ __device__ __forceinline__ const Params& phys(const Params& P, double) { return P; }
+__host__ __device__ __forceinline__ const PhysF& phys(const Params& P, float) { return P.f; }
 
 // Kernel families that can be timed live (discos_probe).
 enum ProbeFamily {
@@ -100,6 +122,49 @@ struct Workspace {
   int n_cells = 0;
 };
 
+// Arguments of the batched step kernel (k_batched.cu), passed by value.
+struct BatchArgs {
+  int R, Ntot, steps, n_cells, n_lo, n_hi;
+  const int* offsets;          // [R + 1]
+  const int* order;            // [R] replicas by descending ion count
+  float* x;                    // [3][Ntot]
+  const float* q;              // [Ntot]
+  const int* species;          // [Ntot] or null
+  const double* phi_b;         // [R][2] or null
+  unsigned* hist;              // [R][nspecies][Ny] or null
+  double* sums;                // [R][4] or null
+  float* F_out;                // [3][Ntot] or null
+  int* nbr;                    // [Ntot] or null
+  int* queue;                  // work counter, finished-CTA counter
+  long long* dstep;            // step index of the next launch
+  const float* piv32;          // Poisson pivots [M][Ny] (complex-mode index)
+  const double* piv64;
+  const short* modes;          // Hartley modes kz * 32 + kx: n_lo low modes, then n_hi
+  const float* fptab;
+};
+
+// State of the batched path, set up on first use.
+struct BatchState {
+  int* order = nullptr;
+  int order_cap = 0;
+  std::vector<int> offsets_seen;
+  int* queue = nullptr;
+  long long* dstep = nullptr;
+  short* modes = nullptr;
+  int n_lo = 0, n_hi = 0;
+  int nsm = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<unsigned char> exec_key;
+  int steps_per_launch = 1;     // launch shape (discos_tune_batched)
+};
+
+size_t batched_smem_bytes(int Ny, int n_cells, int n_tab);
+bool batched_supported(const Params& P);
+cudaError_t batched_prepare(const Params& P, int n_cells);
+cudaError_t launch_batched_reset(int* queue, long long* dstep, long long step0, cudaStream_t s);
+cudaError_t launch_batched_step(const Params& P, const BatchArgs& B, int grid, cudaStream_t s);
+
 }  // namespace discos
 
 struct discos_handle {
@@ -114,11 +179,16 @@ struct discos_handle {
   discos::Probe probe;
   cudaStream_t side = nullptr;       // independent work of a step runs here
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  discos::BatchState* batch = nullptr;   // batched replicas (batch_api.cu)
 };
 
 namespace discos {
 
 void set_error(const std::string& msg);
+discos_status invalid(const std::string& m);
+void* dalloc(discos_handle* h, size_t bytes, bool* ok);
+void dfree(discos_handle* h, void* p);
+void free_batch(discos_handle* h);
 // Number of kernels this library has launched since it was loaded.
 void count_launches(long long n);
 discos_status cuda_status(cudaError_t e, const char* where);

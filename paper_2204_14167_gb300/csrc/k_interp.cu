@@ -33,14 +33,14 @@ __device__ __forceinline__ T phi_ghost(const T* __restrict__ phi, const Params& 
     int m = -1 - iy;
     m = m < Ny ? m : Ny - 1;   // only reached by ions far outside the channel
     T v = phi[((size_t)iz * Ny + m) * Nx + ix];
-    if (P.bc[0] == DISCOS_BC_DIRICHLET) return T(2.0 * P.phi_b[0]) - v;
-    return v - T(P.slope[0]) * T(2 * m + 1);
+    if (P.bc[0] == DISCOS_BC_DIRICHLET) return T(2) * T(phys(P, T()).phi_b[0]) - v;
+    return v - T(phys(P, T()).slope[0]) * T(2 * m + 1);
   }
   int m = iy - Ny;
   m = m < Ny ? m : Ny - 1;
   T v = phi[((size_t)iz * Ny + (Ny - 1 - m)) * Nx + ix];
-  if (P.bc[1] == DISCOS_BC_DIRICHLET) return T(2.0 * P.phi_b[1]) - v;
-  return v + T(P.slope[1]) * T(2 * m + 1);
+  if (P.bc[1] == DISCOS_BC_DIRICHLET) return T(2) * T(phys(P, T()).phi_b[1]) - v;
+  return v + T(phys(P, T()).slope[1]) * T(2 * m + 1);
 }
 
 template <typename T>
@@ -91,9 +91,10 @@ __global__ void k_interp_efield(const T* __restrict__ x, const T* __restrict__ q
     if (as_force) {
       T qq = q[ion];
       T a0 = F_add ? F_add[ion] : T(0), a1 = F_add ? F_add[N + ion] : T(0), a2 = F_add ? F_add[2 * N + ion] : T(0);
-      out[ion] = qq * (Ex + T(P.E_ext[0])) + a0;
-      out[N + ion] = qq * (Ey + T(P.E_ext[1])) + a1;
-      out[2 * N + ion] = qq * (Ez + T(P.E_ext[2])) + a2;
+      const auto& Q = phys(P, T());
+      out[ion] = qq * (Ex + T(Q.E_ext[0])) + a0;
+      out[N + ion] = qq * (Ey + T(Q.E_ext[1])) + a1;
+      out[2 * N + ion] = qq * (Ez + T(Q.E_ext[2])) + a2;
     } else {
       out[ion] = Ex; out[N + ion] = Ey; out[2 * N + ion] = Ez;
     }

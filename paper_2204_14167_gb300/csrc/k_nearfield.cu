@@ -12,18 +12,11 @@
 // neighbour counts are reproducible bit for bit.  Image partners of ion i
 // can only sit in the list-cell row next to the wall, because a list cell is
 // at least psi wide.
-#include "internal.h"
+#include "physics.cuh"
 
 namespace discos {
 
 namespace {
-
-template <typename T>
-__device__ __forceinline__ int cell_coord(T v, int k, int nc) {
-  int c = (int)floor(v);
-  c = c < 0 ? 0 : c / k;
-  return c < nc ? c : nc - 1;
-}
 
 template <typename T>
 __global__ void k_gather(const T* __restrict__ x, const T* __restrict__ q, const int* __restrict__ species, int N,
@@ -36,56 +29,6 @@ __global__ void k_gather(const T* __restrict__ x, const T* __restrict__ q, const
   xs[2 * N + s] = x[2 * N + i];
   qs[s] = q[i];
   sps[s] = species ? species[i] : 0;
-}
-
-template <typename T>
-__device__ __forceinline__ T min_image(T d, T L, T half) {
-  if (d > half) return sub_rn(d, L);
-  if (d < -half) return add_rn(d, L);
-  return d;
-}
-
-template <typename T>
-__device__ __forceinline__ T fp_lookup(const T* __restrict__ tab, int n_tab, T scale, T r) {
-  T t = r * scale;
-  int k = (int)t;
-  if (k > n_tab - 1) k = n_tab - 1;
-  T fr = t - T(k);
-  T a = tab[k], b = tab[k + 1];
-  return a + fr * (b - a);
-}
-
-template <typename T>
-__device__ __forceinline__ void pair_terms(const T xi, const T yi, const T zi, const T qi, const int si,
-                                           const T xj, const T yj, const T zj, const T qj, const int sj,
-                                           bool real, const Params& P, const T* __restrict__ tab, T Lx, T hx,
-                                           T Lz, T hz, T psi2, T lB, T scale, T& fx, T& fy, T& fz, int& cnt) {
-  T ddx = min_image(sub_rn(xi, xj), Lx, hx);
-  T ddy = sub_rn(yi, yj);
-  T ddz = min_image(sub_rn(zi, zj), Lz, hz);
-  T r2 = add_rn(add_rn(mul_rn(ddx, ddx), mul_rn(ddy, ddy)), mul_rn(ddz, ddz));
-  bool in_psi = r2 < psi2;
-  bool in_lj = false;
-  T rcl = T(0);
-  if (real) {
-    rcl = T(P.lj_rc[si][sj]);
-    in_lj = r2 < mul_rn(rcl, rcl);
-  }
-  if (!(in_psi || in_lj)) return;
-  T r = sqrt(r2);
-  T coef = T(0);
-  if (in_psi) {
-    coef += lB * qi * qj * (T(1) / r2 - fp_lookup(tab, P.n_tab, scale, r));
-    ++cnt;
-  }
-  if (in_lj) {
-    T sg = T(P.lj_sigma[si][sj]);
-    T sr2 = sg * sg / r2;
-    T sr6 = sr2 * sr2 * sr2;
-    coef += T(24) * T(P.lj_xi[si][sj]) / r * (T(2) * sr6 * sr6 - sr6);
-  }
-  T cr = coef / r;
-  fx += cr * ddx; fy += cr * ddy; fz += cr * ddz;
 }
 
 // One warp per ion (cell order).  Lanes 0..26 take the 27 neighbour cells;
@@ -156,25 +99,7 @@ __global__ void k_near_field(const T* __restrict__ xs, const T* __restrict__ qs,
     cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   }
   if (lane != 0) return;
-  // short-range wall force (Sec. II.B.2): 12-6 repulsion or the 9-3 form of Eq. LJ93
-  {
-    const T rc = T(P.wall_rc[si]), sg = T(P.wall_sigma[si]), xiw = T(P.wall_xi[si]);
-    for (int wall = 0; wall < 2; ++wall) {
-      T d = wall == 0 ? yi : sub_rn(T(P.Ny), yi);
-      if (!(d < rc)) continue;
-      T f;
-      if (P.wall_type == DISCOS_WALL_WCA) {
-        T sr2 = sg * sg / (d * d);
-        T sr6 = sr2 * sr2 * sr2;
-        f = T(24) * xiw / d * (T(2) * sr6 * sr6 - sr6);
-      } else {
-        T s3 = sg * sg * sg;
-        T d2 = d * d, d4 = d2 * d2;
-        f = T(1.5) * sqrt(T(3)) * xiw * (T(9) * s3 * s3 * s3 / (d4 * d4 * d2) - T(3) * s3 / d4);
-      }
-      fy += wall == 0 ? f : -f;
-    }
-  }
+  fy += wall_force_y(P, si, yi);
   const int i = perm[s];
   if (accumulate) {
     F[i] += fx;

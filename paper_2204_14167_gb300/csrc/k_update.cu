@@ -7,20 +7,11 @@
 //  * plus, on the wet path, dt J(x*) v (Eq. step2);
 //  * the midpoint predictor x* = x + dt/2 J(x) v of Eq. step1.
 // Positions are wrapped in x, z and reflected specularly at the walls.
-#include "internal.h"
+#include "physics.cuh"
 
 namespace discos {
 
 namespace {
-
-template <typename T>
-__device__ __forceinline__ void fit_gamma(const double* c, T yt, T& g, T& dg) {
-  T a3 = T(c[2]) + yt, a5 = T(c[4]) + yt, a7 = T(c[6]) + yt;
-  T i3 = T(1) / a3, i5 = T(1) / a5, i7 = T(1) / a7;
-  T i5_2 = i5 * i5, i7_2 = i7 * i7;
-  g = T(c[0]) + T(c[1]) * i3 + T(c[3]) * i5_2 * i5 + T(c[5]) * i7_2 * i7_2 * i7;
-  dg = -T(c[1]) * i3 * i3 - T(3) * T(c[3]) * i5_2 * i5_2 - T(5) * T(c[5]) * i7_2 * i7_2 * i7_2;
-}
 
 template <typename T>
 __global__ void k_dry_update(T* __restrict__ x, const int* __restrict__ species, const T* __restrict__ F,
@@ -29,38 +20,15 @@ __global__ void k_dry_update(T* __restrict__ x, const int* __restrict__ species,
   if (i >= N) return;
   const int sp = species ? species[i] : 0;
   T p[3] = {x[i], x[N + i], x[2 * N + i]};
-  const T Ny = T(P.Ny);
-  const T y = p[1];
-  const T yt = y <= Ny - y ? y : Ny - y;
-  const T side = y <= Ny - y ? T(1) : T(-1);
-  const T Dt = T(P.D_tot[sp]), Dw = T(P.D_wet[sp]), Dd = T(P.D_dry[sp]);
-  T Gam[2], dGam[2];
-  for (int dir = 0; dir < 2; ++dir) {
-    T gt, dgt, gw, dgw;
-    fit_gamma(P.gamma[sp][dir][0], yt, gt, dgt);
-    fit_gamma(P.gamma[sp][dir][1], yt, gw, dgw);
-    Gam[dir] = (gt * Dt - gw * Dw) / Dd;
-    dGam[dir] = (dgt * Dt - dgw * Dw) / Dd * side;
-  }
   T W[4];
   normals4(u32x4{(uint32_t)i, (uint32_t)step, 0u, (uint32_t)TAG_DRY}, P.seed, W);
-  const T dt = T(P.dt), kT = T(P.kT);
-  const int L[3] = {P.Nx, P.Ny, P.Nz};
-  for (int d = 0; d < 3; ++d) {
-    T G = d == 1 ? Gam[1] : Gam[0];
-    T inc = dt * (Dd * G * F[(size_t)d * N + i] / kT);
-    if (d == 1 && P.drift) inc += dt * Dd * dGam[1];
-    inc += sqrt(T(2) * dt * Dd * (G > T(0) ? G : T(0))) * W[d];
-    if (V) inc = dt * V[(size_t)d * N + i] + inc;
-    T v = p[d] + inc;
-    if (d == 1) {
-      v = v < T(0) ? -v : (v > Ny ? T(2) * Ny - v : v);
-    } else {
-      T Ld = T(L[d]);
-      v = v < T(0) ? v + Ld : (v >= Ld ? v - Ld : v);
-    }
-    x[(size_t)d * N + i] = v;
-  }
+  const T f[3] = {F[i], F[N + i], F[2 * N + i]};
+  T v[3] = {T(0), T(0), T(0)};
+  if (V) { v[0] = V[i]; v[1] = V[N + i]; v[2] = V[2 * N + i]; }
+  dry_move(P, sp, p, f, V ? v : nullptr, W);
+  x[i] = p[0];
+  x[N + i] = p[1];
+  x[2 * N + i] = p[2];
 }
 
 template <typename T>

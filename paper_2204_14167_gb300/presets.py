@@ -72,6 +72,29 @@ def energy_channel_64(precision=FP64):
     return cfg, dict(n_pos=2048, n_neg=2048, ymargin=1.0, min_sep=0.0, seed=20220501)
 
 
+def batched_channels_32(R=512, precision=MIXED, seed=20220502):
+    """R independent replicas of dry_channel_32's channel (Dirichlet phi = 0
+    walls, l_B = 7, 6-point kernel, dt = 0.01), replica r holding an even,
+    charge-neutral number of ions drawn uniformly in [64, 512]."""
+    import numpy as np
+    cfg, rec = dry_channel_32(precision)
+    cfg.max_ions = 512
+    counts = 2 * np.random.default_rng(seed).integers(32, 257, size=R)
+    return cfg, dict(rec, counts=[int(c) for c in counts], seed=seed)
+
+
+def batched_ions(cfg, rec):
+    """Packed ions of a batched preset: (pos (3, Ntot), q, species, offsets)."""
+    import numpy as np
+    from . import synth
+    pos, q, sp, off = [], [], [], [0]
+    for r, n in enumerate(rec["counts"]):
+        p_, q_, s_ = synth.ions(cfg.dims, n // 2, n - n // 2, rec["seed"] + 1 + r, rec["ymargin"], rec["min_sep"])
+        pos.append(p_); q.append(q_); sp.append(s_)
+        off.append(off[-1] + n)
+    return np.concatenate(pos, axis=1), np.concatenate(q), np.concatenate(sp), off
+
+
 PRESETS = {
     "dry_channel_32": dry_channel_32,
     "wet_channel_128x64x128": wet_channel_128x64x128,
