@@ -228,11 +228,111 @@ def run_ours(args):
                            "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{ws}"},
                 "clocks": clocks, "e2e": e2e, "roofline": rl.get("roofline"), "stages_ms": rl.get("stages_ms"),
                 "gpu_launches": int(n_launches)}
+        if not args.no_forms and ws == 1:
+            line["production_forms"] = production_forms()
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def production_forms(steps=20):
+    """The production forms beside the plain path, each on its own workload:
+    the FP64 single-channel path on the same channel (the plain baseline, and
+    the force difference between the two precisions), batched replicas against
+    the plain single-channel path stepping the same replicas one by one, and
+    the differentiable energy (forward + hand-written backward)."""
+    import numpy as np
+    import torch
+    import paper_2204_14167_gb300 as dg
+    from paper_2204_14167_gb300 import presets, synth
+    from paper_2204_14167_gb300.autograd import energy as denergy
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    # plain FP64 against MIXED on the 128 x 64 x 128 wet channel
+    cfg, rec = presets.wet_channel_128x64x128(dg.FP64)
+    pos, q, sp = synth.ions(cfg.dims, rec["n_pos"], rec["n_neg"], rec["seed"], rec["ymargin"], rec["min_sep"])
+    N = pos.shape[1]
+    h64 = dg.Discos(cfg)
+    x64 = torch.tensor(pos, dtype=torch.float64, device="cuda")
+    q64 = torch.tensor(q, dtype=torch.float64, device="cuda")
+    cfgm, _ = presets.wet_channel_128x64x128(dg.MIXED)
+    hm = dg.Discos(cfgm)
+    xm, qm = x64.float().contiguous(), q64.float()
+    F64 = h64.forces(x64, q64)
+    Fm = hm.forces(xm, qm).double()
+    err = float(torch.linalg.norm(Fm - F64) / torch.linalg.norm(F64))
+    st = [0]
+
+    def step64():
+        h64.step(x64, q64, step0=st[0], nsteps=1)
+        st[0] += 1
+    step64()
+    ms64 = timed(step64, max(steps // 2, 3))
+    out["plain_fp64_wet_channel_128x64x128"] = {"ion_steps_per_s": N / (ms64 * 1e-3), "ms_per_step": ms64,
+                                                "mixed_vs_fp64_force_rel_l2": err}
+    del h64, hm, x64, q64, xm, qm
+    # batched replicas: 512 channels of 32^3, 64..512 ions each
+    cfgb, recb = presets.batched_channels_32()
+    posb, qb, spb, off = presets.batched_ions(cfgb, recb)
+    hb = dg.Discos(cfgb)
+    xb = torch.tensor(posb, dtype=torch.float32, device="cuda").contiguous()
+    qbd = torch.tensor(qb, dtype=torch.float32, device="cuda")
+    R = len(off) - 1
+    hist = torch.zeros((R, 1, cfgb.Ny), dtype=torch.int32, device="cuda")
+    sums = torch.zeros((R, 4), dtype=torch.float64, device="cuda")
+    b = hb.make_batch(xb, qbd, off, hist=hist, sums=sums)
+    spl, _ = hb.tune_batched(b, trial_steps=32)
+    K = 64
+    bst = [0]
+
+    def bstep():
+        hb.step_batched(b, step0=bst[0], nsteps=K)
+        bst[0] += K
+    bstep()
+    msb = timed(bstep, 2) / K
+    # the same replicas through the single-channel path, one replica at a time
+    nrep = 8
+    xs = [xb[:, off[r]:off[r + 1]].contiguous() for r in range(nrep)]
+    qs = [qbd[off[r]:off[r + 1]].contiguous() for r in range(nrep)]
+
+    def plain_reps():
+        for r in range(nrep):
+            hb.step(xs[r], qs[r], step0=0, nsteps=1)
+    plain_reps()
+    msp = timed(plain_reps, 5)
+    ions_sub = off[nrep]
+    out["batched_replicas_512x32^3"] = {
+        "ion_steps_per_s": off[-1] / (msb * 1e-3), "ms_per_step": msb, "ions": off[-1], "replicas": R,
+        "steps_per_launch": spl, "graph": True,
+        "plain_single_channel_ion_steps_per_s": ions_sub / (msp * 1e-3)}
+    del hb, xb, qbd, b
+    # differentiable energy on 64^3 with 4096 ions
+    cfge, rece = presets.energy_channel_64(dg.FP64)
+    pose, qe, _ = synth.ions(cfge.dims, rece["n_pos"], rece["n_neg"], rece["seed"], rece["ymargin"], rece["min_sep"])
+    he = dg.Discos(cfge)
+    xe = torch.tensor(pose, dtype=torch.float64, device="cuda").requires_grad_(True)
+    qe_ = torch.tensor(qe, dtype=torch.float64, device="cuda").requires_grad_(True)
+    pb = torch.tensor(cfge.phi_b, dtype=torch.float64, requires_grad=True)
+
+    def fb():
+        U = denergy(he, xe, qe_, pb)
+        U.backward()
+    fb()
+    mse = timed(fb, 10)
+    out["energy_forward_backward_64^3_fp64"] = {"ms_per_call": mse, "ions": int(pose.shape[1])}
+    return out
 
 
 def run_profile(args):
@@ -323,6 +423,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the production-form measurements")
     ap.add_argument("--profile", action="store_true",
                     help="only W warm-up steps and K steps of the workload (for ncu), no timing output")
     args = ap.parse_args()

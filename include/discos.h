@@ -60,6 +60,7 @@ enum { DISCOS_SPREAD_CHARGE = 0, DISCOS_SPREAD_FORCE = 1 };
 enum { DISCOS_INTERP_EFIELD = 0, DISCOS_INTERP_VELOCITY = 1 };
 
 #define DISCOS_MAX_SPECIES 4
+#define DISCOS_MAX_REFINE 4
 
 /* Run configuration.  Citations are to the paper's sections and equations. */
 typedef struct discos_config {
@@ -91,7 +92,8 @@ typedef struct discos_config {
   double wall_rc[DISCOS_MAX_SPECIES];
   double E_ext[3];         /* applied uniform field: F_ext = q E_ext (Eq. totalforce) */
   int precision;           /* DISCOS_FP64 or DISCOS_MIXED */
-  int max_refine;          /* mixed precision: residual refinement sweeps of the Poisson solve */
+  int max_refine;          /* DISCOS_MIXED: sweeps (0..DISCOS_MAX_REFINE) of residual refinement of every
+                              Poisson solve: r = 4 pi lB rho + lap_h phi in double, phi += A^-1 r */
   int wet;                 /* 1: hydrodynamic stage (Stokes + midpoint); 0: dry diffusion only */
   int drift;               /* 1: stochastic drift terms on (RFD + midpoint, div D^dry) */
   int max_ions;            /* capacity of the per-ion workspace */
@@ -302,6 +304,13 @@ discos_status discos_energy(discos_handle* h, const void* x, const void* q, int 
 discos_status discos_energy_backward(discos_handle* h, const void* x, const void* q, int N,
                                      const double* phi_b, const double* dU, void* dx, void* dq,
                                      double* dphi_b, void* stream);
+
+/* Relative residuals ||b - A phi|| / ||b|| (double) of the most recent
+ * Poisson solve of a DISCOS_MIXED handle created with max_refine > 0: rel[0]
+ * after the single-precision solve, rel[k] after k refinement sweeps
+ * (n = max_refine + 1 values written to the host array rel).  Waits for
+ * `stream`.  Other handles return n = 0. */
+discos_status discos_refine_history(discos_handle* h, double* rel, int* n, void* stream);
 
 /* Host-only (no GPU needed): the F^P pair-force table that discos_create
  * builds (Sec. II.B.1, Eq. LC), for kernel `kernel` (es_w, es_beta used by

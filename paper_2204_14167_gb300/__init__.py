@@ -232,6 +232,13 @@ class Discos:
                                          _ptr(F_out), _stream(stream)))
         return x
 
+    def refine_history(self, stream=None):
+        """Relative residuals of the last Poisson solve: [after the solve, after sweep 1, ...]."""
+        buf = (ctypes.c_double * 8)()
+        n = ctypes.c_int()
+        _lib.check(self._lib.discos_refine_history(self._h, buf, ctypes.byref(n), _stream(stream)))
+        return [buf[i] for i in range(n.value)]
+
     # -- batched replicas
     def make_batch(self, x, q, offsets, species=None, phi_b=None, hist=None, sums=None, F_out=None,
                    nbr=None):

@@ -193,7 +193,7 @@ void free_workspace(discos_handle* h) {
   void* ptrs[] = {W.phi, W.spec, W.fgrid, W.piv64, W.piv32, W.tw_x, W.tw_z, W.fptab, W.cell_of, W.counts, W.fill,
                   W.cell_start, W.perm, W.tile_sums, W.xs, W.qs, W.sps, W.F, W.xstar, W.V,
                   W.st_l1, W.st_l2, W.st_di, W.st_ci, W.st_mc,
-                  W.lo_modes, W.is_lo, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf, W.Fn, W.edata};
+                  W.lo_modes, W.is_lo, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf, W.Fn, W.edata, W.rref, W.rres, W.rnorm};
   for (void* p : ptrs) dfree(h, p);
   W = Workspace{};
 }
@@ -377,6 +377,7 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   if (wes > c.Ny - 2 || why > c.Ny - 2) return invalid("kernel wider than the channel");
   if (!(c.psi > 0.0) || c.n_tab < 2) return invalid("psi > 0 and n_tab >= 2 required");
   if (c.nspecies < 1 || c.nspecies > DISCOS_MAX_SPECIES) return invalid("nspecies must be 1..4");
+  if (c.max_refine < 0 || c.max_refine > DISCOS_MAX_REFINE) return invalid("max_refine must be 0..DISCOS_MAX_REFINE");
   if (c.max_ions < 1) return invalid("max_ions must be positive");
   if (c.precision != DISCOS_FP64 && c.precision != DISCOS_MIXED) return invalid("bad precision");
   if (!(c.dt > 0.0) || c.kT < 0.0) return invalid("dt > 0 and kT >= 0 required");
@@ -432,6 +433,7 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   P.wall_type = c.wall_type;
   for (int d = 0; d < 3; ++d) P.E_ext[d] = c.E_ext[d];
   P.inv_kT = 1.0 / c.kT;
+  P.max_refine = c.precision == DISCOS_MIXED ? c.max_refine : 0;
   {
     PhysF& f = P.f;
     for (int a = 0; a < DISCOS_MAX_SPECIES; ++a) {
@@ -501,6 +503,11 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   W.V = dalloc(h, rs * 3 * M, &ok);
   W.Fn = dalloc(h, rs * 3 * M, &ok);
   W.edata = (double*)dalloc(h, sizeof(double) * (3 * (size_t)c.Ny + 4), &ok);
+  if (h->mixed && c.max_refine > 0) {
+    W.rref = dalloc(h, rs * G, &ok);
+    W.rres = dalloc(h, rs * G, &ok);
+    W.rnorm = (double*)dalloc(h, sizeof(double) * 2 * (DISCOS_MAX_REFINE + 1), &ok);
+  }
   if (h->mixed) {
     W.is_lo = (unsigned char*)dalloc(h, modes, &ok);
     W.lo_modes = (int*)dalloc(h, sizeof(int) * modes, &ok);
@@ -756,6 +763,21 @@ discos_status discos_energy_backward(discos_handle* h, const void* x, const void
                                        (float*)dq, dphi_b, s)
                   : energy_impl<double>(h, P, (const double*)x, (const double*)q, N, nullptr, dU, (double*)dx,
                                         (double*)dq, dphi_b, s);
+}
+
+discos_status discos_refine_history(discos_handle* h, double* rel, int* n, void* stream) {
+  if (!h || !rel || !n) return invalid("null pointer");
+  *n = 0;
+  if (!h->W.rnorm) return DISCOS_OK;
+  const int m = h->P.max_refine + 1;
+  double buf[2 * (DISCOS_MAX_REFINE + 1)];
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(buf, h->W.rnorm, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e, "discos_refine_history");
+  for (int i = 0; i < m; ++i) rel[i] = buf[2 * i + 1] > 0.0 ? std::sqrt(buf[2 * i] / buf[2 * i + 1]) : 0.0;
+  *n = m;
+  return DISCOS_OK;
 }
 
 }  // extern "C"

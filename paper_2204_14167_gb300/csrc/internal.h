@@ -47,6 +47,7 @@ struct Params {
   int k_cell, ncx, ncy, ncz;
   int drift;
   uint64_t seed;
+  int max_refine;              // residual refinement sweeps of the mixed Poisson solve
   double inv_D_dry[DISCOS_MAX_SPECIES], inv_kT;
   PhysF f;
 };
@@ -119,6 +120,9 @@ struct Workspace {
   cudaStream_t ystream = nullptr;
   cudaEvent_t yev0 = nullptr, yev1 = nullptr;
   double* edata = nullptr;      // energy: lift profiles [3][Ny], then 3 sums
+  void* rref = nullptr;         // refinement (mixed, max_refine > 0): rho kept for the residual
+  void* rres = nullptr;         //   residual, then correction
+  double* rnorm = nullptr;      //   (|r|^2, |b|^2) before each sweep and after the last
   int n_cells = 0;
 };
 
@@ -226,6 +230,9 @@ template <typename T> cudaError_t launch_energy_grad(const Params& P, const T* x
                                                       const double* dU, T* dx, T* dq, cudaStream_t s);
 cudaError_t launch_lift(const Params& P, double* lift, cudaStream_t s);
 cudaError_t launch_scale2(const double* sums, const double* dU, double* out, cudaStream_t s);
+template <typename T> cudaError_t launch_poisson_residual(const Params& P, const T* rho, const T* phi, T* res,
+                                                           double* norms, cudaStream_t s);
+template <typename T> cudaError_t launch_add_inplace(T* a, const T* b, size_t n, cudaStream_t s);
 template <typename T> cudaError_t launch_poisson_y(const Params& P, Workspace& W, cplx<T>* S, cudaStream_t s);
 template <typename T> cudaError_t launch_stokes_y(const Params& P, Workspace& W, cplx<T>* S, cplx<T>* Sp,
                                                   cudaStream_t s);

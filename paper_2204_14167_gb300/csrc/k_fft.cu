@@ -282,17 +282,16 @@ cudaError_t fft_z_mac(const Params& P, cplx<T>* data, bool inverse, const cplx<T
   return cudaGetLastError();
 }
 
+// One transform-solve-transform pass: phi = A^-1 (scale rho + wall terms)
+// with the ghost-cell terms add0 / add1 on the wall rows.
 template <typename T>
-cudaError_t launch_poisson(const Params& P, Workspace& W, const T* rho, T* phi, cudaStream_t s) {
+cudaError_t poisson_pass(const Params& P, Workspace& W, const T* rho, T* phi, T scale, T add0, T add1,
+                         cudaStream_t s) {
   const int Ny = P.Ny, Nz = P.Nz;
   cplx<T>* S = reinterpret_cast<cplx<T>*>(W.spec);
   const cplx<T>* twx = reinterpret_cast<const cplx<T>*>(W.tw_x);
   const cplx<T>* twz = reinterpret_cast<const cplx<T>*>(W.tw_z);
-  const double fourpi_lB = 4.0 * M_PI * P.lB;
-  // ghost-cell terms of the wall rows (Eqs. esbc1, esbc3)
-  T add0 = P.bc[0] == DISCOS_BC_DIRICHLET ? T(2.0 * P.phi_b[0]) : T(-P.slope[0]);
-  T add1 = P.bc[1] == DISCOS_BC_DIRICHLET ? T(2.0 * P.phi_b[1]) : T(P.slope[1]);
-  cudaError_t e = fft_x_forward<T>(P, rho, Nz * Ny, S, T(fourpi_lB), Ny, add0, add1, twx, s);
+  cudaError_t e = fft_x_forward<T>(P, rho, Nz * Ny, S, scale, Ny, add0, add1, twx, s);
   if (e != cudaSuccess) return e;
   e = fft_z<T>(P, S, Ny, 1, 0, false, twz, s);
   if (e != cudaSuccess) return e;
@@ -301,6 +300,31 @@ cudaError_t launch_poisson(const Params& P, Workspace& W, const T* rho, T* phi, 
   e = fft_z<T>(P, S, Ny, 1, 0, true, twz, s);
   if (e != cudaSuccess) return e;
   return fft_x_inverse<T>(P, S, Nz * Ny, phi, T(1), twx, s);
+}
+
+template <typename T>
+cudaError_t launch_poisson(const Params& P, Workspace& W, const T* rho, T* phi, cudaStream_t s) {
+  const double fourpi_lB = 4.0 * M_PI * P.lB;
+  // ghost-cell terms of the wall rows (Eqs. esbc1, esbc3)
+  const T add0 = P.bc[0] == DISCOS_BC_DIRICHLET ? T(2.0 * P.phi_b[0]) : T(-P.slope[0]);
+  const T add1 = P.bc[1] == DISCOS_BC_DIRICHLET ? T(2.0 * P.phi_b[1]) : T(P.slope[1]);
+  const int sweeps = (sizeof(T) == sizeof(float) && W.rref) ? P.max_refine : 0;
+  if (sweeps == 0) return poisson_pass<T>(P, W, rho, phi, T(fourpi_lB), add0, add1, s);
+  // mixed precision with residual refinement: keep rho (phi may alias it),
+  // solve, then correct with the double-precision residual (k_refine.cu)
+  const size_t G = (size_t)P.Nx * P.Ny * P.Nz;
+  T* rho_keep = reinterpret_cast<T*>(W.rref);
+  T* res = reinterpret_cast<T*>(W.rres);
+  cudaError_t e = cudaMemcpyAsync(rho_keep, rho, sizeof(T) * G, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = launch_fill_zero<double>(W.rnorm, 2 * (DISCOS_MAX_REFINE + 1), s);
+  if (e == cudaSuccess) e = poisson_pass<T>(P, W, rho_keep, phi, T(fourpi_lB), add0, add1, s);
+  for (int it = 0; it < sweeps && e == cudaSuccess; ++it) {
+    e = launch_poisson_residual<T>(P, rho_keep, phi, res, W.rnorm + 2 * it, s);
+    if (e == cudaSuccess) e = poisson_pass<T>(P, W, res, res, T(1), T(0), T(0), s);
+    if (e == cudaSuccess) e = launch_add_inplace<T>(phi, res, G, s);
+  }
+  if (e == cudaSuccess) e = launch_poisson_residual<T>(P, rho_keep, phi, nullptr, W.rnorm + 2 * sweeps, s);
+  return e;
 }
 
 template cudaError_t launch_poisson<float>(const Params&, Workspace&, const float*, float*, cudaStream_t);
