@@ -305,6 +305,25 @@ discos_status discos_energy_backward(discos_handle* h, const void* x, const void
                                      const double* phi_b, const double* dU, void* dx, void* dq,
                                      double* dphi_b, void* stream);
 
+/* The device fault word.  Kernels that move ions set bit 0 when a new
+ * position is not finite and bit 1 when an ion ends outside the channel (a
+ * displacement larger than the channel); neither stops the kernels, whose
+ * indexing stays in bounds for any position.  discos_step copies the word to
+ * the host behind its steps, and the next discos_step call returns
+ * DISCOS_ERR_DEVICE_FAULT, before enqueueing anything, once that copy shows a
+ * set bit.  discos_fault returns the word (sync != 0: read now, waiting for
+ * `stream`; else the last copy that has arrived, 0 if none) and with
+ * clear != 0 resets it. */
+discos_status discos_fault(discos_handle* h, int sync, int clear, unsigned* word, void* stream);
+
+/* Reductions in double over the ions (and the grid): out[8] (device doubles)
+ * = {sum q_i, dV sum_j rho_j (with_rho != 0: the charge is spread again, wall
+ * images folded in; else 0), sum F_x, sum F_y, sum F_z (F[3][N] may be NULL),
+ * count of non-finite positions, count of ions outside the channel, 0}.
+ * Neutrality (Sec. II.B.1) is sum q + the surface charges times Nx Nz. */
+discos_status discos_diagnostics(discos_handle* h, const void* x, const void* q, const void* F, int N,
+                                 int with_rho, double* out, void* stream);
+
 /* Relative residuals ||b - A phi|| / ||b|| (double) of the most recent
  * Poisson solve of a DISCOS_MIXED handle created with max_refine > 0: rel[0]
  * after the single-precision solve, rel[k] after k refinement sweeps

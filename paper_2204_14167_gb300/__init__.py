@@ -232,6 +232,22 @@ class Discos:
                                          _ptr(F_out), _stream(stream)))
         return x
 
+    def fault(self, sync=True, clear=False, stream=None):
+        """The device fault word (bit 0 non-finite position, bit 1 escaped ion)."""
+        w = ctypes.c_uint()
+        _lib.check(self._lib.discos_fault(self._h, int(sync), int(clear), ctypes.byref(w), _stream(stream)))
+        return w.value
+
+    def diagnostics(self, x, q, F=None, with_rho=True, stream=None):
+        """Double-precision sums: dict(sum_q, sum_rho, sum_F, nonfinite, escaped)."""
+        import torch
+        N = self._check_ions(x)
+        out = torch.zeros(8, dtype=torch.float64, device="cuda")
+        _lib.check(self._lib.discos_diagnostics(self._h, _ptr(x), _ptr(q), _ptr(F), N, int(bool(with_rho)),
+                                                _ptr(out), _stream(stream)))
+        o = out.cpu().tolist()
+        return dict(sum_q=o[0], sum_rho=o[1], sum_F=o[2:5], nonfinite=int(o[5]), escaped=int(o[6]))
+
     def refine_history(self, stream=None):
         """Relative residuals of the last Poisson solve: [after the solve, after sweep 1, ...]."""
         buf = (ctypes.c_double * 8)()

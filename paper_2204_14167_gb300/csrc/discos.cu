@@ -193,7 +193,8 @@ void free_workspace(discos_handle* h) {
   void* ptrs[] = {W.phi, W.spec, W.fgrid, W.piv64, W.piv32, W.tw_x, W.tw_z, W.fptab, W.cell_of, W.counts, W.fill,
                   W.cell_start, W.perm, W.tile_sums, W.xs, W.qs, W.sps, W.F, W.xstar, W.V,
                   W.st_l1, W.st_l2, W.st_di, W.st_ci, W.st_mc,
-                  W.lo_modes, W.is_lo, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf, W.Fn, W.edata, W.rref, W.rres, W.rnorm};
+                  W.lo_modes, W.is_lo, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf, W.Fn, W.edata, W.rref, W.rres, W.rnorm,
+                  W.fault, W.diag};
   for (void* p : ptrs) dfree(h, p);
   W = Workspace{};
 }
@@ -267,10 +268,13 @@ discos_status step_impl(discos_handle* h, T* x, const T* q, const int* species, 
     }
     if (e != cudaSuccess) return cuda_status(e, "discos_step");
   }
-  if (F_out && nsteps > 0)
-    return cuda_status(cudaMemcpyAsync(F_out, F, sizeof(T) * 3 * (size_t)N, cudaMemcpyDeviceToDevice, s),
-                       "discos_step");
-  return DISCOS_OK;
+  cudaError_t e = cudaSuccess;
+  if (F_out && nsteps > 0) e = cudaMemcpyAsync(F_out, F, sizeof(T) * 3 * (size_t)N, cudaMemcpyDeviceToDevice, s);
+  // the fault word travels to the host behind the steps; the next call reads it
+  if (e == cudaSuccess && nsteps > 0)
+    e = cudaMemcpyAsync(h->fault_host, W.fault, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && nsteps > 0) e = cudaEventRecord(h->ev_fault, s);
+  return cuda_status(e, "discos_step");
 }
 
 // Electrostatic energy and its adjoint (k_energy.cu).  rho goes to the
@@ -503,6 +507,8 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   W.V = dalloc(h, rs * 3 * M, &ok);
   W.Fn = dalloc(h, rs * 3 * M, &ok);
   W.edata = (double*)dalloc(h, sizeof(double) * (3 * (size_t)c.Ny + 4), &ok);
+  W.fault = (unsigned*)dalloc(h, sizeof(unsigned), &ok);
+  W.diag = (double*)dalloc(h, 8 * sizeof(double), &ok);
   if (h->mixed && c.max_refine > 0) {
     W.rref = dalloc(h, rs * G, &ok);
     W.rres = dalloc(h, rs * G, &ok);
@@ -570,6 +576,8 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
       cudaMemcpy(W.piv32, inv32.data(), sizeof(float) * inv32.size(), cudaMemcpyHostToDevice);
     }
   }
+  h->P.fault = W.fault;
+  cudaMemset(W.fault, 0, sizeof(unsigned));
   if (c.wet) upload_stokes_factors(h);
   cudaMemset(W.fgrid, 0, rs * Gf);   // the wall rows of f_y stay zero from here on
   if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -577,12 +585,15 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
       cudaEventCreateWithFlags(&W.yev0, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&W.yev1, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fault, cudaEventDisableTiming) != cudaSuccess ||
+      cudaHostAlloc((void**)&h->fault_host, sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess) {
     free_workspace(h);
     delete h;
     set_error("stream or event creation failed");
     return DISCOS_ERR_CUDA;
   }
+  *h->fault_host = 0u;     // pinned memory comes back uninitialised
   std::vector<double> tab = cached_fp_table(P.kes, c.psi, c.n_tab);
   if (h->mixed) {
     upload_twiddles<float>(W.tw_x, c.Nx);
@@ -615,6 +626,8 @@ discos_status discos_destroy(discos_handle* h) {
     for (int i = 0; i < 2 * Probe::kMax; ++i) cudaEventDestroy(h->probe.ev[i]);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_fault) cudaEventDestroy(h->ev_fault);
+  if (h->fault_host) cudaFreeHost(h->fault_host);
   delete h;
   return DISCOS_OK;
 }
@@ -729,6 +742,11 @@ discos_status discos_step(discos_handle* h, void* x, const void* q, const int* s
   if (st) return st;
   if (nsteps < 0) return invalid("nsteps must be >= 0");
   if (N > 0 && (!x || !q)) return invalid("null pointer");
+  if (cudaEventQuery(h->ev_fault) == cudaSuccess && *h->fault_host) {
+    set_error(std::string("a previous step flagged the device fault word (") + std::to_string(*h->fault_host) +
+              "): bit 0 non-finite position, bit 1 ion outside the channel; see discos_fault");
+    return DISCOS_ERR_DEVICE_FAULT;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   return h->mixed ? step_impl<float>(h, (float*)x, (const float*)q, species, N, step0, nsteps, (float*)F_out, s)
                   : step_impl<double>(h, (double*)x, (const double*)q, species, N, step0, nsteps, (double*)F_out, s);
@@ -778,6 +796,48 @@ discos_status discos_refine_history(discos_handle* h, double* rel, int* n, void*
   for (int i = 0; i < m; ++i) rel[i] = buf[2 * i + 1] > 0.0 ? std::sqrt(buf[2 * i] / buf[2 * i + 1]) : 0.0;
   *n = m;
   return DISCOS_OK;
+}
+
+discos_status discos_fault(discos_handle* h, int sync, int clear, unsigned* word, void* stream) {
+  if (!h || !word) return invalid("null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (sync) {
+    e = cudaMemcpyAsync(h->fault_host, h->W.fault, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_fault, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(h->ev_fault);
+    if (e != cudaSuccess) return cuda_status(e, "discos_fault");
+  }
+  *word = cudaEventQuery(h->ev_fault) == cudaSuccess ? *h->fault_host : 0u;
+  if (clear) {
+    e = cudaMemsetAsync(h->W.fault, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e, "discos_fault");
+    *h->fault_host = 0u;
+  }
+  return DISCOS_OK;
+}
+
+discos_status discos_diagnostics(discos_handle* h, const void* x, const void* q, const void* F, int N, int with_rho,
+                                 double* out, void* stream) {
+  ProbeScope probe_scope(h);
+  discos_status st = check_n(h, N);
+  if (st) return st;
+  if (!out || (N > 0 && (!x || !q))) return invalid("null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (h->mixed) {
+    float* rho = with_rho ? reinterpret_cast<float*>(h->W.fgrid) : nullptr;
+    if (rho) e = launch_spread_charge<float>(h->P, (const float*)x, (const float*)q, N, rho, s);
+    if (e == cudaSuccess)
+      e = launch_diagnostics<float>(h->P, (const float*)x, (const float*)q, (const float*)F, N, rho, out, s);
+  } else {
+    double* rho = with_rho ? reinterpret_cast<double*>(h->W.fgrid) : nullptr;
+    if (rho) e = launch_spread_charge<double>(h->P, (const double*)x, (const double*)q, N, rho, s);
+    if (e == cudaSuccess)
+      e = launch_diagnostics<double>(h->P, (const double*)x, (const double*)q, (const double*)F, N, rho, out, s);
+  }
+  return cuda_status(e, "discos_diagnostics");
 }
 
 }  // extern "C"

@@ -48,6 +48,7 @@ struct Params {
   int drift;
   uint64_t seed;
   int max_refine;              // residual refinement sweeps of the mixed Poisson solve
+  unsigned* fault;             // device fault word: bit 0 non-finite position, bit 1 escaped ion
   double inv_D_dry[DISCOS_MAX_SPECIES], inv_kT;
   PhysF f;
 };
@@ -123,6 +124,8 @@ struct Workspace {
   void* rref = nullptr;         // refinement (mixed, max_refine > 0): rho kept for the residual
   void* rres = nullptr;         //   residual, then correction
   double* rnorm = nullptr;      //   (|r|^2, |b|^2) before each sweep and after the last
+  unsigned* fault = nullptr;    // device fault word (Params::fault)
+  double* diag = nullptr;       // scratch of discos_diagnostics
   int n_cells = 0;
 };
 
@@ -184,6 +187,8 @@ struct discos_handle {
   cudaStream_t side = nullptr;       // independent work of a step runs here
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   discos::BatchState* batch = nullptr;   // batched replicas (batch_api.cu)
+  unsigned* fault_host = nullptr;        // pinned copy of the fault word, written after each discos_step
+  cudaEvent_t ev_fault = nullptr;
 };
 
 namespace discos {
@@ -232,6 +237,8 @@ cudaError_t launch_lift(const Params& P, double* lift, cudaStream_t s);
 cudaError_t launch_scale2(const double* sums, const double* dU, double* out, cudaStream_t s);
 template <typename T> cudaError_t launch_poisson_residual(const Params& P, const T* rho, const T* phi, T* res,
                                                            double* norms, cudaStream_t s);
+template <typename T> cudaError_t launch_diagnostics(const Params& P, const T* x, const T* q, const T* F, int N,
+                                                      const T* rho, double* out, cudaStream_t s);
 template <typename T> cudaError_t launch_add_inplace(T* a, const T* b, size_t n, cudaStream_t s);
 template <typename T> cudaError_t launch_poisson_y(const Params& P, Workspace& W, cplx<T>* S, cudaStream_t s);
 template <typename T> cudaError_t launch_stokes_y(const Params& P, Workspace& W, cplx<T>* S, cplx<T>* Sp,

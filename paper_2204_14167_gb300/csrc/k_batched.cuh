@@ -504,6 +504,7 @@ __global__ void __launch_bounds__(NT, 1) k_batched_step(Params P, BatchArgs B) {
         float Wn[4];
         normals4(u32x4{(uint32_t)i, (uint32_t)step, (uint32_t)r, (uint32_t)TAG_DRY}, P.seed, Wn);
         dry_move(P, sp, p, f, (const float*)nullptr, Wn);
+        check_position(P, p);
         sx[i] = p[0]; sy[i] = p[1]; sz[i] = p[2];
         if (B.hist) {
           int bin = (int)floorf(p[1]);

@@ -1,3 +1,6 @@
+// Double-precision reductions: the residual refinement of the mixed-precision
+// Poisson solve, and the run diagnostics (charge, neutrality, momentum).
+//
 // Residual refinement of the mixed-precision Poisson solve.  The residual of
 // Eq. poisson with the ghost-cell rows of Eqs. esbc1 / esbc3,
 //     r = 4 pi lB rho + lap_h phi,
@@ -78,6 +81,47 @@ __global__ void k_poisson_residual(Params P, const T* __restrict__ rho, const T*
   }
 }
 
+// out[0] += sum q, out[2..4] += sum F, out[5] += non-finite positions,
+// out[6] += ions outside the channel; out[1] += sum rho (grid part, rho != 0).
+template <typename T>
+__global__ void k_diagnostics(Params P, const T* __restrict__ x, const T* __restrict__ q, const T* __restrict__ F,
+                              int N, const T* __restrict__ rho, double* __restrict__ out) {
+  double a[7] = {0, 0, 0, 0, 0, 0, 0};
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)N; i += stride) {
+    const T px = x[i], py = x[N + i], pz = x[2 * N + i];
+    a[0] += (double)q[i];
+    if (F) {
+      a[2] += (double)F[i];
+      a[3] += (double)F[N + i];
+      a[4] += (double)F[2 * N + i];
+    }
+    if (!(isfinite(px) && isfinite(py) && isfinite(pz))) a[5] += 1.0;
+    else if (px < T(0) || px >= T(P.Nx) || py < T(0) || py > T(P.Ny) || pz < T(0) || pz >= T(P.Nz)) a[6] += 1.0;
+  }
+  if (rho) {
+    const size_t G = (size_t)P.Nx * P.Ny * P.Nz;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < G; i += stride) a[1] += (double)rho[i];
+  }
+  __shared__ double red[7][32];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_xor_sync(0xffffffffu, a[k], o);
+    if (lane == 0) red[k][wid] = a[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      double v = lane < nw ? red[k][lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && v != 0.0) atomicAdd(&out[k], v);
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_add_inplace(T* __restrict__ a, const T* __restrict__ b, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -101,6 +145,18 @@ cudaError_t launch_add_inplace(T* a, const T* b, size_t n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_diagnostics(const Params& P, const T* x, const T* q, const T* F, int N, const T* rho, double* out,
+                               cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, 8 * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  k_diagnostics<T><<<152 * 2, 256, 0, s>>>(P, x, q, F, N, rho, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_diagnostics<float>(const Params&, const float*, const float*, const float*, int, const float*, double*, cudaStream_t);
+template cudaError_t launch_diagnostics<double>(const Params&, const double*, const double*, const double*, int, const double*, double*, cudaStream_t);
 template cudaError_t launch_poisson_residual<float>(const Params&, const float*, const float*, float*, double*, cudaStream_t);
 template cudaError_t launch_poisson_residual<double>(const Params&, const double*, const double*, double*, double*, cudaStream_t);
 template cudaError_t launch_add_inplace<float>(float*, const float*, size_t, cudaStream_t);

@@ -26,6 +26,7 @@ __global__ void k_dry_update(T* __restrict__ x, const int* __restrict__ species,
   T v[3] = {T(0), T(0), T(0)};
   if (V) { v[0] = V[i]; v[1] = V[N + i]; v[2] = V[2 * N + i]; }
   dry_move(P, sp, p, f, V ? v : nullptr, W);
+  check_position(P, p);
   x[i] = p[0];
   x[N + i] = p[1];
   x[2 * N + i] = p[2];

@@ -106,6 +106,16 @@ __device__ __forceinline__ void fit_gamma(const C* c, T yt, T& g, T& dg) {
   dg = -T(c[1]) * i3 * i3 - T(3) * T(c[3]) * i5_2 * i5_2 - T(5) * T(c[5]) * i7_2 * i7_2 * i7_2;
 }
 
+// Flags an updated position in the device fault word: non-finite (bit 0) or
+// outside the channel after the wall reflection (bit 1, a displacement larger
+// than the channel).  The position is left as it is.
+template <typename T>
+__device__ __forceinline__ void check_position(const Params& P, const T p[3]) {
+  if (!P.fault) return;
+  if (!(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) atomicOr(P.fault, 1u);
+  else if (p[1] < T(0) || p[1] > T(P.Ny)) atomicOr(P.fault, 2u);
+}
+
 // One Euler-Maruyama step of the dry part of Eq. ions3 for one ion of species
 // sp: dt (D^dry Gamma F / kT + div D^dry) + sqrt(2 dt D^dry Gamma) W, with
 // Gamma = (gamma^tot D^tot - gamma^wet D^wet) / D^dry (Eqs. diff1-diff2) from

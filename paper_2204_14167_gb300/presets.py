@@ -72,6 +72,28 @@ def energy_channel_64(precision=FP64):
     return cfg, dict(n_pos=2048, n_neg=2048, ymargin=1.0, min_sep=0.0, seed=20220501)
 
 
+def iceo_channel_256x128x256(precision=MIXED):
+    """256 x 128 x 256 channel, conducting (Dirichlet phi = 0) bottom wall and
+    dielectric (Neumann, no surface charge) top wall, 200k + 200k ions
+    uniform in y in [1, 127] and at least 0.9 sigma apart, l_B = 0.96, ion
+    WCA sigma = 0.6, E_x = 0.02,
+    the full wet step of the 128 x 64 x 128 channel (fluctuating Stokes,
+    thermal drift, near-wall mobility)."""
+    cfg, rec = wet_channel_128x64x128(precision)
+    Ny = 128
+    cfg.Nx, cfg.Ny, cfg.Nz = 256, Ny, 256
+    cfg.bc = (BC_DIRICHLET, BC_NEUMANN)
+    cfg.phi_b = (0.0, 0.0)
+    cfg.surf_charge = (0.0, 0.0)
+    cfg.lB = 0.96
+    cfg.E_ext = (0.02, 0.0, 0.0)
+    cfg.gamma_coef = [mobility.gamma_table(0.5 * A_WET_PESKIN4, A_WET_PESKIN4, float(Ny))]
+    cfg.max_ions = 400000
+    for k, v in _wca(0.6).items():
+        setattr(cfg, k, v)
+    return cfg, dict(n_pos=200000, n_neg=200000, ymargin=1.0, min_sep=0.9 * 0.6, seed=20220503)
+
+
 def batched_channels_32(R=512, precision=MIXED, seed=20220502):
     """R independent replicas of dry_channel_32's channel (Dirichlet phi = 0
     walls, l_B = 7, 6-point kernel, dt = 0.01), replica r holding an even,
@@ -99,4 +121,5 @@ PRESETS = {
     "dry_channel_32": dry_channel_32,
     "wet_channel_128x64x128": wet_channel_128x64x128,
     "energy_channel_64": energy_channel_64,
+    "iceo_channel_256x128x256": iceo_channel_256x128x256,
 }
