@@ -227,7 +227,7 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "ions": N, "grid": [cfg.Nx, cfg.Ny, cfg.Nz],
                            "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{ws}"},
                 "clocks": clocks, "e2e": e2e, "roofline": rl.get("roofline"), "stages_ms": rl.get("stages_ms"),
-                "gpu_launches": int(n_launches)}
+                "gpu_launches": int(n_launches), "device_fault": h.fault(sync=True)}
         if not args.no_forms and ws == 1:
             line["production_forms"] = production_forms()
         if not args.no_cpu_baseline:
@@ -297,7 +297,8 @@ def _plain_fp64(out, timed, steps):
     step64()
     ms64 = timed(step64, max(steps // 2, 3))
     out["plain_fp64_wet_channel_128x64x128"] = {"ion_steps_per_s": N / (ms64 * 1e-3), "ms_per_step": ms64,
-                                                "mixed_vs_fp64_force_rel_l2": err}
+                                                "mixed_vs_fp64_force_rel_l2": err,
+                                                "device_fault": h64.fault(sync=True)}
 
 
 def _iceo(out, timed):
@@ -330,7 +331,8 @@ def _iceo(out, timed):
     N5 = p5.shape[1]
     out["iceo_channel_256x128x256"] = {"mixed_ion_steps_per_s": N5 / (ms5m * 1e-3), "mixed_ms_per_step": ms5m,
                                        "fp64_ion_steps_per_s": N5 / (ms5d * 1e-3), "fp64_ms_per_step": ms5d,
-                                       "mixed_vs_fp64_force_rel_l2": err5, "ions": N5}
+                                       "mixed_vs_fp64_force_rel_l2": err5, "ions": N5,
+                                       "device_fault": [h5m.fault(sync=True), h5d.fault(sync=True)]}
 
 
 def _batched(out, timed):
@@ -370,7 +372,7 @@ def _batched(out, timed):
     out["batched_replicas_512x32^3"] = {
         "ion_steps_per_s": off[-1] / (msb * 1e-3), "ms_per_step": msb, "ions": off[-1], "replicas": R,
         "steps_per_launch": spl, "graph": True,
-        "plain_single_channel_ion_steps_per_s": ions_sub / (msp * 1e-3)}
+        "plain_single_channel_ion_steps_per_s": ions_sub / (msp * 1e-3), "device_fault": hb.fault(sync=True)}
 
 
 

@@ -25,11 +25,18 @@ __global__ void k_bin(const T* __restrict__ x, int N, Params P, int* __restrict_
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int cid = -1;
   if (i < N) {
-    int cx = cell_coord(x[i], P.k_cell, P.ncx);
-    int cy = cell_coord(x[N + i], P.k_cell, P.ncy);
-    int cz = cell_coord(x[2 * N + i], P.k_cell, P.ncz);
+    const T px = x[i], py = x[N + i], pz = x[2 * N + i];
+    int cx = cell_coord(px, P.k_cell, P.ncx);
+    int cy = cell_coord(py, P.k_cell, P.ncy);
+    int cz = cell_coord(pz, P.k_cell, P.ncz);
     cid = (cz * P.ncy + cy) * P.ncx + cx;
     cell_of[i] = cid;
+    // positions that would pile into the edge cells are flagged here, before
+    // the per-cell work that such a pile-up would make quadratic
+    if (P.fault) {
+      if (!(isfinite(px) && isfinite(py) && isfinite(pz))) atomicOr(P.fault, 1u);
+      else if (py < T(0) || py > T(P.Ny)) atomicOr(P.fault, 2u);
+    }
   }
   // warp aggregation: one atomic per distinct cell in the warp
   unsigned peers = __match_any_sync(0xffffffffu, cid);
@@ -122,9 +129,12 @@ __global__ void k_scatter(const int* __restrict__ cell_of, int N, const int* __r
   if (cid >= 0) perm[start[cid] + base + rank] = i;
 }
 
-__global__ void k_sort_cells(const int* __restrict__ start, int n_cells, int* __restrict__ perm) {
+__global__ void k_sort_cells(const int* __restrict__ start, int n_cells, int* __restrict__ perm,
+                             const unsigned* __restrict__ fault = nullptr) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_cells) return;
+  // a flagged run may have every ion in one cell: the order no longer matters
+  if (fault && *reinterpret_cast<const volatile unsigned*>(fault)) return;
   int b = start[c], e = start[c + 1];
   for (int a = b + 1; a < e; ++a) {
     int v = perm[a];
@@ -162,7 +172,7 @@ cudaError_t launch_cell_list(const Params& P, Workspace& W, const T* x, int N, c
     k_scatter<<<nb, bs, 0, s>>>(W.cell_of, N, W.cell_start, W.fill, W.perm);
     count_launches(1);
   }
-  k_sort_cells<<<(n + 255) / 256, 256, 0, s>>>(W.cell_start, n, W.perm);
+  k_sort_cells<<<(n + 255) / 256, 256, 0, s>>>(W.cell_start, n, W.perm, P.fault);
   count_launches(1);
   probe_end(PROBE_CELL_LIST, s);
   return cudaGetLastError();

@@ -42,6 +42,9 @@ __global__ void k_near_field(const T* __restrict__ xs, const T* __restrict__ qs,
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (s >= N) return;                       // whole warps exit together
+  // once the fault word is set the positions are garbage and may share one
+  // cell; skip the pair loops (the host reports the fault at the next step)
+  if (P.fault && *reinterpret_cast<const volatile unsigned*>(P.fault)) return;
   const T xi = xs[s], yi = xs[N + s], zi = xs[2 * N + s], qi = qs[s];
   const int si = sps[s];
   const int cx = cell_coord(xi, P.k_cell, P.ncx);

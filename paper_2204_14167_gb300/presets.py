@@ -24,10 +24,13 @@ def _wall():
 
 def dry_channel_32(precision=FP64):
     """32^3 channel, Dirichlet phi = 0 walls, 128 + 128 ions, l_B = 7,
-    6-point kernel, dry diffusion (D = 1, dt = 0.01)."""
+    6-point kernel, dry diffusion (D = 1).  dt = 0.001: explicit
+    Euler-Maruyama needs dt D U''(r) < 1 at WCA contact, U''(0.9 sigma) ~ 560
+    kT per cell^2 for sigma = 3; at dt = 0.01 a 512-ion channel of this kind
+    blows up within a few steps (the oracle does the same)."""
     gam = mobility.gamma_table(1.0, 1.0, 32.0)
     cfg = RunConfig(Nx=32, Ny=32, Nz=32, bc=(BC_DIRICHLET, BC_DIRICHLET), kernel_es=KERNEL_PESKIN6,
-                    kernel_hy=KERNEL_PESKIN6, lB=7.0, dt=0.01, psi=4.0, n_tab=64, D_tot=[1.0], D_wet=[0.0],
+                    kernel_hy=KERNEL_PESKIN6, lB=7.0, dt=0.001, psi=4.0, n_tab=64, D_tot=[1.0], D_wet=[0.0],
                     gamma_coef=[gam], wet=False, precision=precision, max_ions=256, **_wca(3.0), **_wall())
     return cfg, dict(n_pos=128, n_neg=128, ymargin=1.0, min_sep=0.9 * 3.0, seed=20220429)
 
@@ -76,7 +79,7 @@ def iceo_channel_256x128x256(precision=MIXED):
     """256 x 128 x 256 channel, conducting (Dirichlet phi = 0) bottom wall and
     dielectric (Neumann, no surface charge) top wall, 200k + 200k ions
     uniform in y in [1, 127] and at least 0.9 sigma apart, l_B = 0.96, ion
-    WCA sigma = 0.6, E_x = 0.02,
+    WCA sigma = 0.6, E_x = 0.02, dt = 1e-4 (stable at WCA contact),
     the full wet step of the 128 x 64 x 128 channel (fluctuating Stokes,
     thermal drift, near-wall mobility)."""
     cfg, rec = wet_channel_128x64x128(precision)
@@ -89,6 +92,9 @@ def iceo_channel_256x128x256(precision=MIXED):
     cfg.E_ext = (0.02, 0.0, 0.0)
     cfg.gamma_coef = [mobility.gamma_table(0.5 * A_WET_PESKIN4, A_WET_PESKIN4, float(Ny))]
     cfg.max_ions = 400000
+    # explicit Euler-Maruyama is stable at WCA contact for dt D_tot U''(sigma) < 1;
+    # U''(0.6) ~ 3000 kT per cell^2 with D_tot ~ 2.2 gives dt = 1e-4
+    cfg.dt = 1e-4
     for k, v in _wca(0.6).items():
         setattr(cfg, k, v)
     return cfg, dict(n_pos=200000, n_neg=200000, ymargin=1.0, min_sep=0.9 * 0.6, seed=20220503)
@@ -96,7 +102,7 @@ def iceo_channel_256x128x256(precision=MIXED):
 
 def batched_channels_32(R=512, precision=MIXED, seed=20220502):
     """R independent replicas of dry_channel_32's channel (Dirichlet phi = 0
-    walls, l_B = 7, 6-point kernel, dt = 0.01), replica r holding an even,
+    walls, l_B = 7, 6-point kernel, dt = 0.001), replica r holding an even,
     charge-neutral number of ions drawn uniformly in [64, 512]."""
     import numpy as np
     cfg, rec = dry_channel_32(precision)

@@ -8,7 +8,8 @@ make one sample at a time, or that hold at any size.
   images: partner counts bit-exact, forces 1e-10 (FP64) / 1e-4 (MIXED).
 - MIXED forces against FP64 forces on all ions: relative L2 <= 1e-4 (the
   stated single-precision target), and one full wet step from the same state
-  (same Philox noise): displacements within 1e-4.
+  (same Philox noise): displacements within 1e-4 relative plus one float ulp
+  of the coordinates (the MIXED path stores positions in float).
 """
 import numpy as np
 import pytest
@@ -94,4 +95,8 @@ def test_full_size_mixed_against_fp64(state):
     x0 = xm64.cpu().numpy()
     d64 = min_image_disp(x64.cpu().numpy(), x0, c64.dims)
     dm = min_image_disp(xm.double().cpu().numpy(), x0, c64.dims)
-    assert rel_l2(dm, d64) <= 1e-4
+    # the single-precision path stores x + dx in float: one ulp of the largest
+    # coordinate (3e-5 at 256) is a floor on top of the 1e-4 relative target
+    rms = lambda a: float(np.sqrt(np.mean(np.square(a))))
+    ulp = float(np.spacing(np.float32(max(c64.dims))))
+    assert rms(dm - d64) <= 1e-4 * rms(d64) + ulp
