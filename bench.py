@@ -145,6 +145,7 @@ def run_ours(args):
     h = dg.Discos(cfg)
     x = torch.tensor(pos, dtype=torch.float32, device="cuda").contiguous()
     qd = torch.tensor(q, dtype=torch.float32, device="cuda")
+    shape = h.tune_transforms()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
     step = 0
@@ -225,7 +226,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "ions": N, "grid": [cfg.Nx, cfg.Ny, cfg.Nz],
-                           "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{ws}"},
+                           "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{ws}",
+                           "transform_shape": {"fx_pairs": shape[0], "fx_threads": shape[1], "fz_tile": shape[2]}},
                 "clocks": clocks, "e2e": e2e, "roofline": rl.get("roofline"), "stages_ms": rl.get("stages_ms"),
                 "gpu_launches": int(n_launches), "device_fault": h.fault(sync=True)}
         if not args.no_forms and ws == 1:
@@ -405,6 +407,7 @@ def run_profile(args):
     cfg, rec = presets.wet_channel_128x64x128(dg.MIXED)
     pos, q, sp = synth.ions(cfg.dims, rec["n_pos"], rec["n_neg"], rec["seed"], rec["ymargin"], rec["min_sep"])
     h = dg.Discos(cfg)
+    h.tune_transforms()
     x = torch.tensor(pos, dtype=torch.float32, device="cuda").contiguous()
     qd = torch.tensor(q, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()

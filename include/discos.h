@@ -331,6 +331,22 @@ discos_status discos_diagnostics(discos_handle* h, const void* x, const void* q,
  * `stream`.  Other handles return n = 0. */
 discos_status discos_refine_history(discos_handle* h, double* rel, int* n, void* stream);
 
+/* Launch-shape autotuner of the x and z transforms (used by every Poisson
+ * and Stokes solve of the handle): times each candidate shape (x: 128 to
+ * 2048 grid values per block, i.e. 1..2048/Nx row pairs; z: 1..16 columns
+ * per block within the shared-memory limit) on the handle's own buffers at
+ * the Poisson sizes, keeps the fastest, and returns it (out pointers may be
+ * NULL; ms[2] = the x and z times per launch).  Overwrites the handle's
+ * potential and spectrum workspace; blocks until done. */
+discos_status discos_tune_transforms(discos_handle* h, int* fx_pairs, int* fx_threads, int* fz_tile,
+                                     float* ms, void* stream);
+
+/* Sets the transform launch shape directly: fx_pairs row pairs per x block
+ * (fx_pairs * Nx <= 2048, within 48 KB of shared memory), fx_threads (a
+ * multiple of 32), fz_tile columns per z block (a power of two).
+ * Errors: INVALID_ARG outside those limits. */
+discos_status discos_set_transform_shape(discos_handle* h, int fx_pairs, int fx_threads, int fz_tile);
+
 /* Host-only (no GPU needed): the F^P pair-force table that discos_create
  * builds (Sec. II.B.1, Eq. LC), for kernel `kernel` (es_w, es_beta used by
  * DISCOS_KERNEL_ES), f^P(k psi / n_tab) for k = 0..n_tab with l_B = 1 and

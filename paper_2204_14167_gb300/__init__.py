@@ -232,6 +232,17 @@ class Discos:
                                          _ptr(F_out), _stream(stream)))
         return x
 
+    def tune_transforms(self, stream=None):
+        """Pick the fastest transform launch shape; returns (pairs, threads, tile, (ms_x, ms_z))."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_float * 2)()
+        _lib.check(self._lib.discos_tune_transforms(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ms,
+                                                    _stream(stream)))
+        return a.value, b.value, c.value, (ms[0], ms[1])
+
+    def set_transform_shape(self, fx_pairs, fx_threads, fz_tile):
+        _lib.check(self._lib.discos_set_transform_shape(self._h, int(fx_pairs), int(fx_threads), int(fz_tile)))
+
     def fault(self, sync=True, clear=False, stream=None):
         """The device fault word (bit 0 non-finite position, bit 1 escaped ion)."""
         w = ctypes.c_uint()

@@ -74,7 +74,7 @@ EXPORTS = [
     "discos_step", "discos_fp_table", "discos_launch_count", "discos_cell_list_noalloc",
     "discos_probe", "discos_probe_read", "discos_energy", "discos_energy_backward",
     "discos_step_batched", "discos_tune_batched", "discos_set_batched_shape", "discos_refine_history",
-    "discos_fault", "discos_diagnostics",
+    "discos_fault", "discos_diagnostics", "discos_tune_transforms", "discos_set_transform_shape",
 ]
 PROBE_FAMILIES = ["cell_list", "near_field", "noise", "spread_charge", "fft_x", "fft_z", "poisson_y", "interp_e",
                   "spread_force", "stokes_y", "interp_v", "update"]
@@ -111,6 +111,9 @@ def load():
     lib.discos_step_batched.argtypes = [vp, ctypes.POINTER(Batch), i64, i32, vp]
     lib.discos_tune_batched.argtypes = [vp, ctypes.POINTER(Batch), i32, ctypes.POINTER(i32), ctypes.POINTER(D), vp]
     lib.discos_set_batched_shape.argtypes = [vp, i32]
+    lib.discos_tune_transforms.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                           ctypes.POINTER(ctypes.c_float), vp]
+    lib.discos_set_transform_shape.argtypes = [vp, i32, i32, i32]
     lib.discos_fault.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_uint), vp]
     lib.discos_diagnostics.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp]
     lib.discos_refine_history.argtypes = [vp, ctypes.POINTER(D), ctypes.POINTER(i32), vp]

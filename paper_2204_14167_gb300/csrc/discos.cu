@@ -439,6 +439,12 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   P.inv_kT = 1.0 / c.kT;
   P.max_refine = c.precision == DISCOS_MIXED ? c.max_refine : 0;
   {
+    const size_t elem = c.precision == DISCOS_MIXED ? 2 * sizeof(float) : 2 * sizeof(double);
+    P.fx_pp = default_fx_pairs(c.Nx);
+    P.fx_threads = 256;
+    P.fz_tk = default_tile_z(c.Nz, elem);
+  }
+  {
     PhysF& f = P.f;
     for (int a = 0; a < DISCOS_MAX_SPECIES; ++a) {
       P.inv_D_dry[a] = P.D_dry[a] != 0.0 ? 1.0 / P.D_dry[a] : 0.0;
@@ -838,6 +844,34 @@ discos_status discos_diagnostics(discos_handle* h, const void* x, const void* q,
       e = launch_diagnostics<double>(h->P, (const double*)x, (const double*)q, (const double*)F, N, rho, out, s);
   }
   return cuda_status(e, "discos_diagnostics");
+}
+
+discos_status discos_tune_transforms(discos_handle* h, int* fx_pairs, int* fx_threads, int* fz_tile,
+                                     float* ms, void* stream) {
+  if (!h) return invalid("null handle");
+  float best[2] = {0.f, 0.f};
+  cudaError_t e = tune_transforms(h->P, h->W, h->mixed, (cudaStream_t)stream, best);
+  if (e != cudaSuccess) return cuda_status(e, "discos_tune_transforms");
+  if (fx_pairs) *fx_pairs = h->P.fx_pp;
+  if (fx_threads) *fx_threads = h->P.fx_threads;
+  if (fz_tile) *fz_tile = h->P.fz_tk;
+  if (ms) { ms[0] = best[0]; ms[1] = best[1]; }
+  return DISCOS_OK;
+}
+
+discos_status discos_set_transform_shape(discos_handle* h, int fx_pairs, int fx_threads, int fz_tile) {
+  if (!h) return invalid("null handle");
+  const size_t elem = h->mixed ? 2 * sizeof(float) : 2 * sizeof(double);
+  const int N = h->P.Nx;
+  if (fx_pairs < 1 || (size_t)fx_pairs * N > 2048 || 2 * (size_t)fx_pairs * N * elem + 2 * (size_t)fx_pairs * elem > 48 * 1024)
+    return invalid("fx_pairs: 1 .. 2048 / Nx row pairs within 48 KB of shared memory");
+  if (fx_threads < 32 || fx_threads > 1024 || fx_threads % 32) return invalid("fx_threads: a multiple of 32 in 32..1024");
+  if (fz_tile < 1 || (fz_tile & (fz_tile - 1)) || fz_tile > max_tile_z(h->P.Nz, elem))
+    return invalid("fz_tile: a power of two up to the shared-memory limit");
+  h->P.fx_pp = fx_pairs;
+  h->P.fx_threads = fx_threads;
+  h->P.fz_tk = fz_tile;
+  return DISCOS_OK;
 }
 
 }  // extern "C"

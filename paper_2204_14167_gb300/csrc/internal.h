@@ -48,6 +48,7 @@ struct Params {
   int drift;
   uint64_t seed;
   int max_refine;              // residual refinement sweeps of the mixed Poisson solve
+  int fx_pp, fx_threads, fz_tk;  // transform launch shapes (k_fft.cu; discos_tune_transforms)
   unsigned* fault;             // device fault word: bit 0 non-finite position, bit 1 escaped ion
   double inv_D_dry[DISCOS_MAX_SPECIES], inv_kT;
   PhysF f;
@@ -201,6 +202,13 @@ void free_batch(discos_handle* h);
 // Number of kernels this library has launched since it was loaded.
 void count_launches(long long n);
 discos_status cuda_status(cudaError_t e, const char* where);
+
+// Transform launch shapes (k_fft.cu).
+int default_fx_pairs(int Nx);
+int max_tile_z(int Nz, size_t elem);
+int default_tile_z(int Nz, size_t elem);
+int fz_threads(int TK, int Nz);
+cudaError_t tune_transforms(Params& P, Workspace& W, bool mixed, cudaStream_t s, float* best_ms);
 
 // Host code that builds the F^P table (fptable.cpp).
 bool build_fp_table(const KernelParams& kp, double psi, int n_tab, double* out, std::string* err);

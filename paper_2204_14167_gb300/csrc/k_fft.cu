@@ -34,8 +34,8 @@ __device__ cplx<T>* fft_stockham(cplx<T>* in, cplx<T>* out, int N, int logN, int
       const int total = nvec * q;
       const int twstep = N / (4 * Ns);
       for (int b = threadIdx.x; b < total; b += blockDim.x) {
-        const int v = b / q;
-        const int j = b - v * q;
+        const int v = b >> (logN - 2);
+        const int j = b & (q - 1);
         const int k = j & (Ns - 1);
         cplx<T> w1 = tw[k * twstep], w2 = tw[2 * k * twstep];
         if (inverse) { w1.im = -w1.im; w2.im = -w2.im; }
@@ -92,26 +92,29 @@ __global__ void k_rfft_x(const T* __restrict__ in, int R, int N, int logN, int P
   const int PP = pairs_per_block;
   cplx<T>* bufa = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* bufb = bufa + (size_t)PP * N;
+  T* rowadd = reinterpret_cast<T*>(bufb + (size_t)PP * N);   // [2 PP] wall terms of each row
+  for (int t = threadIdx.x; t < 2 * PP; t += blockDim.x) {
+    const int row = 2 * blockIdx.x * PP + t;
+    const int y = row % Nyr;
+    rowadd[t] = (y == 0 ? add0 : T(0)) + (y == Nyr - 1 ? add1 : T(0));
+  }
+  __syncthreads();
   for (int idx = threadIdx.x; idx < PP * N; idx += blockDim.x) {
-    int v = idx / N, n = idx - v * N;
-    int p = blockIdx.x * PP + v;
-    int ra = 2 * p, rb = 2 * p + 1;
+    const int v = idx >> logN, n = idx & (N - 1);
+    const int ra = 2 * (blockIdx.x * PP + v), rb = ra + 1;
     T a = T(0), b = T(0);
-    if (ra < R) {
-      int y = ra % Nyr;
-      a = scale * in[(size_t)ra * N + n] + (y == 0 ? add0 : T(0)) + (y == Nyr - 1 ? add1 : T(0));
-    }
-    if (rb < R) {
-      int y = rb % Nyr;
-      b = scale * in[(size_t)rb * N + n] + (y == 0 ? add0 : T(0)) + (y == Nyr - 1 ? add1 : T(0));
-    }
+    if (ra < R) a = scale * in[(size_t)ra * N + n] + rowadd[2 * v];
+    if (rb < R) b = scale * in[(size_t)rb * N + n] + rowadd[2 * v + 1];
     bufa[idx] = cplx<T>{a, b};
   }
   __syncthreads();
   cplx<T>* r = fft_stockham(bufa, bufb, N, logN, PP, N, tw, false);
   const int M = N / 2 + 1;
+  // idx / M by a float reciprocal: idx < 2^16, so (idx + 1/2) / M stays at
+  // least 1/(2M) away from an integer, far beyond the rounding of the product
+  const float invM = 1.0f / (float)M;
   for (int idx = threadIdx.x; idx < PP * M; idx += blockDim.x) {
-    int v = idx / M, k = idx - v * M;
+    const int v = (int)(((float)idx + 0.5f) * invM), k = idx - v * M;
     int p = blockIdx.x * PP + v;
     int ra = 2 * p, rb = 2 * p + 1;
     cplx<T> Zk = r[v * N + (k & (N - 1))];
@@ -134,7 +137,7 @@ __global__ void k_irfft_x(const cplx<T>* __restrict__ in, int R, int N, int logN
   cplx<T>* bufb = bufa + (size_t)PP * N;
   const int hN = N / 2;
   for (int idx = threadIdx.x; idx < PP * N; idx += blockDim.x) {
-    int v = idx / N, k = idx - v * N;
+    const int v = idx >> logN, k = idx & (N - 1);
     int p = blockIdx.x * PP + v;
     int ra = 2 * p, rb = 2 * p + 1;
     int kk = k <= hN ? k : N - k;
@@ -147,7 +150,7 @@ __global__ void k_irfft_x(const cplx<T>* __restrict__ in, int R, int N, int logN
   __syncthreads();
   cplx<T>* r = fft_stockham(bufa, bufb, N, logN, PP, N, tw, true);
   for (int idx = threadIdx.x; idx < PP * N; idx += blockDim.x) {
-    int v = idx / N, n = idx - v * N;
+    const int v = idx >> logN, n = idx & (N - 1);
     int p = blockIdx.x * PP + v;
     int ra = 2 * p, rb = 2 * p + 1;
     cplx<T> z = r[idx];
@@ -179,8 +182,9 @@ __global__ void k_fft_z(cplx<T>* __restrict__ data, int Nz, int logNz, int Nyr, 
   const int y = blockIdx.y;
   if (y >= Nyr) return;
   const int kx0 = blockIdx.x * TK;
+  const int logTK = 31 - __clz(TK);
   for (int idx = threadIdx.x; idx < TK * Nz; idx += blockDim.x) {
-    int z = idx / TK, c = idx - z * TK;
+    const int z = idx >> logTK, c = idx & (TK - 1);
     int kx = kx0 + c;
     cplx<T> v{T(0), T(0)};
     if (kx < Nxh) v = base[((size_t)z * Nyr + y) * Px + kx];
@@ -190,27 +194,35 @@ __global__ void k_fft_z(cplx<T>* __restrict__ data, int Nz, int logNz, int Nyr, 
   const int nv = Nxh - kx0 < TK ? Nxh - kx0 : TK;   // the last tile holds fewer columns
   cplx<T>* r = fft_stockham(bufa, bufb, Nz, logNz, nv, vs, tw, inverse != 0);
   for (int idx = threadIdx.x; idx < TK * Nz; idx += blockDim.x) {
-    int z = idx / TK, c = idx - z * TK;
+    const int z = idx >> logTK, c = idx & (TK - 1);
     int kx = kx0 + c;
     if (kx < Nxh) base[((size_t)z * Nyr + y) * Px + kx] = r[c * vs + z];
   }
 }
 
-template <typename T>
-int pairs_per_block(int N) {
-  int pp = 1024 / N;
-  return pp < 1 ? 1 : pp;
-}
-
 }  // namespace
 
-// columns per z-transform block: 8 (small blocks keep the launch within one
-// wave at typical sizes), halved while the two buffers exceed 140 KB
-template <typename T>
-int tile_z(int Nz) {
-  int tk = 8;
-  while (tk > 2 && 2 * (size_t)tk * (Nz + 1) * sizeof(cplx<T>) > 140 * 1024) tk >>= 1;
+// Default launch shapes of the transforms (discos_tune_transforms may replace
+// them): 1024 / Nx row pairs per x-block on 256 threads; 8 columns per
+// z-block (small blocks keep the launch within one wave at typical sizes),
+// halved while the two buffers exceed 140 KB.
+int default_fx_pairs(int Nx) {
+  int pp = 1024 / Nx;
+  return pp < 1 ? 1 : pp;
+}
+int max_tile_z(int Nz, size_t elem) {
+  int tk = 16;
+  while (tk > 1 && 2 * (size_t)tk * (Nz + 1) * elem > 140 * 1024) tk >>= 1;
   return tk;
+}
+// one radix-4 butterfly per thread: TK Nz / 4 threads, 64..256
+int fz_threads(int TK, int Nz) {
+  int t = TK * Nz / 4;
+  return t < 64 ? 64 : (t > 256 ? 256 : t);
+}
+int default_tile_z(int Nz, size_t elem) {
+  int tk = max_tile_z(Nz, elem);
+  return tk > 8 ? 8 : tk;
 }
 
 template <typename T>
@@ -227,12 +239,12 @@ template <typename T>
 cudaError_t fft_x_forward(const Params& P, const T* in, int R, cplx<T>* out, T scale, int Nyr, T add0, T add1,
                           const cplx<T>* tw, cudaStream_t s) {
   int N = P.Nx, logN = 31 - __builtin_clz((unsigned)N);
-  int pp = pairs_per_block<T>(N);
+  int pp = P.fx_pp;
   int pairs = (R + 1) / 2;
   int nb = (pairs + pp - 1) / pp;
-  size_t sm = 2 * (size_t)pp * N * sizeof(cplx<T>);
+  size_t sm = 2 * (size_t)pp * N * sizeof(cplx<T>) + 2 * (size_t)pp * sizeof(T);
   probe_begin(PROBE_FFT_X, s);
-  k_rfft_x<T><<<nb, 256, sm, s>>>(in, R, N, logN, P.Px, out, scale, Nyr, add0, add1, tw, pp);
+  k_rfft_x<T><<<nb, P.fx_threads, sm, s>>>(in, R, N, logN, P.Px, out, scale, Nyr, add0, add1, tw, pp);
   count_launches(1);
   probe_end(PROBE_FFT_X, s);
   return cudaGetLastError();
@@ -242,12 +254,12 @@ template <typename T>
 cudaError_t fft_x_inverse(const Params& P, const cplx<T>* in, int R, T* out, T scale, const cplx<T>* tw,
                           cudaStream_t s) {
   int N = P.Nx, logN = 31 - __builtin_clz((unsigned)N);
-  int pp = pairs_per_block<T>(N);
+  int pp = P.fx_pp;
   int pairs = (R + 1) / 2;
   int nb = (pairs + pp - 1) / pp;
   size_t sm = 2 * (size_t)pp * N * sizeof(cplx<T>);
   probe_begin(PROBE_FFT_X, s);
-  k_irfft_x<T><<<nb, 256, sm, s>>>(in, R, N, logN, P.Px, out, scale, tw, pp);
+  k_irfft_x<T><<<nb, P.fx_threads, sm, s>>>(in, R, N, logN, P.Px, out, scale, tw, pp);
   count_launches(1);
   probe_end(PROBE_FFT_X, s);
   return cudaGetLastError();
@@ -257,12 +269,13 @@ template <typename T>
 cudaError_t fft_z(const Params& P, cplx<T>* data, int Nyr, int nfields, size_t field_stride, bool inverse,
                   const cplx<T>* tw, cudaStream_t s) {
   int Nz = P.Nz, logNz = 31 - __builtin_clz((unsigned)Nz);
-  const int TK = tile_z<T>(Nz);
+  const int TK = P.fz_tk;
   size_t sm = 2 * (size_t)TK * (Nz + 1) * sizeof(cplx<T>);
   ensure_fft_z_attr<T>();
   dim3 grid((P.Nxh + TK - 1) / TK, Nyr, nfields);
   probe_begin(PROBE_FFT_Z, s);
-  k_fft_z<T><<<grid, 256, sm, s>>>(data, Nz, logNz, Nyr, P.Px, P.Nxh, inverse ? 1 : 0, tw, field_stride, 0, TK);
+  k_fft_z<T><<<grid, fz_threads(TK, Nz), sm, s>>>(data, Nz, logNz, Nyr, P.Px, P.Nxh, inverse ? 1 : 0, tw,
+                                                   field_stride, 0, TK);
   count_launches(1);
   probe_end(PROBE_FFT_Z, s);
   return cudaGetLastError();
@@ -271,12 +284,13 @@ cudaError_t fft_z(const Params& P, cplx<T>* data, int Nyr, int nfields, size_t f
 template <typename T>
 cudaError_t fft_z_mac(const Params& P, cplx<T>* data, bool inverse, const cplx<T>* tw, cudaStream_t s) {
   int Nz = P.Nz, logNz = 31 - __builtin_clz((unsigned)Nz);
-  const int TK = tile_z<T>(Nz);
+  const int TK = P.fz_tk;
   size_t sm = 2 * (size_t)TK * (Nz + 1) * sizeof(cplx<T>);
   ensure_fft_z_attr<T>();
   dim3 grid((P.Nxh + TK - 1) / TK, P.Ny + 1, 3);
   probe_begin(PROBE_FFT_Z, s);
-  k_fft_z<T><<<grid, 256, sm, s>>>(data, Nz, logNz, P.Ny, P.Px, P.Nxh, inverse ? 1 : 0, tw, 0, 1, TK);
+  k_fft_z<T><<<grid, fz_threads(TK, Nz), sm, s>>>(data, Nz, logNz, P.Ny, P.Px, P.Nxh, inverse ? 1 : 0, tw, 0,
+                                                   1, TK);
   count_launches(1);
   probe_end(PROBE_FFT_Z, s);
   return cudaGetLastError();
@@ -325,6 +339,68 @@ cudaError_t launch_poisson(const Params& P, Workspace& W, const T* rho, T* phi, 
   }
   if (e == cudaSuccess) e = launch_poisson_residual<T>(P, rho_keep, phi, nullptr, W.rnorm + 2 * sweeps, s);
   return e;
+}
+
+// Launch-shape autotuner of the transforms: times each candidate shape of the
+// x transform (row pairs per block, threads) and of the z transform (columns
+// per block) on the handle's own potential and spectrum buffers at the
+// Poisson sizes, and keeps the fastest in P.  Blocks until done.
+template <typename T>
+cudaError_t tune_transforms_t(Params& P, Workspace& W, cudaStream_t s, float* best_ms) {
+  const int N = P.Nx, R = P.Nz * P.Ny;
+  T* grid = reinterpret_cast<T*>(W.phi);
+  cplx<T>* S = reinterpret_cast<cplx<T>*>(W.spec);
+  const cplx<T>* twx = reinterpret_cast<const cplx<T>*>(W.tw_x);
+  const cplx<T>* twz = reinterpret_cast<const cplx<T>*>(W.tw_z);
+  cudaError_t e = launch_fill_zero<T>(grid, (size_t)P.Nx * P.Ny * P.Nz, s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  auto time_it = [&](auto&& launch) -> float {
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int i = 0; i < 10 && e == cudaSuccess; ++i) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 1e30f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    return ms / 10.0f;
+  };
+  Params Q = P;
+  float bx = 1e30f, bz = 1e30f;
+  int best_pp = P.fx_pp, best_th = P.fx_threads, best_tk = P.fz_tk;
+  int last_pp = 0;
+  for (int vals = 128; vals <= 2048 && e == cudaSuccess; vals *= 2) {
+    const int pp = vals / N < 1 ? 1 : vals / N;
+    if (pp == last_pp) continue;
+    if (2 * (size_t)pp * N * sizeof(cplx<T>) + 2 * (size_t)pp * sizeof(T) > 48 * 1024) break;
+    last_pp = pp;
+    int th = pp * N / 4;
+    th = th < 32 ? 32 : (th > 256 ? 256 : th);
+    Q.fx_pp = pp;
+    Q.fx_threads = th;
+    const float ms = time_it([&] { return fft_x_forward<T>(Q, grid, R, S, T(1), P.Ny, T(0), T(0), twx, s); });
+    if (ms < bx) { bx = ms; best_pp = pp; best_th = th; }
+  }
+  Q = P;
+  for (int tk = 1; tk <= max_tile_z(P.Nz, sizeof(cplx<T>)) && e == cudaSuccess; tk *= 2) {
+    Q.fz_tk = tk;
+    const float ms = time_it([&] { return fft_z<T>(Q, S, P.Ny, 1, 0, false, twz, s); });
+    if (ms < bz) { bz = ms; best_tk = tk; }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  P.fx_pp = best_pp;
+  P.fx_threads = best_th;
+  P.fz_tk = best_tk;
+  best_ms[0] = bx;
+  best_ms[1] = bz;
+  return cudaSuccess;
+}
+
+cudaError_t tune_transforms(Params& P, Workspace& W, bool mixed, cudaStream_t s, float* best_ms) {
+  return mixed ? tune_transforms_t<float>(P, W, s, best_ms) : tune_transforms_t<double>(P, W, s, best_ms);
 }
 
 template cudaError_t launch_poisson<float>(const Params&, Workspace&, const float*, float*, cudaStream_t);

@@ -67,6 +67,59 @@ PRECS = [dg.FP64, dg.MIXED]
 BCS = [(0, 0), (1, 1), (0, 1), (1, 0)]
 
 
+SHAPES = [(1, 32, 1), (4, 64, 4), (16, 256, 16), (32, 512, 2)]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_transform_shapes(prec, shape):
+    """Every launch shape the transform autotuner may pick gives the same
+    Poisson and Stokes solutions (32 x 16 x 32: 1..64 row pairs per x block,
+    1..16 columns per z block)."""
+    rng = np.random.default_rng(13)
+    cfg, rec = _small_dry((0, 1), phi_b=(0.3, -0.2), surf=(0.0, 0.01))
+    cfg.precision = prec
+    cfg.eta = 0.7
+    cfg.wet = True
+    h = dg.Discos(cfg)
+    h.set_transform_shape(*shape)
+    Nx, Ny, Nz = cfg.dims
+    rho = rng.normal(size=(Nz, Ny, Nx))
+    rd = torch.tensor(rho, dtype=_dtype(prec), device="cuda")
+    phi = h.solve_poisson(rd).double().cpu().numpy()
+    ref = poisson.solve(rd.double().cpu().numpy(), cfg.bc, cfg.lB, cfg.phi_b, cfg.surf_charge)
+    assert rel_l2(phi, ref) < TOL[prec]["phi"]
+    h0 = dg.Discos(cfg)
+    f = torch.tensor(rng.normal(size=Nx * Nz * (3 * Ny + 1)), dtype=_dtype(prec), device="cuda")
+    u, v, w = mac_split(f.cpu().numpy(), cfg.dims)
+    v[:, 0, :] = 0.0
+    v[:, -1, :] = 0.0
+    f = torch.tensor(mac_join(u, v, w), dtype=_dtype(prec), device="cuda")
+    vel = h.solve_stokes(f.clone()).double().cpu().numpy()
+    vel0 = h0.solve_stokes(f.clone()).double().cpu().numpy()
+    assert rel_l2(vel, vel0) < TOL[prec]["vel"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_transform_tuner(prec):
+    cfg, rec = _small_dry((0, 0))
+    cfg.precision = prec
+    h = dg.Discos(cfg)
+    pp, th, tk, ms = h.tune_transforms()
+    assert 1 <= pp and pp * cfg.Nx <= 2048 and th % 32 == 0 and tk in (1, 2, 4, 8, 16) and min(ms) > 0
+    xd, qd, pos, q, _ = _setup(cfg, rec, prec)
+    rho = h.spread_charge(xd, qd)
+    phi = h.solve_poisson(rho).double().cpu().numpy()
+    ref = poisson.solve(rho.double().cpu().numpy(), cfg.bc, cfg.lB, cfg.phi_b, cfg.surf_charge)
+    assert rel_l2(phi, ref) < TOL[prec]["phi"]
+    with pytest.raises(dg.DiscosError):
+        h.set_transform_shape(0, 32, 1)
+    with pytest.raises(dg.DiscosError):
+        h.set_transform_shape(1, 33, 1)
+    with pytest.raises(dg.DiscosError):
+        h.set_transform_shape(1, 32, 3)
+
+
 @pytest.mark.parametrize("bc", BCS)
 def test_poisson_refinement(bc):
     """Mixed precision with double-precision residual refinement: the
