@@ -216,7 +216,7 @@ def run_ours(args):
     avg_s = probe_ms * 1e-3 / max(probe_n, 1)
     achieved = nbytes / avg_s / 1e9 if nbytes else None
     rl = {"roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                       "frac": achieved / peak if achieved else None, "traffic": None,
+                       "frac": achieved / peak if achieved else None, "traffic": MEASURED_TRAFFIC.get(dominant),
                        "algorithmic_bytes_per_launch": nbytes, "avg_launch_us": avg_s * 1e6,
                        "launches_timed": probe_n, "peak_source": "measured" if peaks else "fallback"},
           "stages_ms": {k: round(v, 5) for k, v in breakdown.items()}}
@@ -425,6 +425,12 @@ def _peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return None
+
+
+# DRAM bytes per launch of a family (cold-cache, one ncu capture of one
+# measured step of `bench.py --profile`; the command and the per-kernel table
+# are in profiles/transforms_scans_dram_wet_channel_128x64x128.md).
+MEASURED_TRAFFIC = {"fft_x": 9.486e6, "fft_z": 10.537e6, "stokes_y": 25.636e6}
 
 
 def algorithmic_bytes(family, cfg, N):

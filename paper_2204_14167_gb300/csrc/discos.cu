@@ -863,7 +863,8 @@ discos_status discos_set_transform_shape(discos_handle* h, int fx_pairs, int fx_
   if (!h) return invalid("null handle");
   const size_t elem = h->mixed ? 2 * sizeof(float) : 2 * sizeof(double);
   const int N = h->P.Nx;
-  if (fx_pairs < 1 || (size_t)fx_pairs * N > 2048 || 2 * (size_t)fx_pairs * N * elem + 2 * (size_t)fx_pairs * elem > 48 * 1024)
+  if (fx_pairs < 1 || (size_t)fx_pairs * N > 2048 ||
+      (2 * (size_t)fx_pairs * N + N / 2) * elem + 2 * (size_t)fx_pairs * elem > 48 * 1024)
     return invalid("fx_pairs: 1 .. 2048 / Nx row pairs within 48 KB of shared memory");
   if (fx_threads < 32 || fx_threads > 1024 || fx_threads % 32) return invalid("fx_threads: a multiple of 32 in 32..1024");
   if (fz_tile < 1 || (fz_tile & (fz_tile - 1)) || fz_tile > max_tile_z(h->P.Nz, elem))

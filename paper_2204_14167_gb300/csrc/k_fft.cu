@@ -92,7 +92,9 @@ __global__ void k_rfft_x(const T* __restrict__ in, int R, int N, int logN, int P
   const int PP = pairs_per_block;
   cplx<T>* bufa = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* bufb = bufa + (size_t)PP * N;
-  T* rowadd = reinterpret_cast<T*>(bufb + (size_t)PP * N);   // [2 PP] wall terms of each row
+  cplx<T>* stw = bufb + (size_t)PP * N;                        // twiddles, staged once per block
+  T* rowadd = reinterpret_cast<T*>(stw + N / 2);               // [2 PP] wall terms of each row
+  for (int t = threadIdx.x; t < N / 2; t += blockDim.x) stw[t] = tw[t];
   for (int t = threadIdx.x; t < 2 * PP; t += blockDim.x) {
     const int row = 2 * blockIdx.x * PP + t;
     const int y = row % Nyr;
@@ -108,7 +110,7 @@ __global__ void k_rfft_x(const T* __restrict__ in, int R, int N, int logN, int P
     bufa[idx] = cplx<T>{a, b};
   }
   __syncthreads();
-  cplx<T>* r = fft_stockham(bufa, bufb, N, logN, PP, N, tw, false);
+  cplx<T>* r = fft_stockham(bufa, bufb, N, logN, PP, N, stw, false);
   const int M = N / 2 + 1;
   // idx / M by a float reciprocal: idx < 2^16, so (idx + 1/2) / M stays at
   // least 1/(2M) away from an integer, far beyond the rounding of the product
@@ -135,6 +137,8 @@ __global__ void k_irfft_x(const cplx<T>* __restrict__ in, int R, int N, int logN
   const int PP = pairs_per_block;
   cplx<T>* bufa = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* bufb = bufa + (size_t)PP * N;
+  cplx<T>* stw = bufb + (size_t)PP * N;                        // twiddles, staged once per block
+  for (int t = threadIdx.x; t < N / 2; t += blockDim.x) stw[t] = tw[t];
   const int hN = N / 2;
   for (int idx = threadIdx.x; idx < PP * N; idx += blockDim.x) {
     const int v = idx >> logN, k = idx & (N - 1);
@@ -148,7 +152,7 @@ __global__ void k_irfft_x(const cplx<T>* __restrict__ in, int R, int N, int logN
     bufa[idx] = cplx<T>{A.re - B.im, A.im + B.re};   // Z = A + i B
   }
   __syncthreads();
-  cplx<T>* r = fft_stockham(bufa, bufb, N, logN, PP, N, tw, true);
+  cplx<T>* r = fft_stockham(bufa, bufb, N, logN, PP, N, stw, true);
   for (int idx = threadIdx.x; idx < PP * N; idx += blockDim.x) {
     const int v = idx >> logN, n = idx & (N - 1);
     int p = blockIdx.x * PP + v;
@@ -172,6 +176,7 @@ __global__ void k_fft_z(cplx<T>* __restrict__ data, int Nz, int logNz, int Nyr, 
   const int vs = Nz + 1;
   cplx<T>* bufa = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* bufb = bufa + (size_t)TK * vs;
+  cplx<T>* stw = bufb + (size_t)TK * vs;                       // twiddles, staged once per block
   cplx<T>* base = data + blockIdx.z * field_stride;
   if (mac) {
     const int Ny = Nyr;
@@ -181,6 +186,7 @@ __global__ void k_fft_z(cplx<T>* __restrict__ data, int Nz, int logNz, int Nyr, 
   }
   const int y = blockIdx.y;
   if (y >= Nyr) return;
+  for (int t = threadIdx.x; t < Nz / 2; t += blockDim.x) stw[t] = tw[t];
   const int kx0 = blockIdx.x * TK;
   const int logTK = 31 - __clz(TK);
   for (int idx = threadIdx.x; idx < TK * Nz; idx += blockDim.x) {
@@ -192,7 +198,7 @@ __global__ void k_fft_z(cplx<T>* __restrict__ data, int Nz, int logNz, int Nyr, 
   }
   __syncthreads();
   const int nv = Nxh - kx0 < TK ? Nxh - kx0 : TK;   // the last tile holds fewer columns
-  cplx<T>* r = fft_stockham(bufa, bufb, Nz, logNz, nv, vs, tw, inverse != 0);
+  cplx<T>* r = fft_stockham(bufa, bufb, Nz, logNz, nv, vs, stw, inverse != 0);
   for (int idx = threadIdx.x; idx < TK * Nz; idx += blockDim.x) {
     const int z = idx >> logTK, c = idx & (TK - 1);
     int kx = kx0 + c;
@@ -242,7 +248,7 @@ cudaError_t fft_x_forward(const Params& P, const T* in, int R, cplx<T>* out, T s
   int pp = P.fx_pp;
   int pairs = (R + 1) / 2;
   int nb = (pairs + pp - 1) / pp;
-  size_t sm = 2 * (size_t)pp * N * sizeof(cplx<T>) + 2 * (size_t)pp * sizeof(T);
+  size_t sm = (2 * (size_t)pp * N + N / 2) * sizeof(cplx<T>) + 2 * (size_t)pp * sizeof(T);
   probe_begin(PROBE_FFT_X, s);
   k_rfft_x<T><<<nb, P.fx_threads, sm, s>>>(in, R, N, logN, P.Px, out, scale, Nyr, add0, add1, tw, pp);
   count_launches(1);
@@ -257,7 +263,7 @@ cudaError_t fft_x_inverse(const Params& P, const cplx<T>* in, int R, T* out, T s
   int pp = P.fx_pp;
   int pairs = (R + 1) / 2;
   int nb = (pairs + pp - 1) / pp;
-  size_t sm = 2 * (size_t)pp * N * sizeof(cplx<T>);
+  size_t sm = (2 * (size_t)pp * N + N / 2) * sizeof(cplx<T>);
   probe_begin(PROBE_FFT_X, s);
   k_irfft_x<T><<<nb, P.fx_threads, sm, s>>>(in, R, N, logN, P.Px, out, scale, tw, pp);
   count_launches(1);
@@ -270,7 +276,7 @@ cudaError_t fft_z(const Params& P, cplx<T>* data, int Nyr, int nfields, size_t f
                   const cplx<T>* tw, cudaStream_t s) {
   int Nz = P.Nz, logNz = 31 - __builtin_clz((unsigned)Nz);
   const int TK = P.fz_tk;
-  size_t sm = 2 * (size_t)TK * (Nz + 1) * sizeof(cplx<T>);
+  size_t sm = (2 * (size_t)TK * (Nz + 1) + Nz / 2) * sizeof(cplx<T>);
   ensure_fft_z_attr<T>();
   dim3 grid((P.Nxh + TK - 1) / TK, Nyr, nfields);
   probe_begin(PROBE_FFT_Z, s);
@@ -285,7 +291,7 @@ template <typename T>
 cudaError_t fft_z_mac(const Params& P, cplx<T>* data, bool inverse, const cplx<T>* tw, cudaStream_t s) {
   int Nz = P.Nz, logNz = 31 - __builtin_clz((unsigned)Nz);
   const int TK = P.fz_tk;
-  size_t sm = 2 * (size_t)TK * (Nz + 1) * sizeof(cplx<T>);
+  size_t sm = (2 * (size_t)TK * (Nz + 1) + Nz / 2) * sizeof(cplx<T>);
   ensure_fft_z_attr<T>();
   dim3 grid((P.Nxh + TK - 1) / TK, P.Ny + 1, 3);
   probe_begin(PROBE_FFT_Z, s);
@@ -373,7 +379,7 @@ cudaError_t tune_transforms_t(Params& P, Workspace& W, cudaStream_t s, float* be
   for (int vals = 128; vals <= 2048 && e == cudaSuccess; vals *= 2) {
     const int pp = vals / N < 1 ? 1 : vals / N;
     if (pp == last_pp) continue;
-    if (2 * (size_t)pp * N * sizeof(cplx<T>) + 2 * (size_t)pp * sizeof(T) > 48 * 1024) break;
+    if ((2 * (size_t)pp * N + N / 2) * sizeof(cplx<T>) + 2 * (size_t)pp * sizeof(T) > 48 * 1024) break;
     last_pp = pp;
     int th = pp * N / 4;
     th = th < 32 ? 32 : (th > 256 ? 256 : th);
