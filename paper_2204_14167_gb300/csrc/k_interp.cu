@@ -153,6 +153,160 @@ __global__ void k_interp_velocity(const T* __restrict__ x, int N, Params P, cons
   }
 }
 
+// The same two gathers with the stencil width W fixed at compile time (4 and
+// 6 points): each lane fetches the y and z weights of its group once, the
+// wall rules of the W (+1) rows are resolved once per ion, and the stencil
+// loops unroll into independent loads.
+template <typename T, int W>
+__global__ void k_interp_efield_w(const T* __restrict__ x, const T* __restrict__ q, int N, Params P,
+                                  const T* __restrict__ phi, T* __restrict__ out, int as_force,
+                                  const T* __restrict__ F_add) {
+  const KernelParams kp = P.kes;
+  const int Nx = P.Nx, Ny = P.Ny;
+  const auto& Q = phys(P, T());
+  int ion = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  int l = threadIdx.x & 7;
+  int gbase = (threadIdx.x & 31) & ~7;
+  bool valid = ion < N;
+  T p[3] = {T(0.5), T(0.5), T(0.5)};
+  if (valid) { p[0] = x[ion]; p[1] = x[N + ion]; p[2] = x[2 * N + ion]; }
+  int c0[3];
+  T cw[3], ew[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    c0[d] = stencil_start(p[d], W) - 1;
+    const int c = c0[d] + l;
+    const bool in = l <= W;
+    cw[d] = in ? kval(p[d] - (T(c) + T(0.5)), kp) : T(0);
+    ew[d] = in ? (kval(p[d] - T(c + 1), kp) - kval(p[d] - T(c), kp)) : T(0);
+  }
+  T cy[W + 1], ey[W + 1], cz[W + 1], ez[W + 1], rs[W + 1], ra[W + 1];
+  int roff[W + 1];
+#pragma unroll
+  for (int j = 0; j <= W; ++j) {
+    cy[j] = __shfl_sync(0xffffffffu, cw[1], gbase + j);
+    ey[j] = __shfl_sync(0xffffffffu, ew[1], gbase + j);
+    cz[j] = __shfl_sync(0xffffffffu, cw[2], gbase + j);
+    ez[j] = __shfl_sync(0xffffffffu, ew[2], gbase + j);
+    // phi at row iy = rs * phi[row] + ra (ghost rows of Eqs. esbc1 / esbc3)
+    const int iy = c0[1] + j;
+    int row = iy;
+    T sg = T(1), ad = T(0);
+    if (iy < 0) {
+      int m = -1 - iy;
+      m = m < Ny ? m : Ny - 1;
+      row = m;
+      if (P.bc[0] == DISCOS_BC_DIRICHLET) { sg = T(-1); ad = T(2) * T(Q.phi_b[0]); }
+      else ad = -T(Q.slope[0]) * T(2 * m + 1);
+    } else if (iy >= Ny) {
+      int m = iy - Ny;
+      m = m < Ny ? m : Ny - 1;
+      row = Ny - 1 - m;
+      if (P.bc[1] == DISCOS_BC_DIRICHLET) { sg = T(-1); ad = T(2) * T(Q.phi_b[1]); }
+      else ad = T(Q.slope[1]) * T(2 * m + 1);
+    }
+    roff[j] = row * Nx;
+    rs[j] = sg;
+    ra[j] = ad;
+  }
+  T Ex = T(0), Ey = T(0), Ez = T(0);
+  if (valid && l <= W) {
+    const int ix = (c0[0] + l) & (Nx - 1);
+#pragma unroll
+    for (int jz = 0; jz <= W; ++jz) {
+      const size_t zoff = (size_t)((c0[2] + jz) & (P.Nz - 1)) * Ny * Nx + ix;
+      T a1 = T(0), a2 = T(0);
+#pragma unroll
+      for (int jy = 0; jy <= W; ++jy) {
+        const T v = rs[jy] * phi[zoff + roff[jy]] + ra[jy];
+        a1 += v * cy[jy];
+        a2 += v * ey[jy];
+      }
+      Ex += a1 * cz[jz];
+      Ey += a2 * cz[jz];
+      Ez += a1 * ez[jz];
+    }
+    Ex *= ew[0];
+    Ey *= cw[0];
+    Ez *= cw[0];
+  }
+  Ex = group_sum8(Ex);
+  Ey = group_sum8(Ey);
+  Ez = group_sum8(Ez);
+  if (valid && l == 0) {
+    if (as_force) {
+      T qq = q[ion];
+      T a0 = F_add ? F_add[ion] : T(0), a1 = F_add ? F_add[N + ion] : T(0), a2 = F_add ? F_add[2 * N + ion] : T(0);
+      out[ion] = qq * (Ex + T(Q.E_ext[0])) + a0;
+      out[N + ion] = qq * (Ey + T(Q.E_ext[1])) + a1;
+      out[2 * N + ion] = qq * (Ez + T(Q.E_ext[2])) + a2;
+    } else {
+      out[ion] = Ex; out[N + ion] = Ey; out[2 * N + ion] = Ez;
+    }
+  }
+}
+
+template <typename T, int W>
+__global__ void k_interp_velocity_w(const T* __restrict__ x, int N, Params P, const T* __restrict__ v,
+                                    T* __restrict__ out) {
+  const KernelParams kp = P.khy;
+  const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
+  int ion = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  int l = threadIdx.x & 7;
+  int gbase = (threadIdx.x & 31) & ~7;
+  bool valid = ion < N;
+  T p[3] = {T(0.5), T(0.5), T(0.5)};
+  if (valid) { p[0] = x[ion]; p[1] = x[N + ion]; p[2] = x[2 * N + ion]; }
+  const size_t G = (size_t)Nx * Ny * Nz;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T* g = v + (c >= 1 ? G : 0) + (c == 2 ? (size_t)Nx * (Ny + 1) * Nz : 0);
+    const int Nyg = c == 1 ? Ny + 1 : Ny;
+    int st[3];
+    T wv[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T sd = p[d] - (d == c ? T(0) : T(0.5));
+      st[d] = stencil_start(sd, W);
+      wv[d] = l < W ? kval(sd - T(st[d] + l), kp) : T(0);
+    }
+    T wy[W], wz[W];
+    int roff[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      wy[j] = __shfl_sync(0xffffffffu, wv[1], gbase + j);
+      wz[j] = __shfl_sync(0xffffffffu, wv[2], gbase + j);
+      int iy = st[1] + j;
+      T sg = T(1);
+      if (c == 1) {           // normal component: ghost face -m = -v(m)
+        if (iy < 0) { iy = -iy; sg = T(-1); }
+        else if (iy > Ny) { iy = 2 * Ny - iy; sg = T(-1); }
+      } else {                // tangential, no slip: ghost -1-m = -u(m)
+        if (iy < 0) { iy = -1 - iy; sg = T(-1); }
+        else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = T(-1); }
+      }
+      iy = iy < 0 ? 0 : (iy >= Nyg ? Nyg - 1 : iy);   // ions far outside only
+      roff[j] = iy * Nx;
+      wy[j] *= sg;
+    }
+    T acc = T(0);
+    if (valid && l < W) {
+      const int ix = (st[0] + l) & (Nx - 1);
+#pragma unroll
+      for (int jz = 0; jz < W; ++jz) {
+        const size_t zoff = (size_t)((st[2] + jz) & (Nz - 1)) * Nyg * Nx + ix;
+        T a = T(0);
+#pragma unroll
+        for (int jy = 0; jy < W; ++jy) a += wy[jy] * g[zoff + roff[jy]];
+        acc += a * wz[jz];
+      }
+      acc *= wv[0];
+    }
+    acc = group_sum8(acc);
+    if (valid && l == 0) out[(size_t)c * N + ion] = acc;
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -162,7 +316,9 @@ cudaError_t launch_interp_efield(const Params& P, const T* x, const T* q, int N,
   int bs = 256;
   int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
   probe_begin(PROBE_INTERP_E, s);
-  k_interp_efield<T><<<nb, bs, 0, s>>>(x, q, N, P, phi, out, as_force ? 1 : 0, F_add);
+  if (P.kes.w == 4) k_interp_efield_w<T, 4><<<nb, bs, 0, s>>>(x, q, N, P, phi, out, as_force ? 1 : 0, F_add);
+  else if (P.kes.w == 6) k_interp_efield_w<T, 6><<<nb, bs, 0, s>>>(x, q, N, P, phi, out, as_force ? 1 : 0, F_add);
+  else k_interp_efield<T><<<nb, bs, 0, s>>>(x, q, N, P, phi, out, as_force ? 1 : 0, F_add);
   count_launches(1);
   probe_end(PROBE_INTERP_E, s);
   return cudaGetLastError();
@@ -174,7 +330,9 @@ cudaError_t launch_interp_velocity(const Params& P, const T* x, int N, const T* 
   int bs = 256;
   int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
   probe_begin(PROBE_INTERP_V, s);
-  k_interp_velocity<T><<<nb, bs, 0, s>>>(x, N, P, v, out);
+  if (P.khy.w == 4) k_interp_velocity_w<T, 4><<<nb, bs, 0, s>>>(x, N, P, v, out);
+  else if (P.khy.w == 6) k_interp_velocity_w<T, 6><<<nb, bs, 0, s>>>(x, N, P, v, out);
+  else k_interp_velocity<T><<<nb, bs, 0, s>>>(x, N, P, v, out);
   count_launches(1);
   probe_end(PROBE_INTERP_V, s);
   return cudaGetLastError();

@@ -124,6 +124,137 @@ __global__ void k_spread_force(const T* __restrict__ x, const T* __restrict__ F,
   }
 }
 
+// The two spreads with the stencil width W fixed at compile time (4 and 6
+// points): the y and z weights of the group are fetched once, the image fold
+// of the W rows is resolved once per ion (and component), and the stencil
+// loops unroll into independent atomics.
+template <typename T, int W>
+__global__ void k_spread_charge_w(const T* __restrict__ x, const T* __restrict__ q, int N, Params P,
+                                  T* __restrict__ rho) {
+  const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
+  const KernelParams kp = P.kes;
+  int ion = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  int l = threadIdx.x & 7;
+  int gbase = (threadIdx.x & 31) & ~7;
+  bool valid = ion < N;
+  T px = T(0.5), py = T(0.5), pz = T(0.5), qq = T(0);
+  if (valid) { px = x[ion]; py = x[N + ion]; pz = x[2 * N + ion]; qq = q[ion]; }
+  const T sx = px - T(0.5), sy = py - T(0.5), sz = pz - T(0.5);
+  const int x0 = stencil_start(sx, W), y0 = stencil_start(sy, W), z0 = stencil_start(sz, W);
+  const T wx = l < W ? kval(sx - T(x0 + l), kp) : T(0);
+  const T wyl = l < W ? kval(sy - T(y0 + l), kp) : T(0);
+  const T wzl = l < W ? kval(sz - T(z0 + l), kp) : T(0);
+  const T s0 = P.bc[0] == DISCOS_BC_DIRICHLET ? T(-1) : T(1);
+  const T s1 = P.bc[1] == DISCOS_BC_DIRICHLET ? T(-1) : T(1);
+  T wy[W], wz[W];
+  int roff[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    wy[j] = __shfl_sync(0xffffffffu, wyl, gbase + j);
+    wz[j] = __shfl_sync(0xffffffffu, wzl, gbase + j);
+    int iy = y0 + j;
+    T sg = T(1);
+    if (iy < 0) { iy = -1 - iy; sg = s0; }
+    else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = s1; }
+    const bool in = iy >= 0 && iy < Ny;
+    roff[j] = in ? iy * Nx : 0;
+    wy[j] = in ? sg * wy[j] : T(0);
+  }
+  if (valid && l < W) {
+    const int ix = (x0 + l) & (Nx - 1);
+    const T qx = qq * wx;
+#pragma unroll
+    for (int jz = 0; jz < W; ++jz) {
+      const size_t zoff = (size_t)((z0 + jz) & (Nz - 1)) * Ny * Nx + ix;
+      const T qz = qx * wz[jz];
+#pragma unroll
+      for (int jy = 0; jy < W; ++jy)
+        if (wy[jy] != T(0)) atomicAdd(&rho[zoff + roff[jy]], qz * wy[jy]);
+    }
+  }
+}
+
+template <typename T, int W>
+__global__ void k_spread_force_w(const T* __restrict__ x, const T* __restrict__ F, int N, Params P,
+                                 T* __restrict__ f, long long step, int rfd) {
+  const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
+  const KernelParams kp = P.khy;
+  const int c = blockIdx.y;
+  int ion = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  int l = threadIdx.x & 7;
+  int gbase = (threadIdx.x & 31) & ~7;
+  bool valid = ion < N;
+  T p[3] = {T(0.5), T(0.5), T(0.5)};
+  T Fc = T(0);
+  T Wr[3] = {T(0), T(0), T(0)};
+  if (valid) {
+    p[0] = x[ion]; p[1] = x[N + ion]; p[2] = x[2 * N + ion];
+    Fc = F[(size_t)c * N + ion];
+    if (rfd) {
+      T g[4];
+      normals4(u32x4{(uint32_t)ion, (uint32_t)step, 0u, (uint32_t)TAG_RFD}, P.seed, g);
+      Wr[0] = g[0]; Wr[1] = g[1]; Wr[2] = g[2];
+    }
+  }
+  int st[3];
+  T wv[3], wd[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const T sd = p[d] - (d == c ? T(0) : T(0.5));
+    st[d] = stencil_start(sd, W);
+    const T z = sd - T(st[d] + l);
+    wv[d] = l < W ? kval(z, kp) : T(0);
+    wd[d] = (l < W && rfd) ? kder(z, kp) : T(0);
+  }
+  const T a = T(phys(P, T()).kT) * (c == 0 ? Wr[0] : (c == 1 ? Wr[1] : Wr[2]));
+  const int Nyg = (c == 1) ? Ny + 1 : Ny;
+  size_t off = 0;
+  if (c >= 1) off += (size_t)Nz * Ny * Nx;
+  if (c == 2) off += (size_t)Nz * (Ny + 1) * Nx;
+  T* g = f + off;
+  T wy[W], dy[W], wz[W], dz[W];
+  int roff[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    wy[j] = __shfl_sync(0xffffffffu, wv[1], gbase + j);
+    dy[j] = __shfl_sync(0xffffffffu, wd[1], gbase + j);
+    wz[j] = __shfl_sync(0xffffffffu, wv[2], gbase + j);
+    dz[j] = __shfl_sync(0xffffffffu, wd[2], gbase + j);
+    int iy = st[1] + j;
+    T sg = T(1);
+    bool ok;
+    if (c == 1) {             // y-faces 0..Ny; wall faces receive real + image = 0
+      if (iy < 0) { iy = -iy; sg = T(-1); }
+      else if (iy > Ny) { iy = 2 * Ny - iy; sg = T(-1); }
+      ok = iy > 0 && iy < Ny;
+    } else {                  // cell-centred in y
+      if (iy < 0) { iy = -1 - iy; sg = T(-1); }
+      else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = T(-1); }
+      ok = iy >= 0 && iy < Ny;
+    }
+    roff[j] = ok ? iy * Nx : 0;
+    const T keep = ok ? sg : T(0);
+    wy[j] *= keep;
+    dy[j] *= keep;
+  }
+  if (valid && l < W) {
+    const int ix = (st[0] + l) & (Nx - 1);
+    const T fx0 = Fc * wv[0];
+    const T r0 = a * Wr[0] * wd[0], r1 = a * Wr[1] * wv[0], r2 = a * Wr[2] * wv[0];
+#pragma unroll
+    for (int jz = 0; jz < W; ++jz) {
+      const size_t zoff = (size_t)((st[2] + jz) & (Nz - 1)) * Nyg * Nx + ix;
+#pragma unroll
+      for (int jy = 0; jy < W; ++jy) {
+        if (wy[jy] == T(0) && dy[jy] == T(0)) continue;
+        T val = fx0 * wy[jy] * wz[jz];
+        if (rfd) val += r0 * wy[jy] * wz[jz] + r1 * dy[jy] * wz[jz] + r2 * wy[jy] * dz[jz];
+        atomicAdd(&g[zoff + roff[jy]], val);
+      }
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_fill(T* __restrict__ p, size_t n) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -154,7 +285,9 @@ cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N,
   }
   int bs = 256;
   int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
-  k_spread_charge<T><<<nb, bs, 0, s>>>(x, q, N, P, rho);
+  if (P.kes.w == 4) k_spread_charge_w<T, 4><<<nb, bs, 0, s>>>(x, q, N, P, rho);
+  else if (P.kes.w == 6) k_spread_charge_w<T, 6><<<nb, bs, 0, s>>>(x, q, N, P, rho);
+  else k_spread_charge<T><<<nb, bs, 0, s>>>(x, q, N, P, rho);
   count_launches(1);
   probe_end(PROBE_SPREAD_CHARGE, s);
   return cudaGetLastError();
@@ -172,7 +305,9 @@ cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, 
   }
   int bs = 256;
   dim3 grid((unsigned)(((size_t)N * 8 + bs - 1) / bs), 3);
-  k_spread_force<T><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0);
+  if (P.khy.w == 4) k_spread_force_w<T, 4><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0);
+  else if (P.khy.w == 6) k_spread_force_w<T, 6><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0);
+  else k_spread_force<T><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0);
   count_launches(1);
   probe_end(PROBE_SPREAD_FORCE, s);
   return cudaGetLastError();

@@ -64,6 +64,16 @@ def _small_dry(bc=(0, 0), kernel=dg.KERNEL_PESKIN6, n=301, Ny=16, phi_b=(0.0, 0.
 
 
 PRECS = [dg.FP64, dg.MIXED]
+# kernels: the 4- and 6-point widths run the unrolled kernels, the 5-point
+# ES kernel the general-width ones
+KERNELS = [(dg.KERNEL_PESKIN4, 4), (dg.KERNEL_PESKIN6, 6), (dg.KERNEL_ES, 5)]
+
+
+def _with_kernel(cfg, kernel):
+    kind, w = kernel
+    cfg.kernel_es = cfg.kernel_hy = kind
+    cfg.es_w = (w, w)
+    return cfg
 BCS = [(0, 0), (1, 1), (0, 1), (1, 0)]
 
 
@@ -148,9 +158,10 @@ def test_poisson_refinement(bc):
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("bc", BCS)
-@pytest.mark.parametrize("kernel", [dg.KERNEL_PESKIN4, dg.KERNEL_PESKIN6])
+@pytest.mark.parametrize("kernel", KERNELS)
 def test_spread_charge(prec, bc, kernel):
-    cfg, rec = _small_dry(bc, kernel)
+    cfg, rec = _small_dry(bc)
+    _with_kernel(cfg, kernel)
     xd, qd, pos, q, _ = _setup(cfg, rec, prec)
     h = dg.Discos(cfg)
     rho = h.spread_charge(xd, qd).double().cpu().numpy()
@@ -178,8 +189,10 @@ def test_poisson(prec, bc):
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("bc", BCS)
-def test_efield_interpolation(prec, bc):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_efield_interpolation(prec, bc, kernel):
     cfg, rec = _small_dry(bc, phi_b=(0.25, -0.5), surf=(0.01, -0.02))
+    _with_kernel(cfg, kernel)
     xd, qd, pos, q, _ = _setup(cfg, rec, prec)
     rng = np.random.default_rng(12)
     Nx, Ny, Nz = cfg.dims
@@ -239,8 +252,10 @@ def test_total_forces(prec, bc):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_spread_force(prec):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_spread_force(prec, kernel):
     cfg, rec = _small_dry((0, 0), kernel=dg.KERNEL_PESKIN4, n=205)
+    _with_kernel(cfg, kernel)
     xd, qd, pos, q, sp = _setup(cfg, rec, prec)
     rng = np.random.default_rng(13)
     Fh = rng.normal(size=(3, pos.shape[1]))
@@ -273,8 +288,10 @@ def test_stokes(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_velocity_interpolation(prec):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_velocity_interpolation(prec, kernel):
     cfg, rec = _small_dry((0, 0), kernel=dg.KERNEL_PESKIN4, n=203)
+    _with_kernel(cfg, kernel)
     xd, qd, pos, q, sp = _setup(cfg, rec, prec)
     rng = np.random.default_rng(15)
     Nx, Ny, Nz = cfg.dims
