@@ -42,7 +42,7 @@ def clocks_sampler():
     path = os.path.join("/tmp", f"discos_clocks_{os.getpid()}.csv")
     try:
         f = open(path, "w")
-        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "50"],
                              stdout=f, stderr=subprocess.DEVNULL)
     except Exception:
         return lambda dev: None
@@ -156,6 +156,9 @@ def run_ours(args):
 
     # dominant kernel family (by per-step time), then the timed region with a
     # live event probe on that family
+    # clock samples from here to the end of the timed region (the probe
+    # pre-pass keeps the GPU under the same load while nvidia-smi starts)
+    stop_clocks = clocks_sampler()
     breakdown, step = kernel_breakdown(dg, h, x, qd, step)
     dominant = max(breakdown, key=breakdown.get)
     dg.probe(h, dominant)
@@ -163,7 +166,6 @@ def run_ours(args):
     # device-timed region: K steps, L2 flushed between steps (outside the events)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stop_clocks = clocks_sampler()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -420,6 +422,26 @@ def run_profile(args):
     print(f"profile: {n1 - n0} warm-up launches, {dg.launch_count() - n1} measured launches")
 
 
+def run_profile_batched(args):
+    """Batched replicas alone for ncu: 152 replicas of 32^3 (one per SM), one
+    launch per step, no graph."""
+    import torch
+    import paper_2204_14167_gb300 as dg
+    from paper_2204_14167_gb300 import presets
+    cfg, rec = presets.batched_channels_32(R=152)
+    pos, q, sp, off = presets.batched_ions(cfg, rec)
+    h = dg.Discos(cfg)
+    x = torch.tensor(pos, dtype=torch.float32, device="cuda").contiguous()
+    qd = torch.tensor(q, dtype=torch.float32, device="cuda")
+    b = h.make_batch(x, qd, off)
+    h.set_batched_shape(1)
+    for k in range(args.warmup + args.steps):
+        h.step_batched(b, step0=k, nsteps=1)
+    torch.cuda.synchronize()
+    print(f"profile-batched: {off[-1]} ions in {len(off) - 1} replicas, {args.warmup + args.steps} launches, "
+          f"fault word {h.fault(sync=True)}")
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -495,11 +517,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the production-form measurements")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="run only batched-replica steps (for ncu)")
     ap.add_argument("--profile", action="store_true",
                     help="only W warm-up steps and K steps of the workload (for ncu), no timing output")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
+    elif args.profile_batched:
+        run_profile_batched(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
