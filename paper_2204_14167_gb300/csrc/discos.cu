@@ -475,6 +475,11 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
     f.lB = (float)P.lB;
     f.psi = (float)P.psi;
     f.tab_scale = (float)P.tab_scale;
+    P.inv_eta = P.eta > 0.0 ? 1.0 / P.eta : 0.0;
+    P.inv_nxnz = 1.0 / ((double)c.Nx * c.Nz);
+    f.eta = (float)P.eta;
+    f.inv_eta = (float)P.inv_eta;
+    f.inv_nxnz = (float)P.inv_nxnz;
   }
   P.k_cell = k;
   P.ncx = c.Nx / k; P.ncy = std::max(1, c.Ny / k); P.ncz = c.Nz / k;

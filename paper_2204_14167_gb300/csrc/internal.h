@@ -22,6 +22,7 @@ struct PhysF {
   float wall_sigma[DISCOS_MAX_SPECIES], wall_xi[DISCOS_MAX_SPECIES], wall_rc[DISCOS_MAX_SPECIES];
   float E_ext[3], slope[2], phi_b[2];
   float dt, kT, inv_kT, lB, psi, tab_scale;
+  float eta, inv_eta, inv_nxnz;
 };
 
 // Everything a kernel needs to know about the run, passed by value.
@@ -51,6 +52,7 @@ struct Params {
   int fx_pp, fx_threads, fz_tk;  // transform launch shapes (k_fft.cu; discos_tune_transforms)
   unsigned* fault;             // device fault word: bit 0 non-finite position, bit 1 escaped ion
   double inv_D_dry[DISCOS_MAX_SPECIES], inv_kT;
+  double inv_eta, inv_nxnz;    // 1 / eta (0 without a fluid), 1 / (Nx Nz): the transforms' normalisation
   PhysF f;
 };
 

@@ -116,7 +116,7 @@ template <typename TS> __device__ __forceinline__ C<double> ldc(const cplx<TS>* 
 template <typename TS, typename TC, int R>
 __global__ void k_poisson_scan(cplx<TS>* __restrict__ S, const TC* __restrict__ piv, const int* __restrict__ list,
                                int n_list, const unsigned char* __restrict__ skip, int Ny, int Nz, int Nxh, int Px,
-                               int singular, double norm) {
+                               int singular, TC norm) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= n_list) return;
@@ -210,7 +210,7 @@ __global__ void k_poisson_scan(cplx<TS>* __restrict__ S, const TC* __restrict__ 
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     int j = j0 + r;
-    if (j < Ny) col[(size_t)j * Px] = cplx<TS>{(TS)(x[r].r * (TC)norm), (TS)(x[r].i * (TC)norm)};
+    if (j < Ny) col[(size_t)j * Px] = cplx<TS>{(TS)(x[r].r * norm), (TS)(x[r].i * norm)};
   }
 }
 
@@ -252,8 +252,9 @@ __global__ void k_stokes_scan(cplx<TS>* __restrict__ S, cplx<TS>* __restrict__ S
   const TC gzr = MC[5 * (size_t)mode + 2], gzi = MC[5 * (size_t)mode + 3];
   const TC mik2 = MC[5 * (size_t)mode + 4];
   const TC K2 = mik2 != TC(0) ? TC(-1) / mik2 : TC(0);
-  const TC eta = (TC)P.eta, ieta = (TC)(1.0 / P.eta);
-  const TC norm = (TC)(1.0 / ((double)P.Nx * P.Nz));
+  const auto& Q = phys(P, TC());      // constants in the arithmetic type, no conversions
+  const TC eta = Q.eta, ieta = Q.inv_eta;
+  const TC norm = Q.inv_nxnz;
   const int j0 = lane * R;
   C<TC> fx[R], fz[R], fy[R], g[R];
 #pragma unroll
@@ -446,7 +447,7 @@ cudaError_t poisson_scan_launch(const Params& P, cplx<TS>* S, const TC* piv, con
                                 const unsigned char* skip, cudaStream_t s) {
   const int Ny = P.Ny;
   const int singular = (P.bc[0] == DISCOS_BC_NEUMANN && P.bc[1] == DISCOS_BC_NEUMANN) ? 1 : 0;
-  const double norm = 1.0 / ((double)P.Nx * P.Nz);
+  const TC norm = (TC)P.inv_nxnz;
   const int bs = 256;
   const int nb = (n * 32 + bs - 1) / bs;
   if (n <= 0) return cudaSuccess;
