@@ -452,7 +452,7 @@ def _peaks():
 # DRAM bytes per launch of a family (cold-cache, one ncu capture of one
 # measured step of `bench.py --profile`; the command and the per-kernel table
 # are in profiles/transforms_scans_dram_wet_channel_128x64x128.md).
-MEASURED_TRAFFIC = {"fft_x": 9.486e6, "fft_z": 10.537e6, "stokes_y": 25.636e6}
+MEASURED_TRAFFIC = {"fft_x": 9.486e6, "fft_z": 10.537e6, "stokes_y": 25.646e6}
 
 
 def algorithmic_bytes(family, cfg, N):
