@@ -79,7 +79,7 @@ def iceo_channel_256x128x256(precision=MIXED):
     """256 x 128 x 256 channel, conducting (Dirichlet phi = 0) bottom wall and
     dielectric (Neumann, no surface charge) top wall, 200k + 200k ions
     uniform in y in [1, 127] and at least 0.9 sigma apart, l_B = 0.96, ion
-    WCA sigma = 0.6, E_x = 0.02, dt = 1e-4 (stable at WCA contact),
+    WCA sigma = 0.6, E_x = 0.02, dt = 5e-5 (stable at WCA contact),
     the full wet step of the 128 x 64 x 128 channel (fluctuating Stokes,
     thermal drift, near-wall mobility)."""
     cfg, rec = wet_channel_128x64x128(precision)
@@ -92,9 +92,10 @@ def iceo_channel_256x128x256(precision=MIXED):
     cfg.E_ext = (0.02, 0.0, 0.0)
     cfg.gamma_coef = [mobility.gamma_table(0.5 * A_WET_PESKIN4, A_WET_PESKIN4, float(Ny))]
     cfg.max_ions = 400000
-    # explicit Euler-Maruyama is stable at WCA contact for dt D_tot U''(sigma) < 1;
-    # U''(0.6) ~ 3000 kT per cell^2 with D_tot ~ 2.2 gives dt = 1e-4
-    cfg.dt = 1e-4
+    # explicit Euler-Maruyama is stable near WCA contact for dt D_tot U''(r) < 1;
+    # at the placement minimum r = 0.9 sigma = 0.54, U'' ~ 6500 kT per cell^2,
+    # and with D_tot ~ 2.2 this gives dt = 5e-5 (0.7)
+    cfg.dt = 5e-5
     for k, v in _wca(0.6).items():
         setattr(cfg, k, v)
     return cfg, dict(n_pos=200000, n_neg=200000, ymargin=1.0, min_sep=0.9 * 0.6, seed=20220503)
