@@ -8,6 +8,7 @@
 // Both use a radix-2 Stockham transform (natural order, no bit reversal).
 // y: the tridiagonal wall-normal system of every (kx, kz) mode, solved by
 //    warp-parallel scans over pre-factored pivots (k_ysolve.cu).
+#include <atomic>
 #include <type_traits>
 #include "internal.h"
 
@@ -233,11 +234,14 @@ int default_tile_z(int Nz, size_t elem) {
 
 template <typename T>
 void ensure_fft_z_attr() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(k_fft_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    done = true;
-  }
+  // the attribute belongs to the current device: set it once per device
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  const unsigned long long bit = 1ull << dev;
+  if (done.load() & bit) return;
+  if (cudaFuncSetAttribute(k_fft_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) == cudaSuccess)
+    done.fetch_or(bit);
 }
 
 // Shared by the Poisson and Stokes paths.
