@@ -104,6 +104,19 @@ class RunConfig:
         return c
 
 
+def _need(t, n, dtype, name, dtypes=None):
+    """Reject a device array that the library would read or write past, or
+    misread: it must be a contiguous CUDA tensor of the handle's type with at
+    least n elements (None passes: the argument is optional)."""
+    if t is None:
+        return
+    ok_type = t.dtype in dtypes if dtypes else t.dtype == dtype
+    if not (getattr(t, "is_cuda", False) and ok_type and t.is_contiguous() and t.numel() >= n):
+        where = "" if getattr(t, "is_cuda", False) else " on the host"
+        raise ValueError(f"{name}: need a contiguous CUDA tensor of {dtype} with at least {n} elements, "
+                         f"got shape {tuple(t.shape)} {t.dtype}{where}")
+
+
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
@@ -148,6 +161,21 @@ class Discos:
         assert x.is_cuda and x.dtype == self.dtype and x.is_contiguous() and x.shape[0] == 3, "bad positions"
         return x.shape[1]
 
+    def _G(self):
+        Nx, Ny, Nz = self.cfg.dims
+        return Nx * Ny * Nz
+
+    def _Gf(self):
+        Nx, Ny, Nz = self.cfg.dims
+        return Nx * Nz * (3 * Ny + 1)
+
+    def _ions_q(self, x, q, species=None):
+        import torch
+        N = self._check_ions(x)
+        _need(q, N, self.dtype, "q")
+        _need(species, N, torch.int32, "species")
+        return N
+
     def empty_grid(self, kind="cell"):
         import torch
         Nx, Ny, Nz = self.cfg.dims
@@ -158,23 +186,30 @@ class Discos:
 
     # -- entry points
     def spread_charge(self, x, q, out=None, stream=None):
-        N = self._check_ions(x)
+        N = self._ions_q(x, q)
+        _need(out, self._G(), self.dtype, "out")
         rho = self.empty_grid("cell") if out is None else out
         _lib.check(self._lib.discos_spread(self._h, _ptr(x), _ptr(q), N, SPREAD_CHARGE, _ptr(rho), _stream(stream)))
         return rho
 
     def spread_force(self, x, F, out=None, stream=None):
         N = self._check_ions(x)
+        _need(F, 3 * N, self.dtype, "F")
+        _need(out, self._Gf(), self.dtype, "out")
         f = self.empty_grid("mac") if out is None else out
         _lib.check(self._lib.discos_spread(self._h, _ptr(x), _ptr(F), N, SPREAD_FORCE, _ptr(f), _stream(stream)))
         return f
 
     def solve_poisson(self, rho, out=None, stream=None):
+        _need(rho, self._G(), self.dtype, "rho")
+        _need(out, self._G(), self.dtype, "out")
         phi = self.empty_grid("cell") if out is None else out
         _lib.check(self._lib.discos_solve_poisson(self._h, _ptr(rho), _ptr(phi), _stream(stream)))
         return phi
 
     def solve_stokes(self, f, out=None, pressure=False, stream=None):
+        _need(f, self._Gf(), self.dtype, "f")
+        _need(out, self._Gf(), self.dtype, "out")
         v = self.empty_grid("mac") if out is None else out
         p = self.empty_grid("cell") if pressure else None
         _lib.check(self._lib.discos_solve_stokes(self._h, _ptr(f), _ptr(v), _ptr(p), _stream(stream)))
@@ -183,6 +218,7 @@ class Discos:
     def interpolate_efield(self, x, phi, stream=None):
         import torch
         N = self._check_ions(x)
+        _need(phi, self._G(), self.dtype, "phi")
         out = torch.empty((3, N), dtype=self.dtype, device="cuda")
         _lib.check(self._lib.discos_interpolate(self._h, _ptr(x), N, INTERP_EFIELD, _ptr(phi), _ptr(out),
                                                 _stream(stream)))
@@ -191,6 +227,7 @@ class Discos:
     def interpolate_velocity(self, x, v, stream=None):
         import torch
         N = self._check_ions(x)
+        _need(v, self._Gf(), self.dtype, "v")
         out = torch.empty((3, N), dtype=self.dtype, device="cuda")
         _lib.check(self._lib.discos_interpolate(self._h, _ptr(x), N, INTERP_VELOCITY, _ptr(v), _ptr(out),
                                                 _stream(stream)))
@@ -208,7 +245,8 @@ class Discos:
 
     def near_field(self, x, q, species=None, F=None, counts=True, stream=None):
         import torch
-        N = self._check_ions(x)
+        N = self._ions_q(x, q, species)
+        _need(F, 3 * N, self.dtype, "F")
         if F is None:
             F = torch.zeros((3, N), dtype=self.dtype, device="cuda")
         nbr = torch.empty(max(N, 1), dtype=torch.int32, device="cuda") if counts else None
@@ -218,7 +256,7 @@ class Discos:
 
     def forces(self, x, q, species=None, counts=False, stream=None):
         import torch
-        N = self._check_ions(x)
+        N = self._ions_q(x, q, species)
         F = torch.empty((3, N), dtype=self.dtype, device="cuda")
         nbr = torch.empty(max(N, 1), dtype=torch.int32, device="cuda") if counts else None
         _lib.check(self._lib.discos_forces(self._h, _ptr(x), _ptr(q), _ptr(species), N, _ptr(F), _ptr(nbr),
@@ -227,7 +265,8 @@ class Discos:
 
     def step(self, x, q, species=None, step0=0, nsteps=1, F_out=None, stream=None):
         """Advance x in place by nsteps steps; returns x."""
-        N = self._check_ions(x)
+        N = self._ions_q(x, q, species)
+        _need(F_out, 3 * N, self.dtype, "F_out")
         _lib.check(self._lib.discos_step(self._h, _ptr(x), _ptr(q), _ptr(species), N, int(step0), int(nsteps),
                                          _ptr(F_out), _stream(stream)))
         return x
@@ -252,7 +291,8 @@ class Discos:
     def diagnostics(self, x, q, F=None, with_rho=True, stream=None):
         """Double-precision sums: dict(sum_q, sum_rho, sum_F, nonfinite, escaped)."""
         import torch
-        N = self._check_ions(x)
+        N = self._ions_q(x, q)
+        _need(F, 3 * N, self.dtype, "F")
         out = torch.zeros(8, dtype=torch.float64, device="cuda")
         _lib.check(self._lib.discos_diagnostics(self._h, _ptr(x), _ptr(q), _ptr(F), N, int(bool(with_rho)),
                                                 _ptr(out), _stream(stream)))
@@ -275,6 +315,16 @@ class Discos:
         import torch
         off = [int(v) for v in offsets]
         R = len(off) - 1
+        Ntot = off[-1] if off else 0
+        ints = (torch.int32, getattr(torch, "uint32", torch.int32))
+        _need(x, 3 * Ntot, self.dtype, "x")          # the library itself requires a MIXED handle
+        _need(q, Ntot, self.dtype, "q")
+        _need(species, Ntot, torch.int32, "species")
+        _need(phi_b, 2 * R, torch.float64, "phi_b")
+        _need(hist, R * self.cfg.nspecies * self.cfg.Ny, torch.int32, "hist", ints)
+        _need(sums, 4 * R, torch.float64, "sums")
+        _need(F_out, 3 * Ntot, self.dtype, "F_out")
+        _need(nbr, Ntot, torch.int32, "nbr")
         b = _lib.Batch()
         b.R = R
         b._off_host = (ctypes.c_int * (R + 1))(*off)
@@ -312,6 +362,7 @@ class Discos:
         """Discrete electrostatic energy U as a float64 CUDA scalar."""
         import torch
         N = self._check_ions(x)
+        _need(q, N, self.dtype, "q")
         U = torch.empty((), dtype=torch.float64, device="cuda") if out is None else out
         _lib.check(self._lib.discos_energy(self._h, _ptr(x), _ptr(q), N, self._phi_b(phi_b), _ptr(U),
                                            _stream(stream)))
@@ -321,6 +372,7 @@ class Discos:
         """(dx, dq, dphi_b) = dU * gradients of U; entries not in `need` are None."""
         import torch
         N = self._check_ions(x)
+        _need(q, N, self.dtype, "q")
         dU = dU.to(device="cuda", dtype=torch.float64).contiguous()
         dx = torch.empty((3, N), dtype=self.dtype, device="cuda") if need[0] else None
         dq = torch.empty(N, dtype=self.dtype, device="cuda") if need[1] else None

@@ -51,3 +51,16 @@ def test_invalid_table_arguments(lib):
     out = (ctypes.c_double * 4)()
     assert lib.discos_fp_table(7, 6, 8.0, 4.0, 3, out) != 0
     assert lib.discos_fp_table(0, 6, 8.0, -1.0, 3, out) != 0
+
+
+def test_binding_rejects_bad_arrays():
+    """The Python binding refuses arrays the library would read past or
+    misread (host tensors, wrong type, too few elements, non-contiguous)
+    before any library call."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    import paper_2204_14167_gb300 as dg
+    dg._need(None, 10, torch.float32, "q")                        # optional argument
+    for bad in (torch.zeros(10), torch.zeros(5, dtype=torch.float32), torch.zeros(20, dtype=torch.float32)[::2]):
+        with pytest.raises(ValueError):
+            dg._need(bad, 10, torch.float32, "q")                 # on the host, short, or strided
