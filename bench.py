@@ -1,14 +1,18 @@
 """Throughput of the DISCOS wall-bounded hot path on GB300.
 
-Workload (one GPU): a 128 x 64 x 128 channel with dielectric (Neumann) walls,
-20,000 +-1 ions, Debye length ~4 cells, E_x = 0.05, full wet step (cell
-list, charge spreading, Poisson, field interpolation, P3M near field with
-images, LJ and wall forces, force spreading with RFD thermal forcing,
-stochastic stress, staggered Stokes, two velocity interpolations, midpoint
-update with the near-wall dry tensor), single-precision bulk with double
-wall-normal solves.  One step = one pass of that path over all ions.
+Workload (one GPU, the default): a 256 x 128 x 256 channel with a conducting
+(Dirichlet) bottom wall and a dielectric (Neumann) top wall, 400,000 +-1
+ions, l_B = 0.96, E_x = 0.02, the full wet step (cell list, charge
+spreading, Poisson, field interpolation, P3M near field with images, LJ and
+wall forces, force spreading with RFD thermal forcing, stochastic stress,
+staggered Stokes, two velocity interpolations, midpoint update with the
+near-wall dry tensor), single-precision bulk with double wall-normal solves.
+One step = one pass of that path over all ions.  `--workload
+wet_channel_128x64x128` selects the 128 x 64 x 128 Neumann channel with
+20,000 ions instead.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME]
 
 Under torchrun each rank runs an independent replica (the path does not
 shard; replicas only) and rank 0 prints one JSON line.
@@ -24,7 +28,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ion-timesteps/s"
-WORKLOAD = "wet_channel_128x64x128: 128x64x128 cells, Neumann walls, 20000 ions, full wet step, FP32+FP64 islands"
+WORKLOADS = {
+    "iceo_channel_256x128x256": "iceo_channel_256x128x256: 256x128x256 cells, conducting bottom and dielectric "
+                                "top wall, 400000 ions, full wet step, FP32+FP64 islands",
+    "wet_channel_128x64x128": "wet_channel_128x64x128: 128x64x128 cells, Neumann walls, 20000 ions, "
+                              "full wet step, FP32+FP64 islands",
+}
+DEFAULT_WORKLOAD = "iceo_channel_256x128x256"
 
 
 def whole_job_rate(units_local, t_ms_local, dist=None, device="cpu"):
@@ -132,7 +142,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "reference_sample": "32x16x16 channel, 300 ions"},
+            "config": {"workload": WORKLOADS[args.workload], "reference_sample": "32x16x16 channel, 300 ions"},
             "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
                              "sample": "FP64 oracle wet steps of a 32x16x16 channel with 300 ions per step"},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -152,7 +162,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.cuda.current_device()
-    cfg, rec = presets.wet_channel_128x64x128(dg.MIXED)
+    cfg, rec = getattr(presets, args.workload)(dg.MIXED)
     cfg.seed = cfg.seed + rank
     pos, q, sp = synth.ions(cfg.dims, rec["n_pos"], rec["n_neg"], rec["seed"] + rank, rec["ymargin"], rec["min_sep"])
     N = pos.shape[1]
@@ -202,22 +212,26 @@ def run_ours(args):
     ms_per_step = t_ms / args.steps
 
     # end to end through the public API with host buffers: pinned H2D of the
-    # step's positions and charges, the step, D2H of the new positions
+    # step's positions and charges, the step, D2H of the new positions; the
+    # same L2 policy as the device-timed loop (flushed between steps, outside
+    # the events)
     xh = torch.tensor(pos, dtype=torch.float32).pin_memory()
     qh = torch.tensor(q, dtype=torch.float32).pin_memory()
     out_h = torch.empty_like(xh).pin_memory()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    starts2 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends2 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     torch.cuda.synchronize()
-    e0.record(stream)
     for k in range(args.steps):
+        flush.fill_(float(k))
+        starts2[k].record(stream)
         x.copy_(xh, non_blocking=True)
         qd.copy_(qh, non_blocking=True)
         h.step(x, qd, step0=step, nsteps=1)
         out_h.copy_(x, non_blocking=True)
+        ends2[k].record(stream)
         step += 1
-    e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
+    e2e_ms = sum(s.elapsed_time(e) for s, e in zip(starts2, ends2))
     e2e = {"value": whole_job_rate(N * args.steps, e2e_ms, dist, "cuda")[0], "unit": METRIC,
            "h2d_bytes_per_step": int(xh.numel() * 4 + qh.numel() * 4),
            "d2h_bytes_per_step": int(out_h.numel() * 4)}
@@ -228,7 +242,7 @@ def run_ours(args):
     avg_s = probe_ms * 1e-3 / max(probe_n, 1)
     achieved = nbytes / avg_s / 1e9 if nbytes else None
     rl = {"roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                       "frac": achieved / peak if achieved else None, "traffic": MEASURED_TRAFFIC.get(dominant),
+                       "frac": achieved / peak if achieved else None, "traffic": MEASURED_TRAFFIC[args.workload].get(dominant),
                        "algorithmic_bytes_per_launch": nbytes, "avg_launch_us": avg_s * 1e6,
                        "launches_timed": probe_n, "peak_source": "measured" if peaks else "fallback"},
           "stages_ms": {k: round(v, 5) for k, v in breakdown.items()}}
@@ -237,7 +251,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "ions": N, "grid": [cfg.Nx, cfg.Ny, cfg.Nz],
+                "config": {"workload": WORKLOADS[args.workload], "ions": N, "grid": [cfg.Nx, cfg.Ny, cfg.Nz],
                            "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{ws}",
                            "transform_shape": {"fx_pairs": shape[0], "fx_threads": shape[1], "fz_tile": shape[2]}},
                 "clocks": clocks, "e2e": e2e, "roofline": rl.get("roofline"), "stages_ms": rl.get("stages_ms"),
@@ -416,7 +430,7 @@ def run_profile(args):
     import torch
     import paper_2204_14167_gb300 as dg
     from paper_2204_14167_gb300 import presets, synth
-    cfg, rec = presets.wet_channel_128x64x128(dg.MIXED)
+    cfg, rec = getattr(presets, args.workload)(dg.MIXED)
     pos, q, sp = synth.ions(cfg.dims, rec["n_pos"], rec["n_neg"], rec["seed"], rec["ymargin"], rec["min_sep"])
     h = dg.Discos(cfg)
     h.tune_transforms()
@@ -462,7 +476,8 @@ def _peaks():
 # DRAM bytes per launch of a family (cold-cache, one ncu capture of one
 # measured step of `bench.py --profile`; the command and the per-kernel table
 # are in profiles/transforms_scans_dram_wet_channel_128x64x128.md).
-MEASURED_TRAFFIC = {"fft_x": 9.486e6, "fft_z": 10.537e6, "stokes_y": 25.646e6}
+MEASURED_TRAFFIC = {"wet_channel_128x64x128": {"fft_x": 9.486e6, "fft_z": 10.537e6, "stokes_y": 25.646e6},
+                    "iceo_channel_256x128x256": {}}
 
 
 def algorithmic_bytes(family, cfg, N):
@@ -525,6 +540,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the production-form measurements")
     ap.add_argument("--profile-batched", action="store_true",

@@ -95,9 +95,13 @@ def fluid_forcing(p, pos, F, step):
     return fx, fy, fz
 
 
-def wet_step(p, pos, q, species, step, pair_dtype=np.float64):
-    """One step of the four-stage algorithm with the midpoint scheme."""
-    F, counts, parts = forces(p, pos, q, species, pair_dtype)
+def wet_increment(p, pos, species, F, step):
+    """Stages 3 and 4 of Sec. II.D for given forces F: the fluid forcing
+    (spread forces, RFD thermal forcing, stochastic stress), the Stokes solve,
+    and the midpoint update of Eqs. step1-step2 (V = J(x*) v with
+    x* = x + dt/2 J(x) v) plus the dry part of Eq. ions3.  With p['drift']
+    false the RFD term is left out and the update is single stage (V = J(x) v).
+    Returns (increment (3, N), fluid fields dict)."""
     fx, fy, fz = fluid_forcing(p, pos, F, step)
     u, v, w, pr = stokes.solve(fx, fy, fz, p['eta'])
     V1 = gridops.interp_velocity(p['kernel_hy'], pos, u, v, w)
@@ -107,5 +111,12 @@ def wet_step(p, pos, q, species, step, pair_dtype=np.float64):
     else:
         V = V1
     inc = p['dt'] * V + dry_increment(p, pos, species, F, step)
+    return inc, dict(u=u, v=v, w=w, p=pr, V1=V1, V=V)
+
+
+def wet_step(p, pos, q, species, step, pair_dtype=np.float64):
+    """One step of the four-stage algorithm with the midpoint scheme."""
+    F, counts, parts = forces(p, pos, q, species, pair_dtype)
+    inc, fluid = wet_increment(p, pos, species, F, step)
     new = wrap_reflect(pos + inc, p['dims'])
-    return new, F, counts, dict(parts, u=u, v=v, w=w, p=pr, V1=V1, V=V)
+    return new, F, counts, dict(parts, **fluid)
