@@ -31,12 +31,14 @@ def _axis_points(kernel, s):
     return idx, wts
 
 
-def spread(kernel, pos, vals, shape, offs, ytype, signs):
+def spread(kernel, pos, vals, shape, offs, ytype, signs, bottom_cols=None):
     """Spread vals[n] at positions pos[:, n] onto a grid of shape (Nz, Ny', Nx).
 
     offs = (ox, oy, oz): coordinate of grid point 0 along each axis (1/2 for
     cell-centred axes, 0 for face axes).  ytype: CELL (Ny points) or FACE
-    (Ny+1 points).  signs = (s_bottom, s_top) for the two wall images.
+    (Ny+1 points).  signs = (s_bottom, s_top) for the two wall images;
+    bottom_cols (Nx,), if given, replaces s_bottom by a sign per grid column
+    (a wall made of parts of different kinds).
     Returns the spread density (the kernel carries the 1/Delta V factor).
     """
     Nz, Nyg, Nx = shape
@@ -50,7 +52,7 @@ def spread(kernel, pos, vals, shape, offs, ytype, signs):
     ix %= Nx
     iz %= Nz
     w = kernel.w
-    for ypos, sgn in images:
+    for m, (ypos, sgn) in enumerate(images):
         iy, wy = kernel.stencil(ypos - offs[1])
         valid = (iy >= 0) & (iy < Nyg)
         wyv = np.where(valid, wy, 0.0)
@@ -58,6 +60,8 @@ def spread(kernel, pos, vals, shape, offs, ytype, signs):
         # (n, w, w, w) contributions, axes (z, y, x)
         contrib = (sgn * vals)[:, None, None, None] * wz[:, :, None, None] \
             * wyv[:, None, :, None] * wx[:, None, None, :]
+        if m == 1 and bottom_cols is not None:
+            contrib = contrib / sgn * np.asarray(bottom_cols)[ix][:, None, None, :]
         K = np.broadcast_to(iz[:, :, None, None], contrib.shape)
         J = np.broadcast_to(iyc[:, None, :, None], contrib.shape)
         I = np.broadcast_to(ix[:, None, None, :], contrib.shape)
@@ -121,10 +125,22 @@ def charge_signs(bc):
     return tuple(-1.0 if b == DIRICHLET else 1.0 for b in bc)
 
 
-def spread_charge(kernel, pos, q, dims, bc):
-    """Charge density rho = S^es q on cell centres with wall images."""
+def strip_cols(dims, strip):
+    """Bool (Nx,): the bottom cell columns under a metal strip (centre in [x0, x1))."""
+    xc = np.arange(dims[0]) + 0.5
+    return (xc >= strip[0]) & (xc < strip[1])
+
+
+def spread_charge(kernel, pos, q, dims, bc, strip=None):
+    """Charge density rho = S^es q on cell centres with wall images.  With a
+    metal strip (x0, x1, phi) in the dielectric bottom wall, the bottom image
+    takes the conducting wall's sign (-1) in the strip's columns (reading:
+    the image follows the kind of wall under each grid column)."""
     Nx, Ny, Nz = dims
-    return spread(kernel, pos, q, (Nz, Ny, Nx), (0.5, 0.5, 0.5), CELL, charge_signs(bc))
+    cols = None
+    if strip is not None:
+        cols = np.where(strip_cols(dims, strip), -1.0, 1.0)
+    return spread(kernel, pos, q, (Nz, Ny, Nx), (0.5, 0.5, 0.5), CELL, charge_signs(bc), cols)
 
 
 def phi_ghost_rules(bc, phi_b, dphidy):
@@ -149,18 +165,27 @@ def phi_ghost_rules(bc, phi_b, dphidy):
     return rules
 
 
-def efield_at_ions(kernel, pos, phi, bc, phi_b, dphidy):
+def efield_at_ions(kernel, pos, phi, bc, phi_b, dphidy, strip=None, E_x=0.0):
     """E^P = J^es(-grad_h phi) (Eq. efieldop) with E on cell faces.
 
     phi is extended with ghost cells (phi_ghost_rules), E = -(phi_i - phi_{i-1})
     is formed on every face of the extended grid, and each component is
-    interpolated with the kernel centred at its own face positions.
+    interpolated with the kernel centred at its own face positions.  With a
+    metal strip (x0, x1, phi_total) in the bottom wall, the ghost cells below
+    the strip's columns follow the Dirichlet rule with phi_m(x) = phi_total +
+    E_x (x - x_c) (see poisson.strip_potential).
     Returns E, shape (3, N).
     """
     Nz, Ny, Nx = phi.shape
     ghost = kernel.w // 2 + 3
     rb, rt = phi_ghost_rules(bc, phi_b, dphidy)
     ext, y0 = extend_y(phi, CELL, ghost, rb, rt)
+    if strip is not None:
+        on = strip_cols((Nx, Ny, Nz), strip)
+        xc = np.arange(Nx) + 0.5
+        pm = strip[2] + E_x * (xc - 0.5 * (strip[0] + strip[1]))
+        for m in range(ghost):
+            ext[:, ghost - 1 - m, on] = 2.0 * pm[on][None, :] - phi[:, m, :][:, on]
     Ex = -(ext - np.roll(ext, 1, axis=2))          # x-face i: phi_i - phi_{i-1}
     Ez = -(ext - np.roll(ext, 1, axis=0))
     Ey = np.zeros_like(ext)                          # y-face at ext index j: phi_j - phi_{j-1}
@@ -176,26 +201,30 @@ def efield_at_ions(kernel, pos, phi, bc, phi_b, dphidy):
 NOSLIP = 0
 
 
-def spread_force(kernel, pos, F, dims):
+def spread_force(kernel, pos, F, dims, slip=(False, False)):
     """Hydrodynamic spreading S^hy F (Eq. kernel2) per MAC component with the
-    no-slip image construction (opposite normal and tangential force).
+    image construction of Sec. II.A: opposite normal force at every wall;
+    opposite tangential force at a no-slip wall, the same at a slip wall.
     Returns (fx on x-faces, fy on y-faces incl. walls, fz on z-faces)."""
     Nx, Ny, Nz = dims
     s = (-1.0, -1.0)
-    fx = spread(kernel, pos, F[0], (Nz, Ny, Nx), (0.0, 0.5, 0.5), CELL, s)
+    st = tuple(1.0 if sl else -1.0 for sl in slip)
+    fx = spread(kernel, pos, F[0], (Nz, Ny, Nx), (0.0, 0.5, 0.5), CELL, st)
     fy = spread(kernel, pos, F[1], (Nz, Ny + 1, Nx), (0.5, 0.0, 0.5), FACE, s)
-    fz = spread(kernel, pos, F[2], (Nz, Ny, Nx), (0.5, 0.5, 0.0), CELL, s)
+    fz = spread(kernel, pos, F[2], (Nz, Ny, Nx), (0.5, 0.5, 0.0), CELL, st)
     return fx, fy, fz
 
 
-def interp_velocity(kernel, pos, u, v, w):
-    """V = J^hy v (Eq. kernel1) with no-slip ghost fill: tangential ghosts are
-    the negated mirror values, normal ghosts the negated mirror values; the
-    wall faces carry v = 0."""
+def interp_velocity(kernel, pos, u, v, w, slip=(False, False)):
+    """V = J^hy v (Eq. kernel1) with ghost fill from the wall conditions:
+    tangential ghosts are the negated mirror values at a no-slip wall and the
+    mirror values at a slip wall, normal ghosts the negated mirror values;
+    the wall faces carry v = 0."""
     ghost = kernel.w // 2 + 3
     zero = (lambda m: 0.0)
-    ue, y0 = extend_y(u, CELL, ghost, (-1.0, zero), (-1.0, zero))
-    we, _ = extend_y(w, CELL, ghost, (-1.0, zero), (-1.0, zero))
+    tb, tt = (1.0 if slip[0] else -1.0), (1.0 if slip[1] else -1.0)
+    ue, y0 = extend_y(u, CELL, ghost, (tb, zero), (tt, zero))
+    we, _ = extend_y(w, CELL, ghost, (tb, zero), (tt, zero))
     ve, y0v = extend_y(v, FACE, ghost, (-1.0, zero), (-1.0, zero))
     Vx = interpolate(kernel, pos, ue, y0, (0.0, 0.5, 0.5))
     Vy = interpolate(kernel, pos, ve, y0v, (0.5, 0.0, 0.5))

@@ -8,7 +8,8 @@ eps = 1/(4 pi l_B)):
   surf_charge; kernel_es, kernel_hy (kernels.Kernel); lB; eta; kT; dt; psi;
   fp_table; lj_sigma/lj_xi/lj_rc [ns][ns]; wall_sigma/wall_xi/wall_rc [ns];
   wall_type; E_ext (3,); gamma_coef [ns][2][2][7]; D_tot, D_wet [ns];
-  wet, drift (bools); seed.
+  wet, drift (bools); seed; slip (bottom, top) hydrodynamic slip walls;
+  strip (x0, x1, phi_total) or None.
 
 Stage 1: rho = S^es q, Poisson (Eq. poisson).  Stage 2: E^P = J^es(-grad phi)
 (Eq. efieldop), F = q E^P + near field (Eqs. fullElectro, LC) + LJ
@@ -24,12 +25,20 @@ from . import gridops, poisson, particles, mobility, stokes, philox
 
 
 def electrostatic_field(p, pos, q):
-    """(rho, phi, E^P at the ions)."""
+    """(rho, phi, E^P at the ions).  p['strip'] = (x0, x1, phi_total) puts a
+    metal strip into the dielectric bottom wall (Sec. IV.B)."""
     dims = p['dims']
-    rho = gridops.spread_charge(p['kernel_es'], pos, q, dims, p['bc'])
-    phi = poisson.solve(rho, p['bc'], p['lB'], p['phi_b'], p['surf_charge'])
+    strip = p.get('strip')
+    rho = gridops.spread_charge(p['kernel_es'], pos, q, dims, p['bc'], strip)
     slopes = poisson.wall_slopes(p['bc'], p['surf_charge'], p['lB'])
-    E = gridops.efield_at_ions(p['kernel_es'], pos, phi, p['bc'], p['phi_b'], slopes)
+    E_x = float(p['E_ext'][0])
+    if strip is None:
+        phi = poisson.solve(rho, p['bc'], p['lB'], p['phi_b'], p['surf_charge'])
+    else:
+        mask = poisson.strip_columns(dims, strip[0], strip[1])
+        pm = poisson.strip_potential(dims, strip[0], strip[1], strip[2], E_x)
+        phi = poisson.solve_strip(rho, p['lB'], mask, pm, p['bc'][1], p['phi_b'][1], p['surf_charge'])
+    E = gridops.efield_at_ions(p['kernel_es'], pos, phi, p['bc'], p['phi_b'], slopes, strip, E_x)
     return rho, phi, E
 
 
@@ -82,12 +91,13 @@ def dry_step(p, pos, q, species, step, pair_dtype=np.float64, replica=0):
 def fluid_forcing(p, pos, F, step):
     """f = S^hy F + f_th + stochastic stress (each optional by flags)."""
     dims = p['dims']
-    fx, fy, fz = gridops.spread_force(p['kernel_hy'], pos, F, dims)
+    slip = p.get('slip', (False, False))
+    fx, fy, fz = gridops.spread_force(p['kernel_hy'], pos, F, dims, slip)
     if p.get('drift', True) and p['kT'] > 0:
-        tx, ty, tz = stokes.rfd_forcing(p['kernel_hy'], pos, dims, p['kT'], step, 0, p['seed'])
+        tx, ty, tz = stokes.rfd_forcing(p['kernel_hy'], pos, dims, p['kT'], step, 0, p['seed'], slip=slip)
         fx, fy, fz = fx + tx, fy + ty, fz + tz
     if p['kT'] > 0:
-        nx, ny, nz = stokes.noise_forcing(dims, p['eta'], p['kT'], p['dt'], step, 0, p['seed'])
+        nx, ny, nz = stokes.noise_forcing(dims, p['eta'], p['kT'], p['dt'], step, 0, p['seed'], slip)
         fx, fy, fz = fx + nx, fy + ny, fz + nz
     fy = fy.copy()
     fy[:, 0, :] = 0.0
@@ -102,12 +112,13 @@ def wet_increment(p, pos, species, F, step):
     x* = x + dt/2 J(x) v) plus the dry part of Eq. ions3.  With p['drift']
     false the RFD term is left out and the update is single stage (V = J(x) v).
     Returns (increment (3, N), fluid fields dict)."""
+    slip = p.get('slip', (False, False))
     fx, fy, fz = fluid_forcing(p, pos, F, step)
-    u, v, w, pr = stokes.solve(fx, fy, fz, p['eta'])
-    V1 = gridops.interp_velocity(p['kernel_hy'], pos, u, v, w)
+    u, v, w, pr = stokes.solve(fx, fy, fz, p['eta'], slip=slip)
+    V1 = gridops.interp_velocity(p['kernel_hy'], pos, u, v, w, slip)
     if p.get('drift', True):
         xs = pos + 0.5 * p['dt'] * V1
-        V = gridops.interp_velocity(p['kernel_hy'], xs, u, v, w)
+        V = gridops.interp_velocity(p['kernel_hy'], xs, u, v, w, slip)
     else:
         V = V1
     inc = p['dt'] * V + dry_increment(p, pos, species, F, step)

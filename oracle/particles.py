@@ -110,16 +110,23 @@ def near_field(pos, q, species, p, table, pair_dtype=np.float64, targets=None):
         F[1, t0:t0 + 256] += np.sum(coef * dy.astype(np.float64) / rs, axis=1)
         F[2, t0:t0 + 256] += np.sum(coef * dz.astype(np.float64) / rs, axis=1)
         counts[t0:t0 + 256] += np.sum(m, axis=1)
-        # images across each wall (the ion's own image included)
+        # images across each wall (the ion's own image included); with a
+        # metal strip in the bottom wall, a partner's bottom image takes the
+        # sign of the wall under it (-1 over the strip's columns)
+        strip = p.get('strip')
         for w in range(2):
             yimg = -X[1] if w == 0 else dt(2 * Ny) - X[1]
+            wsign = wall_sign[w]
+            if w == 0 and strip is not None:
+                col = np.floor(np.asarray(pos, dtype=np.float64)[0]) + 0.5
+                wsign = np.where((col >= strip[0]) & (col < strip[1]), -1.0, 1.0)[None, :]
             dyi = yi - yimg[None, :]
             # the own image has dx = dz = 0 exactly
             dxo, dzo = dx, dz
             r2i = (dxo * dxo + dyi * dyi) + dzo * dzo
             mi = r2i < psi2
             ri = np.sqrt(np.where(mi, r2i, 1).astype(np.float64))
-            ci = np.where(mi, lB * qi * (wall_sign[w] * q[None, :]) *
+            ci = np.where(mi, lB * qi * (wsign * q[None, :]) *
                           (1.0 / ri ** 2 - fp_lookup(table, psi, np.minimum(ri, psi * (1 - 1e-15)))), 0.0)
             F[0, t0:t0 + 256] += np.sum(ci * dxo.astype(np.float64) / ri, axis=1)
             F[1, t0:t0 + 256] += np.sum(ci * dyi.astype(np.float64) / ri, axis=1)

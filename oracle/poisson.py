@@ -101,3 +101,55 @@ def residual(phi, rho, bc, lB, phi_b=(0.0, 0.0), surf_charge=(0.0, 0.0)):
     A = assemble((Nx, Ny, Nz), bc)
     b = rhs(rho, bc, phi_b, wall_slopes(bc, surf_charge, lB), lB).ravel()
     return (b - A @ np.asarray(phi, dtype=np.float64).ravel()).reshape(Nz, Ny, Nx), b.reshape(Nz, Ny, Nx)
+
+
+def strip_columns(dims, x0, x1):
+    """Bottom-wall cells (Nz, Nx) whose centre x + 1/2 lies on the metal strip
+    [x0, x1) (the strip spans the channel in z, Fig. EOgeometry)."""
+    Nx, Ny, Nz = dims
+    xc = np.arange(Nx) + 0.5
+    on = (xc >= x0) & (xc < x1)
+    return np.broadcast_to(on[None, :], (Nz, Nx)).copy()
+
+
+def strip_potential(dims, x0, x1, phi_total, E_x):
+    """phi_m on the strip's cells (Nz, Nx): the fixed potential of the solve
+    that makes the total potential phi + phi_E constant (= phi_total) on the
+    metal, with phi_E = -E_x (x - x_c) the applied field's potential and x_c
+    the strip's centre (Sec. IV.B; reading of where phi_E is zero)."""
+    Nx, Ny, Nz = dims
+    xc = np.arange(Nx) + 0.5
+    pm = phi_total + E_x * (xc - 0.5 * (x0 + x1))
+    return np.broadcast_to(pm[None, :], (Nz, Nx)).copy()
+
+
+def assemble_strip(dims, bc_top, strip):
+    """The 7-point operator with a mixed bottom wall: Dirichlet ghost rows
+    (phi(-1) = 2 phi_m - phi(0)) on the strip cells, Neumann ghost rows
+    (phi(-1) = phi(0) - g) elsewhere; the top wall of type bc_top."""
+    Nx, Ny, Nz = dims
+    A = assemble(dims, (NEUMANN, bc_top)).tolil()
+    idx = np.arange(Nx * Ny * Nz).reshape(Nz, Ny, Nx)
+    for k, i in zip(*np.nonzero(strip)):
+        r = idx[k, 0, i]
+        A[r, r] += 2.0          # Neumann -1 becomes Dirichlet +1
+    return A.tocsr()
+
+
+def solve_strip(rho, lB, strip, phi_m, bc_top, phi_b_top=0.0, surf=(0.0, 0.0), tol=1e-13):
+    """Eq. poisson with a metal strip (Dirichlet patch, potential phi_m on
+    its cells) inside a dielectric bottom wall (Neumann, surface charge
+    surf[0]) and a top wall of type bc_top (Eqs. esbc1 / esbc3), by CG on the
+    assembled operator.  The strip fixes the potential's constant, so no
+    neutrality condition applies."""
+    Nz, Ny, Nx = rho.shape
+    dims = (Nx, Ny, Nz)
+    A = assemble_strip(dims, bc_top, strip)
+    slopes = wall_slopes((NEUMANN, bc_top), surf, lB)
+    b = 4.0 * np.pi * lB * np.asarray(rho, dtype=np.float64).copy()
+    b[:, 0, :] += np.where(strip, 2.0 * phi_m, -slopes[0])
+    b[:, -1, :] += 2.0 * phi_b_top if bc_top == DIRICHLET else slopes[1]
+    phi, info = spla.cg(A, b.ravel(), rtol=tol, atol=0.0, maxiter=20000)
+    if info != 0:
+        raise RuntimeError(f"CG did not converge (info={info})")
+    return phi.reshape(Nz, Ny, Nx)

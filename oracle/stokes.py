@@ -31,10 +31,12 @@ import scipy.sparse.linalg as spla
 from . import gridops, philox
 
 
-def _ops(dims):
-    """Sparse blocks: (Lu, Lv, Lw) = -lap_h with no-slip rules, gradients and
+def _ops(dims, slip=(False, False)):
+    """Sparse blocks: (Lu, Lv, Lw) = -lap_h with the wall rules, gradients and
     divergences.  Unknown layout: u (Nz,Ny,Nx), v interior (Nz,Ny-1,Nx) for
-    faces j = 1..Ny-1, w (Nz,Ny,Nx), p (Nz,Ny,Nx)."""
+    faces j = 1..Ny-1, w (Nz,Ny,Nx), p (Nz,Ny,Nx).  Tangential ghost below a
+    no-slip wall u(-1) = -u(0) (diagonal 6 + 1), below a slip wall
+    u(-1) = +u(0) (zero shear, diagonal 6 - 1), Eq. fluidbc."""
     Nx, Ny, Nz = dims
     nc = Nx * Ny * Nz
     nv = Nx * (Ny - 1) * Nz
@@ -49,8 +51,8 @@ def _ops(dims):
         r.append(ic[:, 1:, :].ravel()); c.append(ic[:, :-1, :].ravel()); v.append(-np.ones(ic[:, 1:, :].size))
         r.append(ic[:, :-1, :].ravel()); c.append(ic[:, 1:, :].ravel()); v.append(-np.ones(ic[:, 1:, :].size))
         d = np.full((Nz, Ny, Nx), 6.0)
-        d[:, 0, :] += 1.0       # ghost u(-1) = -u(0)
-        d[:, -1, :] += 1.0
+        d[:, 0, :] += -1.0 if slip[0] else 1.0      # ghost u(-1) = +-u(0)
+        d[:, -1, :] += -1.0 if slip[1] else 1.0
         r.append(ic.ravel()); c.append(ic.ravel()); v.append(d.ravel())
         return sp.csr_matrix((np.concatenate(v), (np.concatenate(r), np.concatenate(c))), shape=(nc, nc))
 
@@ -79,7 +81,7 @@ def _ops(dims):
     return Lc, lap_face(), Lc, Gx, Gy, Gz
 
 
-def solve(fx, fy, fz, eta, tol=1e-13):
+def solve(fx, fy, fz, eta, tol=1e-13, slip=(False, False)):
     """Velocity (u on x-faces, v on y-faces incl. zero wall faces, w) and p.
 
     fy has shape (Nz, Ny+1, Nx); its wall rows are ignored.  Uzawa form of
@@ -87,11 +89,15 @@ def solve(fx, fy, fz, eta, tol=1e-13):
     solves the Schur complement system  G^T L^-1 G p = G^T L^-1 f  by
     conjugate gradients on mean-zero pressures (the constant is the null
     space), with every L^-1 applied by a sparse LU factorisation of the
-    viscous operator; then vel = L^-1 (f - G p) / eta.
+    viscous operator; then vel = L^-1 (f - G p) / eta.  slip = (bottom, top)
+    slip walls (at most one: with two, the tangential operator has the
+    uniform flow as its null space).
     """
     Nz, Ny, Nx = fx.shape
     dims = (Nx, Ny, Nz)
-    Lu, Lv, Lw, Gx, Gy, Gz = _ops(dims)
+    if slip[0] and slip[1]:
+        raise ValueError("at most one slip wall")
+    Lu, Lv, Lw, Gx, Gy, Gz = _ops(dims, slip)
     lu_c = spla.splu(Lu.tocsc())
     lu_f = spla.splu(Lv.tocsc())
 
@@ -123,14 +129,46 @@ def solve(fx, fy, fz, eta, tol=1e-13):
     return u, v, w, p.reshape(Nz, Ny, Nx)
 
 
+def residual(u, v, w, p, fx, fy, fz, eta, slip=(False, False)):
+    """Momentum residuals f - (eta L vel + G p) on the faces (interior y-faces
+    for v; its wall rows are returned as zero) and the divergence div_h vel,
+    for given velocity and pressure fields, with the operators of Eq.
+    disc_stokes applied by their stencils (no assembly, so it runs at any
+    grid size): -lap_h with the no-slip rules of Eq. fluidbc (tangential
+    ghost = -interior, v = 0 on the wall faces) and p_i - p_{i-1} gradients."""
+    def lap_cell(a):
+        out = 6.0 * a - np.roll(a, 1, 2) - np.roll(a, -1, 2) - np.roll(a, 1, 0) - np.roll(a, -1, 0)
+        out[:, 1:, :] -= a[:, :-1, :]
+        out[:, :-1, :] -= a[:, 1:, :]
+        out[:, 0, :] += -a[:, 0, :] if slip[0] else a[:, 0, :]     # ghost u(-1) = +-u(0)
+        out[:, -1, :] += -a[:, -1, :] if slip[1] else a[:, -1, :]
+        return out
+
+    u = np.asarray(u, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    p = np.asarray(p, dtype=np.float64)
+    rx = fx - (eta * lap_cell(u) + (p - np.roll(p, 1, 2)))
+    rz = fz - (eta * lap_cell(w) + (p - np.roll(p, 1, 0)))
+    vi = v[:, 1:-1, :]
+    lv = 6.0 * vi - np.roll(vi, 1, 2) - np.roll(vi, -1, 2) - np.roll(vi, 1, 0) - np.roll(vi, -1, 0) \
+        - v[:, :-2, :] - v[:, 2:, :]
+    ry = np.zeros_like(v)
+    ry[:, 1:-1, :] = fy[:, 1:-1, :] - (eta * lv + (p[:, 1:, :] - p[:, :-1, :]))
+    return (rx, ry, rz), divergence(u, v, w)
+
+
 def divergence(u, v, w):
     """div_h v at cell centres."""
     return (np.roll(u, -1, axis=2) - u) + (v[:, 1:, :] - v[:, :-1, :]) + (np.roll(w, -1, axis=0) - w)
 
 
-def stress_fields(dims, step, replica, seed):
+def stress_fields(dims, step, replica, seed, slip=(False, False)):
     """Z components from Philox: centres (Zxx, Zyy, Zzz), edges (Zxy, Zxz, Zyz)
-    on an (Nz, Ny+1, Nx) lattice, wall edges of Zxy and Zyz scaled by sqrt 2."""
+    on an (Nz, Ny+1, Nx) lattice, wall edges of Zxy and Zyz scaled by sqrt 2
+    at a no-slip wall and by 0 at a slip wall (no shear stress there; with
+    these scalings D D^T = L + Div^T Div holds for either wall, checked in the
+    tests)."""
     Nx, Ny, Nz = dims
     cell = np.arange(Nx * (Ny + 1) * Nz, dtype=np.uint64)
     a = philox.normals4(cell, step, replica, philox.TAG_STRESS_A, seed)
@@ -143,8 +181,8 @@ def stress_fields(dims, step, replica, seed):
     Zxz = b[0].reshape(sh)[:, :Ny, :]
     Zyz = b[1].reshape(sh).copy()
     for Zw in (Zxy, Zyz):
-        Zw[:, 0, :] *= np.sqrt(2.0)
-        Zw[:, Ny, :] *= np.sqrt(2.0)
+        Zw[:, 0, :] *= 0.0 if slip[0] else np.sqrt(2.0)
+        Zw[:, Ny, :] *= 0.0 if slip[1] else np.sqrt(2.0)
     return Zxx, Zyy, Zzz, Zxy, Zxz, Zyz
 
 
@@ -163,17 +201,17 @@ def stress_divergence(Zxx, Zyy, Zzz, Zxy, Zxz, Zyz):
     return dx, dy, dz
 
 
-def noise_forcing(dims, eta, kT, dt, step, replica, seed):
+def noise_forcing(dims, eta, kT, dt, step, replica, seed, slip=(False, False)):
     amp = np.sqrt(2.0 * kT * eta / dt)
-    Z = stress_fields(dims, step, replica, seed)
+    Z = stress_fields(dims, step, replica, seed, slip)
     dx, dy, dz = stress_divergence(*Z)
     return amp * dx, amp * dy, amp * dz
 
 
-def rfd_forcing(kernel, pos, dims, kT, step, replica, seed, delta=1e-4, first_index=0):
+def rfd_forcing(kernel, pos, dims, kT, step, replica, seed, delta=1e-4, first_index=0, slip=(False, False)):
     """Thermal forcing f_th by random finite differences (reading above)."""
     N = pos.shape[1]
     W = philox.ion_normals(N, step, replica, philox.TAG_RFD, seed, first_index)
-    plus = gridops.spread_force(kernel, pos + 0.5 * delta * W, W, dims)
-    minus = gridops.spread_force(kernel, pos - 0.5 * delta * W, W, dims)
+    plus = gridops.spread_force(kernel, pos + 0.5 * delta * W, W, dims, slip)
+    minus = gridops.spread_force(kernel, pos - 0.5 * delta * W, W, dims, slip)
     return tuple((kT / delta) * (a - b) for a, b in zip(plus, minus))

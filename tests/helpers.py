@@ -15,7 +15,9 @@ def oracle_params(cfg):
         lj_sigma=cfg.lj_sigma, lj_xi=cfg.lj_xi, lj_rc=cfg.lj_rc,
         wall_sigma=cfg.wall_sigma, wall_xi=cfg.wall_xi, wall_rc=cfg.wall_rc, wall_type=cfg.wall_type,
         E_ext=tuple(cfg.E_ext), gamma_coef=cfg.gamma_coef, D_tot=cfg.D_tot, D_wet=cfg.D_wet,
-        wet=bool(cfg.wet), drift=bool(cfg.drift), seed=cfg.seed)
+        wet=bool(cfg.wet), drift=bool(cfg.drift), seed=cfg.seed,
+        strip=(float(cfg.strip_x[0]), float(cfg.strip_x[1]), float(cfg.strip_phi)) if cfg.strip else None,
+        slip=(bool(cfg.bc_hy[0]), bool(cfg.bc_hy[1])))
 
 
 def rel_l2(a, b):

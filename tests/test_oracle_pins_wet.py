@@ -169,3 +169,34 @@ def test_wet_update_without_drift_is_biased():
     rel = _wet_profile(False, steps=240)
     assert rel[0] > 1.5 and rel[-1] > 1.5, rel
     assert np.all(rel[1:-1] < 0.9), rel
+
+
+# ------------------------------------------------------------------ Stokes residual
+def test_stokes_stencil_residual_matches_assembled_operator():
+    """The stencil form of the MAC operator (used for residual checks at
+    full size) equals the assembled saddle system of the solver on random
+    fields, and vanishes on the solver's own solution."""
+    dims = (8, 6, 10)
+    Nx, Ny, Nz = dims
+    rng = np.random.default_rng(3)
+    eta = 0.7
+    u, w, p = (rng.normal(size=(Nz, Ny, Nx)) for _ in range(3))
+    v = rng.normal(size=(Nz, Ny + 1, Nx))
+    v[:, 0] = v[:, -1] = 0.0
+    fx, fz = rng.normal(size=(Nz, Ny, Nx)), rng.normal(size=(Nz, Ny, Nx))
+    fy = rng.normal(size=(Nz, Ny + 1, Nx))
+    fy[:, 0] = fy[:, -1] = 0.0
+    (rx, ry, rz), div = stokes.residual(u, v, w, p, fx, fy, fz, eta)
+    Lu, Lv, Lw, Gx, Gy, Gz = stokes._ops(dims)
+    pr = p.ravel()
+    assert np.allclose(rx.ravel(), fx.ravel() - (eta * (Lu @ u.ravel()) + Gx @ pr), atol=1e-12)
+    assert np.allclose(rz.ravel(), fz.ravel() - (eta * (Lw @ w.ravel()) + Gz @ pr), atol=1e-12)
+    assert np.allclose(ry[:, 1:Ny].ravel(), fy[:, 1:Ny].ravel() - (eta * (Lv @ v[:, 1:Ny].ravel()) + Gy @ pr),
+                       atol=1e-12)
+    # the divergence is minus the adjoint of the gradient
+    assert np.allclose(div.ravel(), -(Gx.T @ u.ravel() + Gy.T @ v[:, 1:Ny].ravel() + Gz.T @ w.ravel()), atol=1e-12)
+    us, vs, ws, ps = stokes.solve(fx, fy, fz, eta)
+    (rx, ry, rz), div = stokes.residual(us, vs, ws, ps, fx, fy, fz, eta)
+    nf = np.sqrt(np.sum(fx ** 2) + np.sum(fy ** 2) + np.sum(fz ** 2))
+    assert np.sqrt(np.sum(rx ** 2) + np.sum(ry ** 2) + np.sum(rz ** 2)) < 1e-10 * nf
+    assert np.max(np.abs(div)) < 1e-10
