@@ -53,6 +53,7 @@ enum {
 };
 
 enum { DISCOS_BC_DIRICHLET = 0, DISCOS_BC_NEUMANN = 1 };
+enum { DISCOS_HY_NOSLIP = 0, DISCOS_HY_SLIP = 1 };
 enum { DISCOS_KERNEL_PESKIN4 = 0, DISCOS_KERNEL_PESKIN6 = 1, DISCOS_KERNEL_ES = 2 };
 enum { DISCOS_FP64 = 0, DISCOS_MIXED = 1 };
 enum { DISCOS_WALL_WCA = 0, DISCOS_WALL_LJ93 = 1 };
@@ -64,7 +65,7 @@ enum { DISCOS_INTERP_EFIELD = 0, DISCOS_INTERP_VELOCITY = 1 };
 
 /* Run configuration.  Citations are to the paper's sections and equations. */
 typedef struct discos_config {
-  int Nx, Ny, Nz;          /* cells; Nx, Nz powers of two in [16, 512], Ny in [8, 512] */
+  int Nx, Ny, Nz;          /* cells; Nx, Nz powers of two in [16, 512], Ny in [8, 256] */
   int bc[2];               /* electrostatic wall type, bottom and top: Eq. esbc1 / Eq. esbc3 */
   double phi_b[2];         /* wall potential of a Dirichlet wall (Eq. esbc1) */
   double surf_charge[2];   /* surface charge of a Neumann wall (Eq. esbc3; -eps dphi/dn = varsigma) */
@@ -93,11 +94,31 @@ typedef struct discos_config {
   double E_ext[3];         /* applied uniform field: F_ext = q E_ext (Eq. totalforce) */
   int precision;           /* DISCOS_FP64 or DISCOS_MIXED */
   int max_refine;          /* DISCOS_MIXED: sweeps (0..DISCOS_MAX_REFINE) of residual refinement of every
-                              Poisson solve: r = 4 pi lB rho + lap_h phi in double, phi += A^-1 r */
+                              Poisson solve (r = 4 pi lB rho + lap_h phi in double, phi += A^-1 r) and,
+                              with wet = 1, every Stokes solve (r = f - (eta L v + G p) in double,
+                              (v, p) += the solve of r); the corrections accumulate in double */
   int wet;                 /* 1: hydrodynamic stage (Stokes + midpoint); 0: dry diffusion only */
   int drift;               /* 1: stochastic drift terms on (RFD + midpoint, div D^dry) */
   int max_ions;            /* capacity of the per-ion workspace */
   uint64_t seed;           /* Philox key for all noise */
+  /* Metal strip (Sec. IV.B, Fig. EOgeometry; mixed conditions on one wall,
+     Sec. II.B.1): strip = 1 puts a conducting strip into the bottom wall,
+     which must be a dielectric (NEUMANN) wall.  The strip spans the channel
+     in z and covers the bottom cells whose centre x + 1/2 lies in
+     [strip_x[0], strip_x[1]); on them the wall condition is Dirichlet with
+     phi_m(x) = strip_phi + E_ext[0] (x - x_c), x_c the strip's centre, so
+     that the total potential phi + phi_E (phi_E = -E_ext[0] (x - x_c)) is
+     strip_phi on the metal.  Wall images and ghost cells follow the cell
+     column: Dirichlet rules above the strip, Neumann rules elsewhere. */
+  int strip;
+  double strip_x[2];
+  double strip_phi;
+  /* Hydrodynamic wall conditions, bottom and top (Eq. fluidbc): NOSLIP, or
+     SLIP (zero normal velocity, zero shear stress: like tangential images in
+     spreading, mirrored tangential ghosts in interpolation and in the
+     viscous operator, no stochastic stress on the wall edges).  At most one
+     slip wall: with two, uniform flow along the walls is undamped. */
+  int bc_hy[2];
 } discos_config;
 
 typedef struct discos_handle discos_handle;
@@ -108,10 +129,13 @@ typedef void (*discos_free_fn)(void* ptr, void* ctx);
 
 /* Creates a handle: validates the configuration, allocates the workspace,
  * builds the F^P pair-force table of Sec. II.B.1 (Eq. LC) for the
- * electrostatic kernel and uploads all constants.  Synchronous.
- * Errors: INVALID_ARG (bad sizes, kernel, cutoff, or an all-Neumann channel
- * whose surface charge makes neutrality impossible is not detected here;
- * see discos_spread), OOM, CUDA. */
+ * electrostatic kernel and uploads all constants (with a metal strip, also
+ * the strip's capacitance matrices).  The handle belongs to the CUDA device
+ * that is current at creation; every later call must be made with that
+ * device current (else INVALID_ARG).  Synchronous.
+ * Errors: INVALID_ARG (bad sizes, kernel, cutoff, strip), OOM (alloc_fn or
+ * cudaMalloc returned NULL; whatever was allocated is freed and no handle is
+ * returned), CUDA. */
 discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn,
                             discos_free_fn free_fn, void* alloc_ctx, discos_handle** out);
 
@@ -144,20 +168,24 @@ discos_status discos_probe_read(discos_handle* h, double* total_ms, int* launche
  *   centred, images of sign -1 (Dirichlet wall) / +1 (Neumann wall).
  * which = DISCOS_SPREAD_FORCE: val = F[3][N]; grid = fx[Nz][Ny][Nx] followed
  *   by fy[Nz][Ny+1][Nx] followed by fz[Nz][Ny][Nx] (one contiguous buffer),
- *   no-slip images (opposite normal and tangential force).
+ *   opposite normal images, tangential images opposite at a no-slip wall
+ *   and like at a slip wall.
  * The grid is overwritten (not accumulated into). */
 discos_status discos_spread(discos_handle* h, const void* x, const void* val, int N, int which,
                             void* grid, void* stream);
 
 /* Poisson solve -eps lap_h phi = rho (Eq. poisson) with the wall conditions
  * of Eqs. esbc1 / esbc3, periodic in x and z: DFTs in x and z and a double
- * precision tridiagonal solve per (kx, kz) mode in y.  rho, phi:
- * [Nz][Ny][Nx] reals (may alias).  For two Neumann walls the potential has
- * zero mean and the charge (plus surface charge) must be neutral to
- * 1e-9 relative (checked on the host only by the caller). */
+ * precision tridiagonal solve per (kx, kz) mode in y (with a metal strip,
+ * plus the capacitance correction on the strip's cells).  rho, phi:
+ * [Nz][Ny][Nx] reals (may alias).  For two Neumann walls (no strip) the
+ * potential has zero mean and the charge plus surface charge must vanish
+ * (Sec. II.B.1): the call sums rho in double first (waiting for `stream`) and
+ * returns NOT_NEUTRAL, with nothing launched, beyond 1e-9 (FP64) / 1e-6
+ * (MIXED) of the summed magnitudes. */
 discos_status discos_solve_poisson(discos_handle* h, const void* rho, void* phi, void* stream);
 
-/* Staggered Stokes solve with no-slip walls (Eqs. disc_stokes, fluidbc):
+/* Staggered Stokes solve with no-slip or slip walls (Eqs. disc_stokes, fluidbc):
  * f = fx|fy|fz as in discos_spread(FORCE); v = u|v|w in the same layout
  * (wall rows of v are zero); p = [Nz][Ny][Nx] pressure (mean zero), may be
  * NULL.  f and v may alias. */
@@ -173,7 +201,9 @@ discos_status discos_interpolate(discos_handle* h, const void* x, int N, int whi
 
 /* Cell list of Sec. II.B.1's neighbour sets: list cells of k grid cells per
  * axis (k = ceil(max(psi, largest LJ cutoff))), cell = min(floor(x) div k,
- * nc - 1); counting sort, ions stable by index inside a cell.
+ * nc - 1) with x and z first moved into the periodic box [0, L) (positions
+ * outside it are binned at their periodic image); counting sort, ions
+ * stable by index inside a cell.
  * cell_start[n_cells + 1] and perm[N] are int32 device arrays (either may be
  * NULL); n_cells_out (host, may be NULL) receives n_cells. */
 discos_status discos_cell_list(discos_handle* h, const void* x, int N, int* cell_start,
@@ -187,10 +217,14 @@ discos_status discos_cell_list(discos_handle* h, const void* x, int N, int* cell
  * counterpart; it builds exactly the list discos_cell_list builds, from the
  * configuration alone (no handle).
  * - It calls no allocating routine.  Its scratch is a file-scope device array
- *   of 1048576 + 2 * 262144 + 257 ints (about 6.3 MB) that every GPU loading
+ *   of 1048576 + 2 * 262144 + 258 ints (about 6.3 MB) that every GPU loading
  *   this library holds until the process exits; hence at most 1048576 ions
  *   and 262144 list cells per call, larger requests return INVALID_ARG with
  *   nothing enqueued.
+ * - Positions that are not finite, or outside [0, Ny] in y, are still binned
+ *   (all of them valid list entries) but switch off the per-cell ordering of
+ *   that call: such ions can all share one cell, where the ordering would
+ *   take quadratic time.  The order inside a cell is then unspecified.
  * - The first call on a device (with that device current) looks up the
  *   array's device address; make that first call before any stream capture.
  * - All calls share the one array: calls that overlap on the GPU (different
@@ -211,7 +245,9 @@ discos_status discos_near_field(discos_handle* h, const void* x, const void* q, 
 
 /* Total force, Eq. totalforce: stages 1 and 2 of Sec. II.D
  * (spread, Poisson, field interpolation, near field, wall, external field).
- * F[3][N] is overwritten; nbr_count may be NULL. */
+ * F[3][N] is overwritten; nbr_count may be NULL.  Two Neumann walls (no
+ * strip): sum q plus the surface charges is checked first as in
+ * discos_solve_poisson (NOT_NEUTRAL). */
 discos_status discos_forces(discos_handle* h, const void* x, const void* q, const int* species,
                             int N, void* F, int* nbr_count, void* stream);
 
@@ -220,7 +256,12 @@ discos_status discos_forces(discos_handle* h, const void* x, const void* q, cons
  * Stokes solve and midpoint update of Eqs. step1-step2 (cfg.wet = 1).
  * x is updated in place (wrapped in x, z; specular reflection at the walls).
  * step0 is the index of the first step (it keys the Philox noise).
- * F_out[3][N] (may be NULL) receives the forces of the last step. */
+ * F_out[3][N] (may be NULL) receives the forces of the last step.
+ * Each step bins the ions and works on copies in cell order; results go
+ * back to the caller's order.  Two Neumann walls (no strip): every step sums
+ * q in double on the device and sets bit 2 of the fault word when the
+ * channel is not neutral (discos_solve_poisson's test); the next call then
+ * returns NOT_NEUTRAL (see discos_fault). */
 discos_status discos_step(discos_handle* h, void* x, const void* q, const int* species, int N,
                           int64_t step0, int nsteps, void* F_out, void* stream);
 
@@ -307,11 +348,12 @@ discos_status discos_energy_backward(discos_handle* h, const void* x, const void
 
 /* The device fault word.  Kernels that move ions set bit 0 when a new
  * position is not finite and bit 1 when an ion ends outside the channel (a
- * displacement larger than the channel); neither stops the kernels, whose
- * indexing stays in bounds for any position.  discos_step copies the word to
- * the host behind its steps, and the next discos_step call returns
- * DISCOS_ERR_DEVICE_FAULT, before enqueueing anything, once that copy shows a
- * set bit.  discos_fault returns the word (sync != 0: read now, waiting for
+ * displacement larger than the channel); the step sets bit 2 for a
+ * non-neutral channel between two Neumann walls.  None stops the kernels,
+ * whose indexing stays in bounds for any position.  discos_step copies the
+ * word to the host behind its steps, and the next discos_step call returns
+ * DISCOS_ERR_NOT_NEUTRAL (bit 2) or DISCOS_ERR_DEVICE_FAULT, before
+ * enqueueing anything, once that copy shows a set bit.  discos_fault returns the word (sync != 0: read now, waiting for
  * `stream`; else the last copy that has arrived, 0 if none) and with
  * clear != 0 resets it. */
 discos_status discos_fault(discos_handle* h, int sync, int clear, unsigned* word, void* stream);
@@ -330,6 +372,13 @@ discos_status discos_diagnostics(discos_handle* h, const void* x, const void* q,
  * (n = max_refine + 1 values written to the host array rel).  Waits for
  * `stream`.  Other handles return n = 0. */
 discos_status discos_refine_history(discos_handle* h, double* rel, int* n, void* stream);
+
+/* The same for the most recent Stokes solve of a DISCOS_MIXED wet handle
+ * created with max_refine > 0: relative residuals ||f - (eta L v + G p)|| /
+ * ||f|| of the MAC system of Eq. disc_stokes, with v and p carried in
+ * double (rel[0] after the single-precision solve, rel[k] after k sweeps).
+ * Other handles return n = 0. */
+discos_status discos_refine_history_stokes(discos_handle* h, double* rel, int* n, void* stream);
 
 /* Launch-shape autotuner of the x and z transforms (used by every Poisson
  * and Stokes solve of the handle): times each candidate shape (x: 128 to

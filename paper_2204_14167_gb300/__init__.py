@@ -9,11 +9,12 @@ from dataclasses import dataclass, field
 import ctypes
 
 from . import _lib
-from ._lib import (BC_DIRICHLET, BC_NEUMANN, KERNEL_PESKIN4, KERNEL_PESKIN6, KERNEL_ES, FP64, MIXED,
+from ._lib import (BC_DIRICHLET, BC_NEUMANN, HY_NOSLIP, HY_SLIP, KERNEL_PESKIN4, KERNEL_PESKIN6, KERNEL_ES, FP64, MIXED,
                    WALL_WCA, WALL_LJ93, SPREAD_CHARGE, SPREAD_FORCE, INTERP_EFIELD, INTERP_VELOCITY,
                    DiscosError)
 
-__all__ = ["RunConfig", "Discos", "DiscosError", "fp_table", "BC_DIRICHLET", "BC_NEUMANN", "KERNEL_PESKIN4",
+__all__ = ["RunConfig", "Discos", "DiscosError", "fp_table", "BC_DIRICHLET", "BC_NEUMANN", "HY_NOSLIP", "HY_SLIP",
+           "KERNEL_PESKIN4",
            "KERNEL_PESKIN6", "KERNEL_ES", "FP64", "MIXED", "WALL_WCA", "WALL_LJ93"]
 
 
@@ -60,6 +61,12 @@ class RunConfig:
     drift: bool = True
     max_ions: int = 1024
     seed: int = 20220428
+    # metal strip in the (dielectric) bottom wall: cells with centre in [x0, x1)
+    strip: bool = False
+    strip_x: tuple = (0.0, 0.0)
+    strip_phi: float = 0.0
+    # hydrodynamic wall conditions (bottom, top): HY_NOSLIP or HY_SLIP
+    bc_hy: tuple = (0, 0)
 
     @property
     def dims(self):
@@ -101,13 +108,18 @@ class RunConfig:
         c.drift = int(bool(self.drift))
         c.max_ions = int(self.max_ions)
         c.seed = int(self.seed)
+        c.strip = int(bool(self.strip))
+        c.strip_x[0], c.strip_x[1] = float(self.strip_x[0]), float(self.strip_x[1])
+        c.strip_phi = float(self.strip_phi)
+        c.bc_hy[0], c.bc_hy[1] = int(self.bc_hy[0]), int(self.bc_hy[1])
         return c
 
 
-def _need(t, n, dtype, name, dtypes=None):
+def _need(t, n, dtype, name, dtypes=None, device=None):
     """Reject a device array that the library would read or write past, or
     misread: it must be a contiguous CUDA tensor of the handle's type with at
-    least n elements (None passes: the argument is optional)."""
+    least n elements, on the handle's GPU (None passes: the argument is
+    optional)."""
     if t is None:
         return
     ok_type = t.dtype in dtypes if dtypes else t.dtype == dtype
@@ -115,6 +127,8 @@ def _need(t, n, dtype, name, dtypes=None):
         where = "" if getattr(t, "is_cuda", False) else " on the host"
         raise ValueError(f"{name}: need a contiguous CUDA tensor of {dtype} with at least {n} elements, "
                          f"got shape {tuple(t.shape)} {t.dtype}{where}")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name}: on {t.device}, but the handle lives on {device}")
 
 
 def _ptr(t):
@@ -137,6 +151,9 @@ class Discos:
         if not torch.cuda.is_available():
             raise RuntimeError("libdiscos needs a CUDA device")
         torch.cuda.init()
+        # the library launches on the current device; the handle's workspace
+        # lives on the device current at creation, and every tensor must too
+        self.device = torch.device("cuda", torch.cuda.current_device())
         self.cfg = cfg
         self._c = cfg.to_c()
         h = ctypes.c_void_p()
@@ -157,8 +174,15 @@ class Discos:
             pass
 
     # -- helpers
+    def _need(self, t, n, dtype, name, dtypes=None):
+        _need(t, n, dtype, name, dtypes, self.device)
+
     def _check_ions(self, x):
-        assert x.is_cuda and x.dtype == self.dtype and x.is_contiguous() and x.shape[0] == 3, "bad positions"
+        if not (getattr(x, "is_cuda", False) and x.dtype == self.dtype and x.is_contiguous() and x.dim() == 2
+                and x.shape[0] == 3):
+            raise ValueError(f"positions: need a contiguous (3, N) CUDA tensor of {self.dtype}")
+        if x.device != self.device:
+            raise ValueError(f"positions: on {x.device}, but the handle lives on {self.device}")
         return x.shape[1]
 
     def _G(self):
@@ -172,44 +196,44 @@ class Discos:
     def _ions_q(self, x, q, species=None):
         import torch
         N = self._check_ions(x)
-        _need(q, N, self.dtype, "q")
-        _need(species, N, torch.int32, "species")
+        self._need(q, N, self.dtype, "q")
+        self._need(species, N, torch.int32, "species")
         return N
 
     def empty_grid(self, kind="cell"):
         import torch
         Nx, Ny, Nz = self.cfg.dims
         if kind == "cell":
-            return torch.empty((Nz, Ny, Nx), dtype=self.dtype, device="cuda")
+            return torch.empty((Nz, Ny, Nx), dtype=self.dtype, device=self.device)
         n = Nx * Nz * (3 * Ny + 1)
-        return torch.empty(n, dtype=self.dtype, device="cuda")
+        return torch.empty(n, dtype=self.dtype, device=self.device)
 
     # -- entry points
     def spread_charge(self, x, q, out=None, stream=None):
         N = self._ions_q(x, q)
-        _need(out, self._G(), self.dtype, "out")
+        self._need(out, self._G(), self.dtype, "out")
         rho = self.empty_grid("cell") if out is None else out
         _lib.check(self._lib.discos_spread(self._h, _ptr(x), _ptr(q), N, SPREAD_CHARGE, _ptr(rho), _stream(stream)))
         return rho
 
     def spread_force(self, x, F, out=None, stream=None):
         N = self._check_ions(x)
-        _need(F, 3 * N, self.dtype, "F")
-        _need(out, self._Gf(), self.dtype, "out")
+        self._need(F, 3 * N, self.dtype, "F")
+        self._need(out, self._Gf(), self.dtype, "out")
         f = self.empty_grid("mac") if out is None else out
         _lib.check(self._lib.discos_spread(self._h, _ptr(x), _ptr(F), N, SPREAD_FORCE, _ptr(f), _stream(stream)))
         return f
 
     def solve_poisson(self, rho, out=None, stream=None):
-        _need(rho, self._G(), self.dtype, "rho")
-        _need(out, self._G(), self.dtype, "out")
+        self._need(rho, self._G(), self.dtype, "rho")
+        self._need(out, self._G(), self.dtype, "out")
         phi = self.empty_grid("cell") if out is None else out
         _lib.check(self._lib.discos_solve_poisson(self._h, _ptr(rho), _ptr(phi), _stream(stream)))
         return phi
 
     def solve_stokes(self, f, out=None, pressure=False, stream=None):
-        _need(f, self._Gf(), self.dtype, "f")
-        _need(out, self._Gf(), self.dtype, "out")
+        self._need(f, self._Gf(), self.dtype, "f")
+        self._need(out, self._Gf(), self.dtype, "out")
         v = self.empty_grid("mac") if out is None else out
         p = self.empty_grid("cell") if pressure else None
         _lib.check(self._lib.discos_solve_stokes(self._h, _ptr(f), _ptr(v), _ptr(p), _stream(stream)))
@@ -218,8 +242,8 @@ class Discos:
     def interpolate_efield(self, x, phi, stream=None):
         import torch
         N = self._check_ions(x)
-        _need(phi, self._G(), self.dtype, "phi")
-        out = torch.empty((3, N), dtype=self.dtype, device="cuda")
+        self._need(phi, self._G(), self.dtype, "phi")
+        out = torch.empty((3, N), dtype=self.dtype, device=self.device)
         _lib.check(self._lib.discos_interpolate(self._h, _ptr(x), N, INTERP_EFIELD, _ptr(phi), _ptr(out),
                                                 _stream(stream)))
         return out
@@ -227,8 +251,8 @@ class Discos:
     def interpolate_velocity(self, x, v, stream=None):
         import torch
         N = self._check_ions(x)
-        _need(v, self._Gf(), self.dtype, "v")
-        out = torch.empty((3, N), dtype=self.dtype, device="cuda")
+        self._need(v, self._Gf(), self.dtype, "v")
+        out = torch.empty((3, N), dtype=self.dtype, device=self.device)
         _lib.check(self._lib.discos_interpolate(self._h, _ptr(x), N, INTERP_VELOCITY, _ptr(v), _ptr(out),
                                                 _stream(stream)))
         return out
@@ -238,18 +262,18 @@ class Discos:
         N = self._check_ions(x)
         n = ctypes.c_int()
         _lib.check(self._lib.discos_cell_list(self._h, _ptr(x), 0, None, None, ctypes.byref(n), _stream(stream)))
-        start = torch.empty(n.value + 1, dtype=torch.int32, device="cuda")
-        perm = torch.empty(max(N, 1), dtype=torch.int32, device="cuda")
+        start = torch.empty(n.value + 1, dtype=torch.int32, device=self.device)
+        perm = torch.empty(max(N, 1), dtype=torch.int32, device=self.device)
         _lib.check(self._lib.discos_cell_list(self._h, _ptr(x), N, _ptr(start), _ptr(perm), None, _stream(stream)))
         return start, perm[:N]
 
     def near_field(self, x, q, species=None, F=None, counts=True, stream=None):
         import torch
         N = self._ions_q(x, q, species)
-        _need(F, 3 * N, self.dtype, "F")
+        self._need(F, 3 * N, self.dtype, "F")
         if F is None:
-            F = torch.zeros((3, N), dtype=self.dtype, device="cuda")
-        nbr = torch.empty(max(N, 1), dtype=torch.int32, device="cuda") if counts else None
+            F = torch.zeros((3, N), dtype=self.dtype, device=self.device)
+        nbr = torch.empty(max(N, 1), dtype=torch.int32, device=self.device) if counts else None
         _lib.check(self._lib.discos_near_field(self._h, _ptr(x), _ptr(q), _ptr(species), N, _ptr(F), _ptr(nbr),
                                                _stream(stream)))
         return (F, nbr[:N]) if counts else F
@@ -257,8 +281,8 @@ class Discos:
     def forces(self, x, q, species=None, counts=False, stream=None):
         import torch
         N = self._ions_q(x, q, species)
-        F = torch.empty((3, N), dtype=self.dtype, device="cuda")
-        nbr = torch.empty(max(N, 1), dtype=torch.int32, device="cuda") if counts else None
+        F = torch.empty((3, N), dtype=self.dtype, device=self.device)
+        nbr = torch.empty(max(N, 1), dtype=torch.int32, device=self.device) if counts else None
         _lib.check(self._lib.discos_forces(self._h, _ptr(x), _ptr(q), _ptr(species), N, _ptr(F), _ptr(nbr),
                                            _stream(stream)))
         return (F, nbr[:N]) if counts else F
@@ -266,7 +290,7 @@ class Discos:
     def step(self, x, q, species=None, step0=0, nsteps=1, F_out=None, stream=None):
         """Advance x in place by nsteps steps; returns x."""
         N = self._ions_q(x, q, species)
-        _need(F_out, 3 * N, self.dtype, "F_out")
+        self._need(F_out, 3 * N, self.dtype, "F_out")
         _lib.check(self._lib.discos_step(self._h, _ptr(x), _ptr(q), _ptr(species), N, int(step0), int(nsteps),
                                          _ptr(F_out), _stream(stream)))
         return x
@@ -292,8 +316,8 @@ class Discos:
         """Double-precision sums: dict(sum_q, sum_rho, sum_F, nonfinite, escaped)."""
         import torch
         N = self._ions_q(x, q)
-        _need(F, 3 * N, self.dtype, "F")
-        out = torch.zeros(8, dtype=torch.float64, device="cuda")
+        self._need(F, 3 * N, self.dtype, "F")
+        out = torch.zeros(8, dtype=torch.float64, device=self.device)
         _lib.check(self._lib.discos_diagnostics(self._h, _ptr(x), _ptr(q), _ptr(F), N, int(bool(with_rho)),
                                                 _ptr(out), _stream(stream)))
         o = out.cpu().tolist()
@@ -304,6 +328,13 @@ class Discos:
         buf = (ctypes.c_double * 8)()
         n = ctypes.c_int()
         _lib.check(self._lib.discos_refine_history(self._h, buf, ctypes.byref(n), _stream(stream)))
+        return [buf[i] for i in range(n.value)]
+
+    def refine_history_stokes(self, stream=None):
+        """Relative residuals of the last Stokes solve: [after the solve, after sweep 1, ...]."""
+        buf = (ctypes.c_double * 8)()
+        n = ctypes.c_int()
+        _lib.check(self._lib.discos_refine_history_stokes(self._h, buf, ctypes.byref(n), _stream(stream)))
         return [buf[i] for i in range(n.value)]
 
     # -- batched replicas
@@ -317,18 +348,18 @@ class Discos:
         R = len(off) - 1
         Ntot = off[-1] if off else 0
         ints = (torch.int32, getattr(torch, "uint32", torch.int32))
-        _need(x, 3 * Ntot, self.dtype, "x")          # the library itself requires a MIXED handle
-        _need(q, Ntot, self.dtype, "q")
-        _need(species, Ntot, torch.int32, "species")
-        _need(phi_b, 2 * R, torch.float64, "phi_b")
-        _need(hist, R * self.cfg.nspecies * self.cfg.Ny, torch.int32, "hist", ints)
-        _need(sums, 4 * R, torch.float64, "sums")
-        _need(F_out, 3 * Ntot, self.dtype, "F_out")
-        _need(nbr, Ntot, torch.int32, "nbr")
+        self._need(x, 3 * Ntot, self.dtype, "x")          # the library itself requires a MIXED handle
+        self._need(q, Ntot, self.dtype, "q")
+        self._need(species, Ntot, torch.int32, "species")
+        self._need(phi_b, 2 * R, torch.float64, "phi_b")
+        self._need(hist, R * self.cfg.nspecies * self.cfg.Ny, torch.int32, "hist", ints)
+        self._need(sums, 4 * R, torch.float64, "sums")
+        self._need(F_out, 3 * Ntot, self.dtype, "F_out")
+        self._need(nbr, Ntot, torch.int32, "nbr")
         b = _lib.Batch()
         b.R = R
         b._off_host = (ctypes.c_int * (R + 1))(*off)
-        b._off_dev = torch.tensor(off, dtype=torch.int32, device="cuda")
+        b._off_dev = torch.tensor(off, dtype=torch.int32, device=self.device)
         b.offsets_host = ctypes.cast(b._off_host, ctypes.POINTER(ctypes.c_int))
         b.offsets = b._off_dev.data_ptr()
         b._keep = (x, q, species, phi_b, hist, sums, F_out, nbr)
@@ -362,8 +393,8 @@ class Discos:
         """Discrete electrostatic energy U as a float64 CUDA scalar."""
         import torch
         N = self._check_ions(x)
-        _need(q, N, self.dtype, "q")
-        U = torch.empty((), dtype=torch.float64, device="cuda") if out is None else out
+        self._need(q, N, self.dtype, "q")
+        U = torch.empty((), dtype=torch.float64, device=self.device) if out is None else out
         _lib.check(self._lib.discos_energy(self._h, _ptr(x), _ptr(q), N, self._phi_b(phi_b), _ptr(U),
                                            _stream(stream)))
         return U
@@ -372,11 +403,11 @@ class Discos:
         """(dx, dq, dphi_b) = dU * gradients of U; entries not in `need` are None."""
         import torch
         N = self._check_ions(x)
-        _need(q, N, self.dtype, "q")
-        dU = dU.to(device="cuda", dtype=torch.float64).contiguous()
-        dx = torch.empty((3, N), dtype=self.dtype, device="cuda") if need[0] else None
-        dq = torch.empty(N, dtype=self.dtype, device="cuda") if need[1] else None
-        db = torch.empty(2, dtype=torch.float64, device="cuda") if need[2] else None
+        self._need(q, N, self.dtype, "q")
+        dU = dU.to(device=self.device, dtype=torch.float64).contiguous()
+        dx = torch.empty((3, N), dtype=self.dtype, device=self.device) if need[0] else None
+        dq = torch.empty(N, dtype=self.dtype, device=self.device) if need[1] else None
+        db = torch.empty(2, dtype=torch.float64, device=self.device) if need[2] else None
         _lib.check(self._lib.discos_energy_backward(self._h, _ptr(x), _ptr(q), N, self._phi_b(phi_b), _ptr(dU),
                                                     _ptr(dx), _ptr(dq), _ptr(db), _stream(stream)))
         return dx, dq, db

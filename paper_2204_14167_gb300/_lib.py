@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, "libdiscos.so")
 MAX_SPECIES = 4
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_NOT_NEUTRAL, ERR_NOT_CONVERGED, ERR_DEVICE_FAULT, ERR_TIMEOUT, ERR_CUDA = range(8)
 BC_DIRICHLET, BC_NEUMANN = 0, 1
+HY_NOSLIP, HY_SLIP = 0, 1
 KERNEL_PESKIN4, KERNEL_PESKIN6, KERNEL_ES = 0, 1, 2
 FP64, MIXED = 0, 1
 WALL_WCA, WALL_LJ93 = 0, 1
@@ -48,6 +49,10 @@ class Config(ctypes.Structure):
         ("drift", ctypes.c_int),
         ("max_ions", ctypes.c_int),
         ("seed", ctypes.c_uint64),
+        ("strip", ctypes.c_int),
+        ("strip_x", D * 2),
+        ("strip_phi", D),
+        ("bc_hy", ctypes.c_int * 2),
     ]
 
 
@@ -75,6 +80,7 @@ EXPORTS = [
     "discos_probe", "discos_probe_read", "discos_energy", "discos_energy_backward",
     "discos_step_batched", "discos_tune_batched", "discos_set_batched_shape", "discos_refine_history",
     "discos_fault", "discos_diagnostics", "discos_tune_transforms", "discos_set_transform_shape",
+    "discos_refine_history_stokes",
 ]
 PROBE_FAMILIES = ["cell_list", "near_field", "noise", "spread_charge", "fft_x", "fft_z", "poisson_y", "interp_e",
                   "spread_force", "stokes_y", "interp_v", "update"]
@@ -117,6 +123,7 @@ def load():
     lib.discos_fault.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_uint), vp]
     lib.discos_diagnostics.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp]
     lib.discos_refine_history.argtypes = [vp, ctypes.POINTER(D), ctypes.POINTER(i32), vp]
+    lib.discos_refine_history_stokes.argtypes = [vp, ctypes.POINTER(D), ctypes.POINTER(i32), vp]
     lib.discos_cell_list_noalloc.argtypes = [ctypes.POINTER(Config), vp, i32, vp, vp, ctypes.POINTER(i32), vp]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int

@@ -26,6 +26,7 @@ discos_status check_batch(discos_handle* h, const discos_batch* b, int* Ntot) {
   if (c.bc[0] == DISCOS_BC_NEUMANN && c.bc[1] == DISCOS_BC_NEUMANN)
     return invalid("batched replicas need at least one Dirichlet wall");
   if (c.wet) return invalid("batched replicas run the dry step (cfg.wet = 0)");
+  if (c.strip) return invalid("batched replicas have no metal strip");
   const Params& P = h->P;
   if (P.ncx < 3 || P.ncz < 3 || P.ncx * P.ncy * P.ncz > 4096) return invalid("list cells outside the batched limits");
   if (c.n_tab > 1024) return invalid("n_tab > 1024 for the batched path");

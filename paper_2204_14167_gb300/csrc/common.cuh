@@ -217,6 +217,27 @@ __device__ __forceinline__ void normals4(u32x4 c, uint64_t seed, float out[4]) {
   out[0] = a * c1; out[1] = a * s1; out[2] = b * c3; out[3] = b * s3;
 }
 
+// The first two of the four normals of normals4 (one Box-Muller pair), for
+// draws that use only those.
+__device__ __forceinline__ void normals2(u32x4 c, uint64_t seed, double out[2]) {
+  u32x4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const double s = 2.3283064365386963e-10;
+  double u0 = ((double)r.x + 0.5) * s, u1 = ((double)r.y + 0.5) * s;
+  double a = sqrt(-2.0 * log(u0));
+  double s1, c1;
+  sincospi(2.0 * u1, &s1, &c1);
+  out[0] = a * c1; out[1] = a * s1;
+}
+__device__ __forceinline__ void normals2(u32x4 c, uint64_t seed, float out[2]) {
+  u32x4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const float s = 2.3283064365386963e-10f, h = 1.1641532182693481e-10f;
+  float u0 = fmaf((float)r.x, s, h), u1 = fmaf((float)r.y, s, h);
+  float a = sqrtf(-2.0f * logf(u0));
+  float s1, c1;
+  sincospif(2.0f * u1, &s1, &c1);
+  out[0] = a * c1; out[1] = a * s1;
+}
+
 enum { TAG_DRY = 1, TAG_RFD = 2, TAG_STRESS_A = 3, TAG_STRESS_B = 4 };
 
 // ------------------------------------------------------------ warp helpers

@@ -132,9 +132,9 @@ void upload_table(void* dst, const std::vector<double>& t) {
 
 // Per-mode factors of the Stokes wall-normal systems (see k_stokes.cu):
 // the L D L^T factors of the pentadiagonal K^2 A_f + D_y^T A_c D_y
-// (diagonal K^4 + 4K^2 + 6, +1 on the first and last rows; first
-// off-diagonal -2K^2 - 4; second off-diagonal 1) and the Thomas pivots of
-// A_c (diagonal K^2 + 2, +1 on the wall rows; off-diagonals -1).
+// (diagonal K^4 + 4K^2 + 6, +1 (no-slip) or -1 (slip) on the first and last
+// rows; first off-diagonal -2K^2 - 4; second off-diagonal 1) and the Thomas
+// pivots of A_c (diagonal K^2 + 2, +-1 on the wall rows; off-diagonals -1).
 void upload_stokes_factors(discos_handle* h) {
   const discos_config& c = h->cfg;
   const int Ny = c.Ny, Nxh = h->P.Nxh, Nz = c.Nz;
@@ -154,11 +154,14 @@ void upload_stokes_factors(discos_handle* h) {
       mc[5 * m + 3] = std::sin(tz);
       mc[5 * m + 4] = zero ? 0.0 : -1.0 / K2;
       const double e = -2.0 * K2 - 4.0, f = 1.0;
+      // the tangential ghost of a no-slip wall (-u(0)) adds +1 to its cell
+      // row's diagonal, that of a slip wall (+u(0)) -1 (Eq. fluidbc)
+      const double sb = h->P.slip[0] ? -1.0 : 1.0, st = h->P.slip[1] ? -1.0 : 1.0;
       double Dm1 = 0.0, Dm2 = 0.0, l1m1 = 0.0;
       for (int i = 0; i < n; ++i) {
         double a2 = i >= 2 ? f / Dm2 : 0.0;
         double a1 = i >= 1 ? (e - (i >= 2 ? a2 * l1m1 * Dm2 : 0.0)) / Dm1 : 0.0;
-        double d = K2 * K2 + 4.0 * K2 + 6.0 + (i == 0 ? 1.0 : 0.0) + (i == n - 1 ? 1.0 : 0.0);
+        double d = K2 * K2 + 4.0 * K2 + 6.0 + (i == 0 ? sb : 0.0) + (i == n - 1 ? st : 0.0);
         double D = d - a1 * a1 * Dm1 - a2 * a2 * Dm2;
         l1[m * Ny + i + 1] = zero ? 0.0 : a1;
         l2[m * Ny + i + 1] = zero ? 0.0 : a2;
@@ -167,7 +170,7 @@ void upload_stokes_factors(discos_handle* h) {
       }
       double mm = 0.0;
       for (int j = 0; j < Ny; ++j) {
-        double a = K2 + 2.0 + (j == 0 ? 1.0 : 0.0) + (j == Ny - 1 ? 1.0 : 0.0);
+        double a = K2 + 2.0 + (j == 0 ? sb : 0.0) + (j == Ny - 1 ? st : 0.0);
         mm = j == 0 ? a : a - 1.0 / mm;
         ci[m * Ny + j] = 1.0 / mm;
       }
@@ -187,47 +190,210 @@ void upload_stokes_factors(discos_handle* h) {
   }
 }
 
+// Inverse of a dense n x n matrix (row major) by Gauss-Jordan elimination
+// with partial pivoting, in double; false if singular.
+bool invert_dense(std::vector<double>& a, int n) {
+  std::vector<double> inv((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(a[(size_t)r * n + col]) > std::fabs(a[(size_t)piv * n + col])) piv = r;
+    if (!(std::fabs(a[(size_t)piv * n + col]) > 0.0)) return false;
+    if (piv != col)
+      for (int k = 0; k < n; ++k) {
+        std::swap(a[(size_t)piv * n + k], a[(size_t)col * n + k]);
+        std::swap(inv[(size_t)piv * n + k], inv[(size_t)col * n + k]);
+      }
+    const double d = 1.0 / a[(size_t)col * n + col];
+    for (int k = 0; k < n; ++k) { a[(size_t)col * n + k] *= d; inv[(size_t)col * n + k] *= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double f = a[(size_t)r * n + col];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        a[(size_t)r * n + k] -= f * a[(size_t)col * n + k];
+        inv[(size_t)r * n + k] -= f * inv[(size_t)col * n + k];
+      }
+    }
+  }
+  a.swap(inv);
+  return true;
+}
+
+// Metal strip (k_strip.cu): the strip's cell columns, the bottom-row terms
+// of the base solve, and per z mode the inverse capacitance matrix
+// (I/2 + C_kz)^-1, C_kz[a][b] = (1/Nx) sum_kx g(kx, kz) cos(2 pi kx (a - b) / Nx)
+// with g = [T^-1]_00 the bottom-to-bottom entry of the wall-normal
+// tridiagonal inverse of mode (kx, kz) for an all-dielectric bottom wall.
+// When that operator is singular (top wall dielectric as well), its (0, 0)
+// mode takes the pseudo-inverse entry (DCT-II eigenbasis of the
+// all-Neumann second difference) and the kz = 0 matrix is the bordered
+// one of k_strip.cu.
+void setup_strip(discos_handle* h, std::vector<double>& add0, std::vector<double>& Minv) {
+  const discos_config& c = h->cfg;
+  Params& P = h->P;
+  const int Nx = c.Nx, Ny = c.Ny, Nz = c.Nz;
+  const int Ws = P.strip_i1 - P.strip_i0, S = Ws + 1;
+  add0.assign(Nx, 0.0);
+  for (int i = 0; i < Nx; ++i)
+    add0[i] = on_strip(P, i) ? 2.0 * (P.strip_phi + P.E_ext[0] * ((i + 0.5) - P.strip_xc)) : -P.slope[0];
+  const double top = c.bc[1] == DISCOS_BC_DIRICHLET ? 2.0 * c.phi_b[1] : P.slope[1];
+  double sum0 = 0.0;
+  for (double v : add0) sum0 += v;
+  P.strip_walls = (double)Nz * sum0 + (double)Nx * Nz * top;
+  std::vector<double> g((size_t)Nx);
+  std::vector<double> cp(Ny), dd(Ny);
+  Minv.assign((size_t)Nz * S * S, 0.0);
+  for (int kz = 0; kz < Nz; ++kz) {
+    const double lz = 2.0 - 2.0 * std::cos(2.0 * M_PI * kz / Nz);
+    for (int kx = 0; kx < Nx; ++kx) {
+      const double lam = lz + 2.0 - 2.0 * std::cos(2.0 * M_PI * kx / Nx);
+      if (P.strip_singular && kx == 0 && kz == 0) {
+        double acc = 0.0;
+        for (int m = 1; m < Ny; ++m) {
+          const double v0 = std::cos(M_PI * m / (2.0 * Ny));
+          acc += (2.0 / Ny) * v0 * v0 / (2.0 - 2.0 * std::cos(M_PI * m / Ny));
+        }
+        g[kx] = acc;
+        continue;
+      }
+      // Thomas solve of T u = e_0, T = tridiag(-1, 2 + lam, -1) with the wall rows
+      for (int j = 0; j < Ny; ++j) {
+        dd[j] = 2.0 + lam + (j == 0 ? -1.0 : 0.0) +
+                (j == Ny - 1 ? (c.bc[1] == DISCOS_BC_DIRICHLET ? 1.0 : -1.0) : 0.0);
+      }
+      std::vector<double> rhs(Ny, 0.0);
+      rhs[0] = 1.0;
+      double m = dd[0];
+      cp[0] = -1.0 / m;
+      rhs[0] /= m;
+      for (int j = 1; j < Ny; ++j) {
+        m = dd[j] + cp[j - 1];
+        cp[j] = -1.0 / m;
+        rhs[j] = (rhs[j] + rhs[j - 1]) / m;
+      }
+      for (int j = Ny - 2; j >= 0; --j) rhs[j] -= cp[j] * rhs[j + 1];
+      g[kx] = rhs[0];
+    }
+    std::vector<double> cd(Ws);
+    for (int d = 0; d < Ws; ++d) {
+      double acc = 0.0;
+      for (int kx = 0; kx < Nx; ++kx) acc += g[kx] * std::cos(2.0 * M_PI * (double)((long long)kx * d % Nx) / Nx);
+      cd[d] = acc / Nx;
+    }
+    const bool border = P.strip_singular && kz == 0;
+    const int n = border ? S : Ws;
+    std::vector<double> a((size_t)n * n, 0.0);
+    for (int i = 0; i < Ws; ++i)
+      for (int j = 0; j < Ws; ++j) a[(size_t)i * n + j] = cd[i > j ? i - j : j - i] + (i == j ? 0.5 : 0.0);
+    if (border) {
+      for (int i = 0; i < Ws; ++i) {
+        a[(size_t)i * n + Ws] = -1.0;
+        a[(size_t)Ws * n + i] = 1.0;
+      }
+    }
+    invert_dense(a, n);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) Minv[(size_t)kz * S * S + (size_t)i * S + j] = a[(size_t)i * n + j];
+  }
+}
+
 void free_workspace(discos_handle* h) {
   free_batch(h);
   Workspace& W = h->W;
   void* ptrs[] = {W.phi, W.spec, W.fgrid, W.piv64, W.piv32, W.tw_x, W.tw_z, W.fptab, W.cell_of, W.counts, W.fill,
-                  W.cell_start, W.perm, W.tile_sums, W.xs, W.qs, W.sps, W.F, W.xstar, W.V,
+                  W.cell_start, W.perm, W.tile_sums, W.xs, W.qs, W.sps, W.xq, W.F, W.xstar, W.V,
                   W.st_l1, W.st_l2, W.st_di, W.st_ci, W.st_mc,
                   W.lo_modes, W.is_lo, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf, W.Fn, W.edata, W.rref, W.rres, W.rnorm,
-                  W.fault, W.diag};
+                  W.fault, W.diag, W.nsum, W.phi64, W.sref, W.sres, W.pres, W.v64, W.p64, W.snorm,
+                  W.strip_g, W.strip_add0, W.strip_r, W.strip_shat, W.strip_M, W.strip_c};
   for (void* p : ptrs) dfree(h, p);
   W = Workspace{};
 }
 
-// Stages 1 and 2 of Sec. II.D.  The near field (cell list + pair loop) does
-// not depend on the potential, so it runs on the handle's side stream while
-// the main stream spreads the charge and solves the Poisson problem; the
-// field interpolation then adds the near-field forces (F = q (E + E_ext) +
-// F_near).  `side_extra` enqueues further independent work on the side
-// stream before it rejoins (the step uses it for the stochastic stress).
+// Neutrality of a channel between two Neumann walls (Sec. II.B.1): the
+// charge plus the walls' surface charge must vanish, else the Poisson problem
+// has no solution.  Relative tolerance 1e-9 (FP64) / 1e-6 (MIXED) of the
+// summed magnitudes.
+bool all_neumann(const discos_handle* h) {
+  return h->P.bc[0] == DISCOS_BC_NEUMANN && h->P.bc[1] == DISCOS_BC_NEUMANN && !h->P.strip;
+}
+double surface_total(const discos_handle* h, bool absolute) {
+  const double a = h->cfg.surf_charge[0], b = h->cfg.surf_charge[1];
+  return (absolute ? std::fabs(a) + std::fabs(b) : a + b) * (double)h->cfg.Nx * (double)h->cfg.Nz;
+}
+double neutral_tol(const discos_handle* h) { return h->mixed ? 1e-6 : 1e-9; }
+
+// Synchronous check of n charges (or cell charges) v before a solve.
+template <typename T>
+discos_status check_neutral_sync(discos_handle* h, const T* v, size_t n, cudaStream_t s, const char* what) {
+  if (!all_neumann(h)) return DISCOS_OK;
+  double buf[2] = {0.0, 0.0};
+  cudaError_t e = launch_charge_sums<T>(v, n, h->W.nsum, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(buf, h->W.nsum, sizeof(buf), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e, what);
+  const double net = buf[0] + surface_total(h, false);
+  if (!(std::fabs(net) <= neutral_tol(h) * (buf[1] + surface_total(h, true)) + 1e-12)) {
+    set_error(std::string(what) + ": two Neumann walls need a neutral channel (charge + surface charge = " +
+              std::to_string(net) + ")");
+    return DISCOS_ERR_NOT_NEUTRAL;
+  }
+  return DISCOS_OK;
+}
+
+// The single-operation entry points work on the ions in the caller's order.
+template <typename T>
+cudaError_t spread_impl(discos_handle* h, const T* x, const T* val, int N, int which, T* grid, cudaStream_t s) {
+  if (which == DISCOS_SPREAD_CHARGE) return launch_spread_charge<T>(h->P, x, val, N, grid, s);
+  return launch_spread_force<T>(h->P, x, val, N, grid, 0, false, s, false, nullptr, false);
+}
+
+template <typename T>
+cudaError_t interp_impl(discos_handle* h, const T* x, int N, int which, const T* grid, T* out, cudaStream_t s) {
+  if (which == DISCOS_INTERP_VELOCITY) return launch_interp_velocity<T>(h->P, x, N, grid, out, s, nullptr);
+  return launch_interp_efield<T>(h->P, x, static_cast<const T*>(nullptr), N, grid, out, false, s,
+                                 static_cast<const T*>(nullptr), nullptr);
+}
+
+// Stages 1 and 2 of Sec. II.D.  The ions are first binned and copied into
+// cell order (W.xs, W.qs, W.sps, W.xq; W.perm maps a sorted index to the
+// caller's), so that every particle kernel after it walks space in order and
+// its grid accesses stay local.  The near field does not depend on the
+// potential, so it runs on the handle's side stream while the main stream
+// spreads the charge and solves the Poisson problem; the field interpolation
+// then adds the near-field forces (F = q (E + E_ext) + F_near).  `side_extra`
+// enqueues further independent work on the side stream before it rejoins
+// (the step uses it for the stochastic stress).  With sorted_out the forces
+// stay in cell order (the step's own use), else they are written in the
+// caller's order; nbr is always in the caller's order.
 template <typename T, typename Extra>
 discos_status forces_impl(discos_handle* h, const T* x, const T* q, const int* species, int N, T* F, int* nbr,
-                          cudaStream_t s, Extra side_extra) {
+                          cudaStream_t s, Extra side_extra, bool sorted_out) {
   const Params& P = h->P;
   Workspace& W = h->W;
   T* phi = reinterpret_cast<T*>(W.phi);
   T* Fn = reinterpret_cast<T*>(W.Fn);
-  cudaError_t e = cudaEventRecord(h->ev_fork, s);
+  cudaError_t e = launch_sort_ions<T>(P, W, x, q, species, N, s);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
-  if (e == cudaSuccess) e = launch_near_field<T>(P, W, x, q, species, N, Fn, nbr, h->side, false);
+  if (e == cudaSuccess) e = launch_near_field_sorted<T>(P, W, N, Fn, nbr, nullptr, W.perm, h->side, false);
   if (e == cudaSuccess) e = side_extra(h->side);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->side);
-  if (e == cudaSuccess) e = launch_spread_charge<T>(P, x, q, N, phi, s);
+  const T* xs = reinterpret_cast<const T*>(W.xs);
+  const T* qs = reinterpret_cast<const T*>(W.qs);
+  if (e == cudaSuccess) e = launch_spread_charge<T>(P, xs, qs, N, phi, s, true);
   if (e == cudaSuccess) e = launch_poisson<T>(P, W, phi, phi, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_join, 0);
-  if (e == cudaSuccess) e = launch_interp_efield<T>(P, x, q, N, phi, F, true, s, Fn);
+  if (e == cudaSuccess) e = launch_interp_efield<T>(P, xs, qs, N, phi, F, true, s, Fn, sorted_out ? nullptr : W.perm);
   return cuda_status(e, "discos_forces");
 }
 
 template <typename T>
 discos_status forces_impl(discos_handle* h, const T* x, const T* q, const int* species, int N, T* F, int* nbr,
                           cudaStream_t s) {
-  return forces_impl<T>(h, x, q, species, N, F, nbr, s, [](cudaStream_t) { return cudaSuccess; });
+  return forces_impl<T>(h, x, q, species, N, F, nbr, s, [](cudaStream_t) { return cudaSuccess; }, false);
 }
 
 template <typename T>
@@ -239,37 +405,48 @@ discos_status step_impl(discos_handle* h, T* x, const T* q, const int* species, 
   T* fg = reinterpret_cast<T*>(W.fgrid);
   T* V = reinterpret_cast<T*>(W.V);
   T* xs = reinterpret_cast<T*>(W.xstar);
+  const T* xsrt = reinterpret_cast<const T*>(W.xs);
   const bool wet = h->cfg.wet != 0;
   const bool thermal = P.kT > 0.0;
   const bool drift = P.drift != 0;
   const size_t nf = (size_t)P.Nx * P.Nz * (3 * P.Ny + 1);
   for (int n = 0; n < nsteps; ++n) {
     const int64_t step = step0 + n;
+    // two Neumann walls: a non-neutral channel sets bit 2 of the fault word,
+    // and the next discos_step call returns DISCOS_ERR_NOT_NEUTRAL
+    if (all_neumann(h)) {
+      cudaError_t e = launch_charge_sums<T>(q, (size_t)N, W.nsum, s);
+      if (e == cudaSuccess)
+        e = launch_neutral_flag(W.nsum, surface_total(h, false), surface_total(h, true), neutral_tol(h), W.fault, s);
+      if (e != cudaSuccess) return cuda_status(e, "discos_step");
+    }
     // the stochastic stress (or a zero fill) initialises the fluid forcing on
     // the side stream, overlapping the electrostatics
     auto side = [&](cudaStream_t ss) -> cudaError_t {
       if (!wet) return cudaSuccess;
       return thermal ? launch_stress_noise<T>(P, fg, step, ss, true) : launch_fill_zero<T>(fg, nf, ss);
     };
-    discos_status st = forces_impl<T>(h, x, q, species, N, F, nullptr, s, side);
+    // F comes back in cell order: everything below works on the sorted ions
+    // and the update writes each new position back to the caller's index
+    discos_status st = forces_impl<T>(h, x, q, species, N, F, nullptr, s, side, true);
     if (st != DISCOS_OK) return st;
     cudaError_t e = cudaSuccess;
     if (wet) {
-      e = launch_spread_force<T>(P, x, F, N, fg, step, drift && thermal, s, true);
+      e = launch_spread_force<T>(P, xsrt, F, N, fg, step, drift && thermal, s, true, W.perm, true);
       if (e == cudaSuccess) e = launch_stokes<T>(P, W, fg, fg, nullptr, s);
-      if (e == cudaSuccess) e = launch_interp_velocity<T>(P, x, N, fg, V, s);
+      if (e == cudaSuccess) e = launch_interp_velocity<T>(P, xsrt, N, fg, V, s, nullptr);
       if (drift) {
-        if (e == cudaSuccess) e = launch_midpoint<T>(P, x, V, N, xs, s);
-        if (e == cudaSuccess) e = launch_interp_velocity<T>(P, xs, N, fg, V, s);
+        if (e == cudaSuccess) e = launch_midpoint<T>(P, xsrt, V, N, xs, s);
+        if (e == cudaSuccess) e = launch_interp_velocity<T>(P, xs, N, fg, V, s, nullptr);
       }
-      if (e == cudaSuccess) e = launch_dry_update<T>(P, x, species, F, V, N, step, s);
+      if (e == cudaSuccess) e = launch_dry_update<T>(P, x, W.sps, F, V, N, step, s, xsrt, W.perm);
     } else {
-      e = launch_dry_update<T>(P, x, species, F, nullptr, N, step, s);
+      e = launch_dry_update<T>(P, x, W.sps, F, nullptr, N, step, s, xsrt, W.perm);
     }
     if (e != cudaSuccess) return cuda_status(e, "discos_step");
   }
   cudaError_t e = cudaSuccess;
-  if (F_out && nsteps > 0) e = cudaMemcpyAsync(F_out, F, sizeof(T) * 3 * (size_t)N, cudaMemcpyDeviceToDevice, s);
+  if (F_out && nsteps > 0) e = launch_scatter3<T>(F, W.perm, N, reinterpret_cast<T*>(F_out), s);
   // the fault word travels to the host behind the steps; the next call reads it
   if (e == cudaSuccess && nsteps > 0)
     e = cudaMemcpyAsync(h->fault_host, W.fault, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
@@ -300,6 +477,7 @@ discos_status energy_impl(discos_handle* h, const Params& P, const T* x, const T
 }
 
 discos_status energy_args(discos_handle* h, const double* phi_b, Params* P) {
+  if (h->P.strip) return invalid("the energy is not defined with a metal strip");
   if (h->P.bc[0] == DISCOS_BC_NEUMANN && h->P.bc[1] == DISCOS_BC_NEUMANN)
     return invalid("the energy needs at least one Dirichlet wall (two Neumann walls fix no potential)");
   *P = h->P;
@@ -313,11 +491,21 @@ discos_status energy_args(discos_handle* h, const double* phi_b, Params* P) {
   return DISCOS_OK;
 }
 
+// The library launches on the current device; the handle's workspace lives on
+// the device that was current when it was created.
+discos_status check_device(discos_handle* h) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device)
+    return invalid("the current CUDA device is not the one the handle was created on");
+  return DISCOS_OK;
+}
+
 discos_status check_n(discos_handle* h, int N) {
   if (!h) return invalid("null handle");
   if (N < 0 || N > h->cfg.max_ions) return invalid("N outside [0, max_ions]");
-  return DISCOS_OK;
+  return check_device(h);
 }
+
 
 }  // namespace
 }  // namespace discos
@@ -372,7 +560,7 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   const discos_config& c = *cfg;
   if (!is_pow2(c.Nx) || c.Nx < 16 || c.Nx > 512) return invalid("Nx must be a power of two in [16, 512]");
   if (!is_pow2(c.Nz) || c.Nz < 16 || c.Nz > 512) return invalid("Nz must be a power of two in [16, 512]");
-  if (c.Ny < 8 || c.Ny > 512) return invalid("Ny must be in [8, 512]");
+  if (c.Ny < 8 || c.Ny > 256) return invalid("Ny must be in [8, 256]");
   for (int w = 0; w < 2; ++w)
     if (c.bc[w] != DISCOS_BC_DIRICHLET && c.bc[w] != DISCOS_BC_NEUMANN) return invalid("bad wall type");
   int wes = kernel_width(c.kernel_es, c.es_w[0]);
@@ -396,6 +584,21 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   if (k < 1) k = 1;
   if (c.Nx / k < 3 || c.Nz / k < 3) return invalid("cutoff too large for the box (need 3 list cells per periodic axis)");
   if (2.0 * c.psi > std::min(c.Nx, c.Nz)) return invalid("psi must be at most half the periodic box");
+  for (int w = 0; w < 2; ++w)
+    if (c.bc_hy[w] != DISCOS_HY_NOSLIP && c.bc_hy[w] != DISCOS_HY_SLIP) return invalid("bad bc_hy");
+  if (c.bc_hy[0] == DISCOS_HY_SLIP && c.bc_hy[1] == DISCOS_HY_SLIP)
+    return invalid("at most one slip wall (two leave uniform flow along the walls undamped)");
+  int strip_i0 = 0, strip_i1 = 0;
+  if (c.strip) {
+    if (c.bc[0] != DISCOS_BC_NEUMANN) return invalid("the metal strip sits in a dielectric (NEUMANN) bottom wall");
+    if (!std::isfinite(c.strip_x[0]) || !std::isfinite(c.strip_x[1]) || !std::isfinite(c.strip_phi))
+      return invalid("strip_x and strip_phi must be finite");
+    strip_i0 = std::max(0, (int)std::ceil(c.strip_x[0] - 0.5));
+    strip_i1 = std::min(c.Nx, (int)std::ceil(c.strip_x[1] - 0.5));
+    if (strip_i1 <= strip_i0) return invalid("the metal strip covers no cell column");
+    if (strip_i1 - strip_i0 > 128) return invalid("the metal strip is at most 128 cell columns wide");
+    if (c.max_refine > 0) return invalid("residual refinement is not available with a metal strip");
+  }
 
   discos_handle* h = new discos_handle();
   h->cfg = c;
@@ -483,8 +686,20 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   }
   P.k_cell = k;
   P.ncx = c.Nx / k; P.ncy = std::max(1, c.Ny / k); P.ncz = c.Nz / k;
+  if (c.strip) {
+    P.strip = 1;
+    P.strip_i0 = strip_i0;
+    P.strip_i1 = strip_i1;
+    P.strip_singular = c.bc[1] == DISCOS_BC_NEUMANN ? 1 : 0;
+    P.strip_phi = c.strip_phi;
+    P.strip_xc = 0.5 * (c.strip_x[0] + c.strip_x[1]);
+    P.f.strip_phi = (float)P.strip_phi;
+    P.f.strip_xc = (float)P.strip_xc;
+  }
   P.drift = c.drift;
   P.seed = c.seed;
+  P.slip[0] = c.bc_hy[0] == DISCOS_HY_SLIP ? 1 : 0;
+  P.slip[1] = c.bc_hy[1] == DISCOS_HY_SLIP ? 1 : 0;
 
   // workspace
   const size_t rs = h->mixed ? sizeof(float) : sizeof(double);
@@ -513,6 +728,7 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   W.xs = dalloc(h, rs * 3 * M, &ok);
   W.qs = dalloc(h, rs * M, &ok);
   W.sps = (int*)dalloc(h, sizeof(int) * M, &ok);
+  W.xq = dalloc(h, (h->mixed ? 16 : 32) * M, &ok);
   W.F = dalloc(h, rs * 3 * M, &ok);
   W.xstar = dalloc(h, rs * 3 * M, &ok);
   W.V = dalloc(h, rs * 3 * M, &ok);
@@ -520,10 +736,20 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   W.edata = (double*)dalloc(h, sizeof(double) * (3 * (size_t)c.Ny + 4), &ok);
   W.fault = (unsigned*)dalloc(h, sizeof(unsigned), &ok);
   W.diag = (double*)dalloc(h, 8 * sizeof(double), &ok);
+  W.nsum = (double*)dalloc(h, 4 * sizeof(double), &ok);
   if (h->mixed && c.max_refine > 0) {
     W.rref = dalloc(h, rs * G, &ok);
     W.rres = dalloc(h, rs * G, &ok);
     W.rnorm = (double*)dalloc(h, sizeof(double) * 2 * (DISCOS_MAX_REFINE + 1), &ok);
+    W.phi64 = (double*)dalloc(h, sizeof(double) * G, &ok);
+    if (c.wet) {
+      W.sref = dalloc(h, rs * Gf, &ok);
+      W.sres = dalloc(h, rs * Gf, &ok);
+      W.pres = dalloc(h, rs * G, &ok);
+      W.v64 = (double*)dalloc(h, sizeof(double) * Gf, &ok);
+      W.p64 = (double*)dalloc(h, sizeof(double) * G, &ok);
+      W.snorm = (double*)dalloc(h, sizeof(double) * 2 * (DISCOS_MAX_REFINE + 1), &ok);
+    }
   }
   if (h->mixed) {
     W.is_lo = (unsigned char*)dalloc(h, modes, &ok);
@@ -544,11 +770,28 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
     W.st_ci = (double*)dalloc(h, sizeof(double) * c.Ny * modes, &ok);
     W.st_mc = (double*)dalloc(h, sizeof(double) * 5 * modes, &ok);
   }
+  std::vector<double> strip_add0, strip_M;
+  if (c.strip) {
+    const int Ws = P.strip_i1 - P.strip_i0;
+    W.strip_g = dalloc(h, rs * G, &ok);
+    W.strip_add0 = dalloc(h, rs * c.Nx, &ok);
+    W.strip_r = (double*)dalloc(h, sizeof(double) * c.Nz * Ws, &ok);
+    W.strip_shat = (double*)dalloc(h, 2 * sizeof(double) * c.Nz * Ws, &ok);
+    W.strip_M = (double*)dalloc(h, sizeof(double) * c.Nz * (Ws + 1) * (Ws + 1), &ok);
+    W.strip_c = (double*)dalloc(h, sizeof(double), &ok);
+  }
   if (!ok) {
     free_workspace(h);
     delete h;
     set_error("device allocation failed");
     return DISCOS_ERR_OOM;
+  }
+  if (c.strip) {
+    setup_strip(h, strip_add0, strip_M);
+    if (h->mixed) upload_table<float>(W.strip_add0, strip_add0);
+    else upload_table<double>(W.strip_add0, strip_add0);
+    cudaMemcpy(W.strip_M, strip_M.data(), sizeof(double) * strip_M.size(), cudaMemcpyHostToDevice);
+    cudaMemset(W.strip_c, 0, sizeof(double));
   }
   // Thomas pivots of the Poisson wall-normal systems, one set per (kx, kz), [M][Ny]
   {
@@ -649,17 +892,11 @@ discos_status discos_spread(discos_handle* h, const void* x, const void* val, in
   discos_status st = check_n(h, N);
   if (st) return st;
   if (!grid || (N > 0 && (!x || !val))) return invalid("null pointer");
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e;
-  if (which == DISCOS_SPREAD_CHARGE) {
-    e = h->mixed ? launch_spread_charge<float>(h->P, (const float*)x, (const float*)val, N, (float*)grid, s)
-                 : launch_spread_charge<double>(h->P, (const double*)x, (const double*)val, N, (double*)grid, s);
-  } else if (which == DISCOS_SPREAD_FORCE) {
-    e = h->mixed ? launch_spread_force<float>(h->P, (const float*)x, (const float*)val, N, (float*)grid, 0, false, s)
-                 : launch_spread_force<double>(h->P, (const double*)x, (const double*)val, N, (double*)grid, 0, false, s);
-  } else {
+  if (which != DISCOS_SPREAD_CHARGE && which != DISCOS_SPREAD_FORCE)
     return invalid("which must be DISCOS_SPREAD_CHARGE or DISCOS_SPREAD_FORCE");
-  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = h->mixed ? spread_impl<float>(h, (const float*)x, (const float*)val, N, which, (float*)grid, s)
+                           : spread_impl<double>(h, (const double*)x, (const double*)val, N, which, (double*)grid, s);
   return cuda_status(e, "discos_spread");
 }
 
@@ -667,7 +904,13 @@ discos_status discos_solve_poisson(discos_handle* h, const void* rho, void* phi,
   ProbeScope probe_scope(h);
   if (!h) return invalid("null handle");
   if (!rho || !phi) return invalid("null pointer");
+  discos_status st = check_device(h);
+  if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  const size_t G = (size_t)h->P.Nx * h->P.Ny * h->P.Nz;
+  st = h->mixed ? check_neutral_sync<float>(h, (const float*)rho, G, s, "discos_solve_poisson")
+                : check_neutral_sync<double>(h, (const double*)rho, G, s, "discos_solve_poisson");
+  if (st) return st;
   cudaError_t e = h->mixed ? launch_poisson<float>(h->P, h->W, (const float*)rho, (float*)phi, s)
                            : launch_poisson<double>(h->P, h->W, (const double*)rho, (double*)phi, s);
   return cuda_status(e, "discos_solve_poisson");
@@ -679,6 +922,7 @@ discos_status discos_solve_stokes(discos_handle* h, const void* f, void* v, void
   if (!f || !v) return invalid("null pointer");
   if (!(h->P.eta > 0.0)) return invalid("eta must be positive");
   if (!h->cfg.wet) return invalid("the handle was created without the hydrodynamic stage (wet = 0)");
+  if (discos_status st = check_device(h)) return st;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = h->mixed ? launch_stokes<float>(h->P, h->W, (const float*)f, (float*)v, (float*)p, s)
                            : launch_stokes<double>(h->P, h->W, (const double*)f, (double*)v, (double*)p, s);
@@ -691,17 +935,11 @@ discos_status discos_interpolate(discos_handle* h, const void* x, int N, int whi
   discos_status st = check_n(h, N);
   if (st) return st;
   if (!grid || (N > 0 && (!x || !out))) return invalid("null pointer");
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e;
-  if (which == DISCOS_INTERP_EFIELD) {
-    e = h->mixed ? launch_interp_efield<float>(h->P, (const float*)x, nullptr, N, (const float*)grid, (float*)out, false, s)
-                 : launch_interp_efield<double>(h->P, (const double*)x, nullptr, N, (const double*)grid, (double*)out, false, s);
-  } else if (which == DISCOS_INTERP_VELOCITY) {
-    e = h->mixed ? launch_interp_velocity<float>(h->P, (const float*)x, N, (const float*)grid, (float*)out, s)
-                 : launch_interp_velocity<double>(h->P, (const double*)x, N, (const double*)grid, (double*)out, s);
-  } else {
+  if (which != DISCOS_INTERP_EFIELD && which != DISCOS_INTERP_VELOCITY)
     return invalid("which must be DISCOS_INTERP_EFIELD or DISCOS_INTERP_VELOCITY");
-  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = h->mixed ? interp_impl<float>(h, (const float*)x, N, which, (const float*)grid, (float*)out, s)
+                           : interp_impl<double>(h, (const double*)x, N, which, (const double*)grid, (double*)out, s);
   return cuda_status(e, "discos_interpolate");
 }
 
@@ -742,6 +980,9 @@ discos_status discos_forces(discos_handle* h, const void* x, const void* q, cons
   if (st) return st;
   if (N > 0 && (!x || !q || !F)) return invalid("null pointer");
   cudaStream_t s = (cudaStream_t)stream;
+  st = h->mixed ? check_neutral_sync<float>(h, (const float*)q, (size_t)N, s, "discos_forces")
+                : check_neutral_sync<double>(h, (const double*)q, (size_t)N, s, "discos_forces");
+  if (st) return st;
   return h->mixed ? forces_impl<float>(h, (const float*)x, (const float*)q, species, N, (float*)F, nbr_count, s)
                   : forces_impl<double>(h, (const double*)x, (const double*)q, species, N, (double*)F, nbr_count, s);
 }
@@ -754,6 +995,10 @@ discos_status discos_step(discos_handle* h, void* x, const void* q, const int* s
   if (nsteps < 0) return invalid("nsteps must be >= 0");
   if (N > 0 && (!x || !q)) return invalid("null pointer");
   if (cudaEventQuery(h->ev_fault) == cudaSuccess && *h->fault_host) {
+    if (*h->fault_host & 4u) {
+      set_error("a previous step found the channel between two Neumann walls not neutral (fault word bit 2)");
+      return DISCOS_ERR_NOT_NEUTRAL;
+    }
     set_error(std::string("a previous step flagged the device fault word (") + std::to_string(*h->fault_host) +
               "): bit 0 non-finite position, bit 1 ion outside the channel; see discos_fault");
     return DISCOS_ERR_DEVICE_FAULT;
@@ -794,19 +1039,27 @@ discos_status discos_energy_backward(discos_handle* h, const void* x, const void
                                         (double*)dq, dphi_b, s);
 }
 
-discos_status discos_refine_history(discos_handle* h, double* rel, int* n, void* stream) {
+static discos_status refine_history(discos_handle* h, const double* norms, double* rel, int* n, void* stream) {
   if (!h || !rel || !n) return invalid("null pointer");
   *n = 0;
-  if (!h->W.rnorm) return DISCOS_OK;
+  if (!norms) return DISCOS_OK;
   const int m = h->P.max_refine + 1;
   double buf[2 * (DISCOS_MAX_REFINE + 1)];
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(buf, h->W.rnorm, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaMemcpyAsync(buf, norms, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(e, "discos_refine_history");
   for (int i = 0; i < m; ++i) rel[i] = buf[2 * i + 1] > 0.0 ? std::sqrt(buf[2 * i] / buf[2 * i + 1]) : 0.0;
   *n = m;
   return DISCOS_OK;
+}
+
+discos_status discos_refine_history(discos_handle* h, double* rel, int* n, void* stream) {
+  return refine_history(h, h ? h->W.rnorm : nullptr, rel, n, stream);
+}
+
+discos_status discos_refine_history_stokes(discos_handle* h, double* rel, int* n, void* stream) {
+  return refine_history(h, h ? h->W.snorm : nullptr, rel, n, stream);
 }
 
 discos_status discos_fault(discos_handle* h, int sync, int clear, unsigned* word, void* stream) {

@@ -23,6 +23,7 @@ struct PhysF {
   float E_ext[3], slope[2], phi_b[2];
   float dt, kT, inv_kT, lB, psi, tab_scale;
   float eta, inv_eta, inv_nxnz;
+  float strip_phi, strip_xc;
 };
 
 // Everything a kernel needs to know about the run, passed by value.
@@ -50,15 +51,34 @@ struct Params {
   uint64_t seed;
   int max_refine;              // residual refinement sweeps of the mixed Poisson solve
   int fx_pp, fx_threads, fz_tk;  // transform launch shapes (k_fft.cu; discos_tune_transforms)
-  unsigned* fault;             // device fault word: bit 0 non-finite position, bit 1 escaped ion
+  // metal strip in the bottom wall (k_strip.cu): Dirichlet on the cell columns [strip_i0, strip_i1) with
+  // phi_m(x) = strip_phi + E_ext[0] (x - strip_xc); strip_singular: the all-dielectric base operator is
+  // singular (top wall Neumann); strip_walls: the sum of the base solve's wall terms over the grid
+  int strip, strip_i0, strip_i1, strip_singular;
+  int slip[2];                 // hydrodynamic slip walls (bottom, top): tangential images and ghosts +1, else -1
+  double strip_phi, strip_xc, strip_walls;
+  unsigned* fault;             // device fault word: bit 0 non-finite position, bit 1 escaped ion,
+                               // bit 2 a non-neutral channel between two Neumann walls
   double inv_D_dry[DISCOS_MAX_SPECIES], inv_kT;
   double inv_eta, inv_nxnz;    // 1 / eta (0 without a fluid), 1 / (Nx Nz): the transforms' normalisation
   PhysF f;
 };
 
+// Whether the bottom-wall cell column ix (0 <= ix < Nx) lies on the metal strip.
+__host__ __device__ __forceinline__ bool on_strip(const Params& P, int ix) {
+  return P.strip && ix >= P.strip_i0 && ix < P.strip_i1;
+}
+
 // The physics constants in the arithmetic type of the caller.
 __host__ __device__ __forceinline__ const Params& phys(const Params& P, double) { return P; }
 __host__ __device__ __forceinline__ const PhysF& phys(const Params& P, float) { return P.f; }
+
+// The metal strip's potential phi_m at cell column ix (centre ix + 1/2).
+template <typename T>
+__host__ __device__ __forceinline__ T strip_phi_m(const Params& P, int ix, T) {
+  const auto& Q = phys(P, T());
+  return T(Q.strip_phi) + T(Q.E_ext[0]) * (T(ix) + T(0.5) - T(Q.strip_xc));
+}
 
 // Kernel families that can be timed live (discos_probe).
 enum ProbeFamily {
@@ -99,6 +119,7 @@ struct Workspace {
   void* xs = nullptr;          // sorted positions [3][max_ions] real
   void* qs = nullptr;          // sorted charges [max_ions] real
   int* sps = nullptr;          // sorted species [max_ions]
+  void* xq = nullptr;          // sorted (x, y, z, q) packed [max_ions] float4 / 32-byte double4
   void* F = nullptr;           // forces [3][max_ions] real
   void* xstar = nullptr;       // midpoint positions [3][max_ions] real
   void* V = nullptr;           // interpolated velocities [3][max_ions] real
@@ -127,8 +148,24 @@ struct Workspace {
   void* rref = nullptr;         // refinement (mixed, max_refine > 0): rho kept for the residual
   void* rres = nullptr;         //   residual, then correction
   double* rnorm = nullptr;      //   (|r|^2, |b|^2) before each sweep and after the last
+  double* phi64 = nullptr;      //   the refined potential, accumulated in double
+  // refinement of the Stokes solve (mixed, max_refine > 0, wet)
+  void* sref = nullptr;         //   forcing kept for the residual (f and v may alias)
+  void* sres = nullptr;         //   residual, then velocity correction
+  void* pres = nullptr;         //   pressure of each solve
+  double* v64 = nullptr;        //   velocity and pressure accumulated in double
+  double* p64 = nullptr;
+  double* snorm = nullptr;      //   (|r|^2, |f|^2) before each sweep and after the last
+  // metal strip (k_strip.cu)
+  void* strip_g = nullptr;      //   [Nz][Ny][Nx] real: the strip sources, then their solve
+  void* strip_add0 = nullptr;   //   [Nx] real: bottom-row terms of the base solve (2 phi_m on the strip, -g off it)
+  double* strip_r = nullptr;    //   [Nz][Ws] base solution on the strip cells
+  double* strip_shat = nullptr; //   [Nz][Ws] complex strip sources per z mode
+  double* strip_M = nullptr;    //   [Nz][Ws + 1][Ws + 1] inverse capacitance matrices
+  double* strip_c = nullptr;    //   the constant of the bordered kz = 0 system
   unsigned* fault = nullptr;    // device fault word (Params::fault)
   double* diag = nullptr;       // scratch of discos_diagnostics
+  double* nsum = nullptr;       // neutrality sums (sum q, sum |q|) of an all-Neumann channel
   int n_cells = 0;
 };
 
@@ -218,38 +255,68 @@ double es_normalisation(int w, double beta);
 
 // Launch wrappers (one per kernel family); T = float or double.
 template <typename T> cudaError_t launch_cell_list(const Params& P, Workspace& W, const T* x, int N, cudaStream_t s);
-template <typename T> cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N, T* rho, cudaStream_t s);
-template <typename T> cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, T* f,
-                                                      int64_t step, bool rfd, cudaStream_t s,
-                                                      bool accumulate = false);
+template <typename T> cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N, T* rho, cudaStream_t s,
+                                                       bool decorrelate = false);
 template <typename T> cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_t s,
                                                       bool overwrite = false);
 template <typename T> cudaError_t launch_poisson(const Params& P, Workspace& W, const T* rho, T* phi, cudaStream_t s);
+template <typename T> cudaError_t launch_poisson_strip(const Params& P, Workspace& W, const T* rho, T* phi, T fourpi_lB,
+                                                       T add1, cudaStream_t s);
 template <typename T> cudaError_t launch_stokes(const Params& P, Workspace& W, const T* f, T* v, T* p, cudaStream_t s);
-template <typename T> cudaError_t launch_interp_efield(const Params& P, const T* x, const T* q, int N, const T* phi,
-                                                       T* out, bool as_force, cudaStream_t s,
-                                                       const T* F_add = nullptr);
-template <typename T> cudaError_t launch_interp_velocity(const Params& P, const T* x, int N, const T* v, T* out,
-                                                         cudaStream_t s);
 template <typename T> cudaError_t launch_near_field(const Params& P, Workspace& W, const T* x, const T* q,
                                                     const int* species, int N, T* F, int* nbr, cudaStream_t s,
                                                     bool accumulate = true);
+// Cell list of x, then sorted copies of the ions (W.xs, W.qs, W.sps, W.xq;
+// W.perm maps sorted index -> caller's index).
+template <typename T> cudaError_t launch_sort_ions(const Params& P, Workspace& W, const T* x, const T* q,
+                                                   const int* species, int N, cudaStream_t s);
+// Near field of the sorted ions; F written at f_index[s] and nbr at
+// n_index[s] (NULL: at s, the sorted order).
+template <typename T> cudaError_t launch_near_field_sorted(const Params& P, Workspace& W, int N, T* F, int* nbr,
+                                                           const int* f_index, const int* n_index, cudaStream_t s,
+                                                           bool accumulate);
 template <typename T> cudaError_t launch_dry_update(const Params& P, T* x, const int* species, const T* F,
-                                                   const T* V, int N, int64_t step, cudaStream_t s);
+                                                   const T* V, int N, int64_t step, cudaStream_t s,
+                                                   const T* xin = nullptr, const int* index = nullptr);
+template <typename T> cudaError_t launch_scatter3(const T* src, const int* index, int N, T* dst, cudaStream_t s);
+
+// Spreading and interpolation (k_spread.cu, k_interp.cu).  decorrelate:
+// visit the ions in a scattered order (atomics of ions in cell order collide);
+// noise_index: the caller's index of each ion (the RFD noise key); out_index:
+// where each ion's result goes.
+template <typename T> cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, T* f,
+                                                      int64_t step, bool rfd, cudaStream_t s, bool accumulate,
+                                                      const int* noise_index, bool decorrelate);
+template <typename T> cudaError_t launch_interp_efield(const Params& P, const T* x, const T* q, int N, const T* phi,
+                                                       T* out, bool as_force, cudaStream_t s, const T* F_add,
+                                                       const int* out_index);
+template <typename T> cudaError_t launch_interp_velocity(const Params& P, const T* x, int N, const T* v, T* out,
+                                                         cudaStream_t s, const int* out_index);
 template <typename T> cudaError_t launch_midpoint(const Params& P, const T* x, const T* V, int N, T* xstar,
                                                   cudaStream_t s);
 template <typename T> cudaError_t launch_fill_zero(T* p, size_t n, cudaStream_t s);
+template <typename T> cudaError_t launch_fill_value(T* p, size_t n, T value, cudaStream_t s);
 template <typename T> cudaError_t launch_energy_sums(const Params& P, const T* rho, const T* phi, const double* lift,
                                                       double* sums, cudaStream_t s);
 template <typename T> cudaError_t launch_energy_grad(const Params& P, const T* x, const T* q, int N, const T* phi,
                                                       const double* dU, T* dx, T* dq, cudaStream_t s);
 cudaError_t launch_lift(const Params& P, double* lift, cudaStream_t s);
 cudaError_t launch_scale2(const double* sums, const double* dU, double* out, cudaStream_t s);
-template <typename T> cudaError_t launch_poisson_residual(const Params& P, const T* rho, const T* phi, T* res,
-                                                           double* norms, cudaStream_t s);
+template <typename T, typename TP> cudaError_t launch_poisson_residual(const Params& P, const T* rho, const TP* phi,
+                                                                        T* res, double* norms, cudaStream_t s);
+template <typename T> cudaError_t launch_stokes_residual(const Params& P, const T* f, const double* v, const double* p,
+                                                          T* res, double* norms, cudaStream_t s);
+template <typename T> cudaError_t launch_accumulate(double* acc, const T* d, size_t n, cudaStream_t s);
+template <typename TD, typename TS> cudaError_t launch_convert(TD* dst, const TS* src, size_t n, cudaStream_t s);
 template <typename T> cudaError_t launch_diagnostics(const Params& P, const T* x, const T* q, const T* F, int N,
                                                       const T* rho, double* out, cudaStream_t s);
 template <typename T> cudaError_t launch_add_inplace(T* a, const T* b, size_t n, cudaStream_t s);
+// out[0..1] = (sum v, sum |v|) in double.
+template <typename T> cudaError_t launch_charge_sums(const T* v, size_t n, double* out, cudaStream_t s);
+// Sets bit 2 of *fault when the sums of launch_charge_sums plus the surface
+// charge are not neutral to tol.
+cudaError_t launch_neutral_flag(const double* sums, double surface, double surface_abs, double tol, unsigned* fault,
+                                cudaStream_t s);
 template <typename T> cudaError_t launch_poisson_y(const Params& P, Workspace& W, cplx<T>* S, cudaStream_t s);
 template <typename T> cudaError_t launch_stokes_y(const Params& P, Workspace& W, cplx<T>* S, cplx<T>* Sp,
                                                   cudaStream_t s);

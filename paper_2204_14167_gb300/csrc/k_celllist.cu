@@ -4,7 +4,7 @@
 // per-cell sort by ion index that makes the order deterministic, and a gather
 // of the ions into cell order.
 #include <mutex>
-#include "internal.h"
+#include "physics.cuh"
 
 namespace discos {
 
@@ -12,20 +12,15 @@ namespace {
 
 constexpr int kScanTile = 1024;
 
-template <typename T>
-__device__ __forceinline__ int cell_coord(T v, int k, int nc) {
-  int c = (int)floor(v);
-  c = c < 0 ? 0 : c / k;
-  return c < nc ? c : nc - 1;
-}
-
+// x and z are periodic: a position outside [0, L) is binned where its
+// periodic image inside the box lies (the sorted copies hold that image).
 template <typename T>
 __global__ void k_bin(const T* __restrict__ x, int N, Params P, int* __restrict__ cell_of,
                       int* __restrict__ counts) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int cid = -1;
   if (i < N) {
-    const T px = x[i], py = x[N + i], pz = x[2 * N + i];
+    const T px = wrap_coord(x[i], P.Nx), py = x[N + i], pz = wrap_coord(x[2 * N + i], P.Nz);
     int cx = cell_coord(px, P.k_cell, P.ncx);
     int cy = cell_coord(py, P.k_cell, P.ncy);
     int cz = cell_coord(pz, P.k_cell, P.ncz);
@@ -203,7 +198,8 @@ namespace {
 constexpr int kNoAllocMaxIons = 1 << 20;      // ions per call
 constexpr int kNoAllocMaxCells = 1 << 18;     // list cells per call
 constexpr int kNoAllocMaxTiles = kNoAllocMaxCells / kScanTile + 1;
-constexpr size_t kNoAllocInts = (size_t)kNoAllocMaxIons + 2 * (size_t)kNoAllocMaxCells + kNoAllocMaxTiles;
+// cell ids, counts, fill counters, scan tile sums, and one fault word
+constexpr size_t kNoAllocInts = (size_t)kNoAllocMaxIons + 2 * (size_t)kNoAllocMaxCells + kNoAllocMaxTiles + 1;
 
 static __device__ __align__(256) int g_noalloc_scratch[kNoAllocInts];
 
@@ -234,6 +230,9 @@ extern "C" discos_status discos_cell_list_noalloc(const discos_config* cfg, cons
   int k = (int)ceil(rcmax - 1e-12);
   if (k < 1) k = 1;
   Params P{};
+  P.Nx = c.Nx;
+  P.Ny = c.Ny;
+  P.Nz = c.Nz;
   P.k_cell = k;
   P.ncx = c.Nx / k;
   P.ncy = c.Ny / k > 1 ? c.Ny / k : 1;
@@ -275,11 +274,17 @@ extern "C" discos_status discos_cell_list_noalloc(const discos_config* cfg, cons
   int* counts = cell_of + kNoAllocMaxIons;
   int* fill = counts + kNoAllocMaxCells;
   int* tile_sums = fill + kNoAllocMaxCells;
+  // positions that are not finite or leave the channel in y set this word in
+  // the binning; the per-cell sort then stands down (such ions can all share
+  // one cell, which would make it quadratic)
+  unsigned* fault = reinterpret_cast<unsigned*>(tile_sums + kNoAllocMaxTiles);
+  P.fault = fault;
   const int n = (int)n_cells;
   cudaStream_t s = (cudaStream_t)stream;
   // the array keeps the previous call's contents: clear what must start at zero
   e = cudaMemsetAsync(counts, 0, sizeof(int) * n, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(fill, 0, sizeof(int) * n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fault, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return cuda_status(e, "discos_cell_list_noalloc");
   const int bs = 256;
   const int nb = (N + bs - 1) / bs;
@@ -297,7 +302,7 @@ extern "C" discos_status discos_cell_list_noalloc(const discos_config* cfg, cons
     k_scatter<<<nb, bs, 0, s>>>(cell_of, N, cell_start, fill, perm);
     count_launches(1);
   }
-  k_sort_cells<<<(n + 255) / 256, 256, 0, s>>>(cell_start, n, perm);
+  k_sort_cells<<<(n + 255) / 256, 256, 0, s>>>(cell_start, n, perm, fault);
   count_launches(1);
   return cuda_status(cudaGetLastError(), "discos_cell_list_noalloc");
 }

@@ -2,10 +2,10 @@
 // with the wall conditions of Eqs. esbc1 / esbc3.
 //
 // x: real rows -> half spectra (Nx/2 + 1 modes, row pitch Px), two real rows
-//    packed into one complex radix-2 transform held in shared memory.
-// z: complex transforms down the columns of the half spectrum, a tile of 16
-//    consecutive x-modes per block so that every load is a 16-element run.
-// Both use a radix-2 Stockham transform (natural order, no bit reversal).
+//    packed into one complex transform per warp, held in registers (a
+//    shared-memory Stockham transform serves Nx = 16).
+// z: complex transforms down the columns of the half spectrum, in place, two
+//    x-mode columns per warp held in registers.
 // y: the tridiagonal wall-normal system of every (kx, kz) mode, solved by
 //    warp-parallel scans over pre-factored pivots (k_ysolve.cu).
 #include <atomic>
@@ -88,7 +88,8 @@ __device__ cplx<T>* fft_stockham(cplx<T>* in, cplx<T>* out, int N, int logN, int
 // Input value = scale * in + (row's y == 0 ? add0) + (row's y == Nyr-1 ? add1).
 template <typename T>
 __global__ void k_rfft_x(const T* __restrict__ in, int R, int N, int logN, int Px, cplx<T>* __restrict__ out,
-                         T scale, int Nyr, T add0, T add1, const cplx<T>* __restrict__ tw, int pairs_per_block) {
+                         T scale, int Nyr, T add0, T add1, const cplx<T>* __restrict__ tw, int pairs_per_block,
+                         const T* __restrict__ add0x) {
   extern __shared__ unsigned char smem_raw[];
   const int PP = pairs_per_block;
   cplx<T>* bufa = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -106,8 +107,8 @@ __global__ void k_rfft_x(const T* __restrict__ in, int R, int N, int logN, int P
     const int v = idx >> logN, n = idx & (N - 1);
     const int ra = 2 * (blockIdx.x * PP + v), rb = ra + 1;
     T a = T(0), b = T(0);
-    if (ra < R) a = scale * in[(size_t)ra * N + n] + rowadd[2 * v];
-    if (rb < R) b = scale * in[(size_t)rb * N + n] + rowadd[2 * v + 1];
+    if (ra < R) a = scale * in[(size_t)ra * N + n] + rowadd[2 * v] + ((add0x && ra % Nyr == 0) ? add0x[n] : T(0));
+    if (rb < R) b = scale * in[(size_t)rb * N + n] + rowadd[2 * v + 1] + ((add0x && rb % Nyr == 0) ? add0x[n] : T(0));
     bufa[idx] = cplx<T>{a, b};
   }
   __syncthreads();
@@ -164,20 +165,165 @@ __global__ void k_irfft_x(const cplx<T>* __restrict__ in, int R, int N, int logN
   }
 }
 
-// Complex transform along z of the half spectra [Nz][Nyr][Px] (field f =
-// blockIdx.z at offset f * field_stride), TK consecutive x-modes per block.
-// Shared layout [column][Nz + 1] (padded so that the column-interleaved
-// loads and stores do not collide in a bank).
-// mac != 0: the three MAC fields u | v | w stored back to back with Ny, Ny+1
-// and Ny rows per z-plane (Nyr = Ny is passed; grid.y = Ny + 1).
+// ------------------------------------------------------------------------
+// Register-resident transforms (the default for Nx >= 32 and every Nz).
+//
+// A length N = P G transform held by a group of G lanes, P values per lane:
+// lane r holds x[r + G p], p < P.  Four steps: a P-point DFT over each
+// lane's registers (register p then holds k2 = bitrev(p)), the twiddles
+// W_N^(r k2), then a G-point DFT across the lanes (radix-2 stages on
+// __shfl_xor, decimation in frequency), after which lane r, register p holds
+// X[k2 + P bitrev(r)].  Only the real-pair split of the x
+// transform and the reordering of its inverse go through shared memory.
+
+// exp(-+2 pi i m / N) for 0 <= m < N from the half table tw[m], m < N/2.
 template <typename T>
-__global__ void k_fft_z(cplx<T>* __restrict__ data, int Nz, int logNz, int Nyr, int Px, int Nxh, int inverse,
-                        const cplx<T>* __restrict__ tw, size_t field_stride, int mac, int TK) {
+__device__ __forceinline__ cplx<T> twid(const cplx<T>* __restrict__ tw, int m, int N, bool inverse) {
+  const int h = N >> 1;
+  cplx<T> w = tw[m & (h - 1)];
+  if (m & h) { w.re = -w.re; w.im = -w.im; }
+  if (inverse) w.im = -w.im;
+  return w;
+}
+
+template <int P>
+__host__ __device__ constexpr int brev_c(int i) {
+  int r = 0;
+  for (int b = 1; b < P; b <<= 1) { r = (r << 1) | (i & 1); i >>= 1; }
+  return r;
+}
+
+// P-point DFT of the registers, radix-2 decimation in frequency: natural
+// order in, register p holds output brev_c<P>(p) (every register index is a
+// compile-time constant, so the values stay in registers).
+template <typename T, int P>
+__device__ __forceinline__ void reg_dft(cplx<T> (&v)[P], const cplx<T>* __restrict__ tw, int N, bool inverse) {
+#pragma unroll
+  for (int half = P / 2; half >= 1; half >>= 1) {
+#pragma unroll
+    for (int i = 0; i < P; i += 2 * half) {
+#pragma unroll
+      for (int j = 0; j < half; ++j) {
+        const cplx<T> a = v[i + j], b = v[i + j + half];
+        v[i + j] = cadd(a, b);
+        const cplx<T> d = csub(a, b);
+        v[i + j + half] = j == 0 ? d : cmul(d, twid(tw, j * (N / (2 * half)), N, inverse));
+      }
+    }
+  }
+}
+
+// G-point DFT across the lanes r = 0..G-1 of a group (G = 16 or 32), one per
+// register: after it lane r holds output bitrev(r).
+template <typename T, int P>
+__device__ __forceinline__ void lane_dft(cplx<T> (&v)[P], int r, int G, const cplx<T>* __restrict__ tw, int N,
+                                         bool inverse) {
+  for (int s = G >> 1; s >= 1; s >>= 1) {
+    const bool hi = (r & s) != 0;
+    const cplx<T> w = twid(tw, (r & (s - 1)) * (N / (2 * s)), N, inverse);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const cplx<T> u{__shfl_xor_sync(0xffffffffu, v[p].re, s), __shfl_xor_sync(0xffffffffu, v[p].im, s)};
+      v[p] = hi ? cmul(csub(u, v[p]), w) : cadd(v[p], u);
+    }
+  }
+}
+
+// Forward real transform of two rows per warp (packed as one complex
+// transform of length N = 32 P), half spectra out.  Input value = scale * in
+// + the row's wall term (y == 0: add0, y == Nyr - 1: add1).
+template <typename T, int P>
+__global__ void k_rfft_x_w(const T* __restrict__ in, int R, int Px, cplx<T>* __restrict__ out, T scale, int Nyr,
+                           T add0, T add1, const cplx<T>* __restrict__ tw, const T* __restrict__ add0x) {
+  constexpr int N = 32 * P;
   extern __shared__ unsigned char smem_raw[];
-  const int vs = Nz + 1;
-  cplx<T>* bufa = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* bufb = bufa + (size_t)TK * vs;
-  cplx<T>* stw = bufb + (size_t)TK * vs;                       // twiddles, staged once per block
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  cplx<T>* sz = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)wib * 32 * (P + 1);
+  const int ra = 2 * (blockIdx.x * (blockDim.x >> 5) + wib), rb = ra + 1;
+  if (ra >= R) return;                       // whole warps
+  const bool hasb = rb < R;
+  const int ya = ra % Nyr, yb = rb % Nyr;
+  const T adda = (ya == 0 ? add0 : T(0)) + (ya == Nyr - 1 ? add1 : T(0));
+  const T addb = (yb == 0 ? add0 : T(0)) + (yb == Nyr - 1 ? add1 : T(0));
+  const T* pa = in + (size_t)ra * N;
+  const T* pb = in + (size_t)rb * N;
+  // a bottom row may carry a term per column (the metal strip's wall data)
+  const bool xa = add0x && ya == 0, xb = add0x && yb == 0;
+  cplx<T> v[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int n = lane + 32 * p;
+    v[p] = cplx<T>{scale * pa[n] + adda + (xa ? add0x[n] : T(0)),
+                   hasb ? scale * pb[n] + addb + (xb ? add0x[n] : T(0)) : T(0)};
+  }
+  reg_dft<T, P>(v, tw, N, false);
+#pragma unroll
+  for (int p = 1; p < P; ++p) v[p] = cmul(v[p], twid(tw, lane * brev_c<P>(p), N, false));
+  lane_dft<T, P>(v, lane, 32, tw, N, false);
+  const int k1 = (int)(__brev((unsigned)lane) >> 27);
+#pragma unroll
+  for (int p = 0; p < P; ++p) sz[k1 * (P + 1) + brev_c<P>(p)] = v[p];
+  __syncwarp();
+  // A = (Z_k + conj Z_{N-k}) / 2,  B = (Z_k - conj Z_{N-k}) / (2i)
+  for (int k = lane; k <= N / 2; k += 32) {
+    const int kn = (N - k) & (N - 1);
+    const cplx<T> Zk = sz[(k / P) * (P + 1) + (k % P)];
+    const cplx<T> Zn = sz[(kn / P) * (P + 1) + (kn % P)];
+    out[(size_t)ra * Px + k] = cplx<T>{T(0.5) * (Zk.re + Zn.re), T(0.5) * (Zk.im - Zn.im)};
+    if (hasb) out[(size_t)rb * Px + k] = cplx<T>{T(0.5) * (Zk.im + Zn.im), T(-0.5) * (Zk.re - Zn.re)};
+  }
+}
+
+// Inverse of k_rfft_x_w (unnormalised): half spectra -> real rows times scale.
+template <typename T, int P>
+__global__ void k_irfft_x_w(const cplx<T>* __restrict__ in, int R, int Px, T* __restrict__ out, T scale,
+                            const cplx<T>* __restrict__ tw) {
+  constexpr int N = 32 * P;
+  extern __shared__ unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  cplx<T>* sz = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)wib * 32 * (P + 1);
+  const int ra = 2 * (blockIdx.x * (blockDim.x >> 5) + wib), rb = ra + 1;
+  if (ra >= R) return;
+  const bool hasb = rb < R;
+  cplx<T> v[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int k = lane + 32 * p;
+    const int kk = k <= N / 2 ? k : N - k;
+    cplx<T> A = in[(size_t)ra * Px + kk];
+    cplx<T> B = hasb ? in[(size_t)rb * Px + kk] : cplx<T>{T(0), T(0)};
+    if (k > N / 2) { A.im = -A.im; B.im = -B.im; }
+    v[p] = cplx<T>{A.re - B.im, A.im + B.re};      // Z = A + i B
+  }
+  reg_dft<T, P>(v, tw, N, true);
+#pragma unroll
+  for (int p = 1; p < P; ++p) v[p] = cmul(v[p], twid(tw, lane * brev_c<P>(p), N, true));
+  lane_dft<T, P>(v, lane, 32, tw, N, true);
+  const int k1 = (int)(__brev((unsigned)lane) >> 27);
+#pragma unroll
+  for (int p = 0; p < P; ++p) sz[k1 * (P + 1) + brev_c<P>(p)] = v[p];
+  __syncwarp();
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int n = lane + 32 * p;
+    const cplx<T> z = sz[(n / P) * (P + 1) + (n % P)];
+    out[(size_t)ra * N + n] = scale * z.re;
+    if (hasb) out[(size_t)rb * N + n] = scale * z.im;
+  }
+}
+
+// Complex transform along z, in place: 32 / G x-mode columns per warp, G
+// lanes per column (G = 8 for float: 4 columns x 8 bytes fill a 32-byte
+// sector per z row; G = 16 for double), M = Nz / G values per lane.
+// blockIdx.y = y row, blockIdx.z = field (mac: the three MAC spectra
+// u | v | w with Ny, Ny + 1, Ny rows).
+template <typename T, int G, int M>
+__global__ void k_fft_z_w(cplx<T>* __restrict__ data, int Nyr, int Px, int Nxh, int inverse,
+                          const cplx<T>* __restrict__ tw, size_t field_stride, int mac) {
+  constexpr int Nz = G * M;
+  constexpr int LOGG = G == 8 ? 3 : (G == 16 ? 4 : 5);
+  const int lane = threadIdx.x & 31, r = lane & (G - 1);
+  const int kx = (32 / G) * (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) + lane / G;
   cplx<T>* base = data + blockIdx.z * field_stride;
   if (mac) {
     const int Ny = Nyr;
@@ -186,24 +332,22 @@ __global__ void k_fft_z(cplx<T>* __restrict__ data, int Nz, int logNz, int Nyr, 
     else { base = data; }
   }
   const int y = blockIdx.y;
-  if (y >= Nyr) return;
-  for (int t = threadIdx.x; t < Nz / 2; t += blockDim.x) stw[t] = tw[t];
-  const int kx0 = blockIdx.x * TK;
-  const int logTK = 31 - __clz(TK);
-  for (int idx = threadIdx.x; idx < TK * Nz; idx += blockDim.x) {
-    const int z = idx >> logTK, c = idx & (TK - 1);
-    int kx = kx0 + c;
-    cplx<T> v{T(0), T(0)};
-    if (kx < Nxh) v = base[((size_t)z * Nyr + y) * Px + kx];
-    bufa[c * vs + z] = v;
-  }
-  __syncthreads();
-  const int nv = Nxh - kx0 < TK ? Nxh - kx0 : TK;   // the last tile holds fewer columns
-  cplx<T>* r = fft_stockham(bufa, bufb, Nz, logNz, nv, vs, stw, inverse != 0);
-  for (int idx = threadIdx.x; idx < TK * Nz; idx += blockDim.x) {
-    const int z = idx >> logTK, c = idx & (TK - 1);
-    int kx = kx0 + c;
-    if (kx < Nxh) base[((size_t)z * Nyr + y) * Px + kx] = r[c * vs + z];
+  if (y >= Nyr) return;                      // whole blocks
+  const bool ok = kx < Nxh;
+  cplx<T>* col = base + (size_t)y * Px + kx;
+  const size_t zs = (size_t)Nyr * Px;
+  cplx<T> v[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) v[m] = ok ? col[(size_t)(r + G * m) * zs] : cplx<T>{T(0), T(0)};
+  const bool inv = inverse != 0;
+  reg_dft<T, M>(v, tw, Nz, inv);
+#pragma unroll
+  for (int p = 1; p < M; ++p) v[p] = cmul(v[p], twid(tw, r * brev_c<M>(p), Nz, inv));
+  lane_dft<T, M>(v, r, G, tw, Nz, inv);
+  const int k1 = (int)(__brev((unsigned)r) >> (32 - LOGG));
+  if (ok) {
+#pragma unroll
+    for (int p = 0; p < M; ++p) col[(size_t)(brev_c<M>(p) + M * k1) * zs] = v[p];
   }
 }
 
@@ -232,29 +376,45 @@ int default_tile_z(int Nz, size_t elem) {
   return tk > 8 ? 8 : tk;
 }
 
+
+// Register-resident x transforms for Nx >= 32: fx_pp row pairs (warps) per
+// block, within 48 KB of shared memory.
 template <typename T>
-void ensure_fft_z_attr() {
-  // the attribute belongs to the current device: set it once per device
-  static std::atomic<unsigned long long> done{0};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
-  const unsigned long long bit = 1ull << dev;
-  if (done.load() & bit) return;
-  if (cudaFuncSetAttribute(k_fft_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) == cudaSuccess)
-    done.fetch_or(bit);
+int x_warps_per_block(const Params& P) {
+  const int Pn = P.Nx / 32;
+  const size_t per_warp = 32 * (size_t)(Pn + 1) * sizeof(cplx<T>);
+  int w = P.fx_pp < 1 ? 1 : (P.fx_pp > 16 ? 16 : P.fx_pp);
+  while (w > 1 && w * per_warp > 48 * 1024) --w;
+  return w;
 }
+
+#define DISCOS_X_DISPATCH(KERNEL, ...)                                                        \
+  switch (P.Nx) {                                                                             \
+    case 32: KERNEL<T, 1><<<nb, 32 * wpb, sm, s>>>(__VA_ARGS__); break;                       \
+    case 64: KERNEL<T, 2><<<nb, 32 * wpb, sm, s>>>(__VA_ARGS__); break;                       \
+    case 128: KERNEL<T, 4><<<nb, 32 * wpb, sm, s>>>(__VA_ARGS__); break;                      \
+    case 256: KERNEL<T, 8><<<nb, 32 * wpb, sm, s>>>(__VA_ARGS__); break;                      \
+    default: KERNEL<T, 16><<<nb, 32 * wpb, sm, s>>>(__VA_ARGS__); break;                      \
+  }
 
 // Shared by the Poisson and Stokes paths.
 template <typename T>
 cudaError_t fft_x_forward(const Params& P, const T* in, int R, cplx<T>* out, T scale, int Nyr, T add0, T add1,
-                          const cplx<T>* tw, cudaStream_t s) {
+                          const cplx<T>* tw, cudaStream_t s, const T* add0x) {
   int N = P.Nx, logN = 31 - __builtin_clz((unsigned)N);
-  int pp = P.fx_pp;
-  int pairs = (R + 1) / 2;
-  int nb = (pairs + pp - 1) / pp;
-  size_t sm = (2 * (size_t)pp * N + N / 2) * sizeof(cplx<T>) + 2 * (size_t)pp * sizeof(T);
+  const int pairs = (R + 1) / 2;
   probe_begin(PROBE_FFT_X, s);
-  k_rfft_x<T><<<nb, P.fx_threads, sm, s>>>(in, R, N, logN, P.Px, out, scale, Nyr, add0, add1, tw, pp);
+  if (N >= 32) {
+    const int wpb = x_warps_per_block<T>(P);
+    const int nb = (pairs + wpb - 1) / wpb;
+    const size_t sm = (size_t)wpb * 32 * (N / 32 + 1) * sizeof(cplx<T>);
+    DISCOS_X_DISPATCH(k_rfft_x_w, in, R, P.Px, out, scale, Nyr, add0, add1, tw, add0x)
+  } else {
+    int pp = P.fx_pp;
+    int nb = (pairs + pp - 1) / pp;
+    size_t sm = (2 * (size_t)pp * N + N / 2) * sizeof(cplx<T>) + 2 * (size_t)pp * sizeof(T);
+    k_rfft_x<T><<<nb, P.fx_threads, sm, s>>>(in, R, N, logN, P.Px, out, scale, Nyr, add0, add1, tw, pp, add0x);
+  }
   count_launches(1);
   probe_end(PROBE_FFT_X, s);
   return cudaGetLastError();
@@ -264,58 +424,78 @@ template <typename T>
 cudaError_t fft_x_inverse(const Params& P, const cplx<T>* in, int R, T* out, T scale, const cplx<T>* tw,
                           cudaStream_t s) {
   int N = P.Nx, logN = 31 - __builtin_clz((unsigned)N);
-  int pp = P.fx_pp;
-  int pairs = (R + 1) / 2;
-  int nb = (pairs + pp - 1) / pp;
-  size_t sm = (2 * (size_t)pp * N + N / 2) * sizeof(cplx<T>);
+  const int pairs = (R + 1) / 2;
   probe_begin(PROBE_FFT_X, s);
-  k_irfft_x<T><<<nb, P.fx_threads, sm, s>>>(in, R, N, logN, P.Px, out, scale, tw, pp);
+  if (N >= 32) {
+    const int wpb = x_warps_per_block<T>(P);
+    const int nb = (pairs + wpb - 1) / wpb;
+    const size_t sm = (size_t)wpb * 32 * (N / 32 + 1) * sizeof(cplx<T>);
+    DISCOS_X_DISPATCH(k_irfft_x_w, in, R, P.Px, out, scale, tw)
+  } else {
+    int pp = P.fx_pp;
+    int nb = (pairs + pp - 1) / pp;
+    size_t sm = (2 * (size_t)pp * N + N / 2) * sizeof(cplx<T>);
+    k_irfft_x<T><<<nb, P.fx_threads, sm, s>>>(in, R, N, logN, P.Px, out, scale, tw, pp);
+  }
   count_launches(1);
   probe_end(PROBE_FFT_X, s);
+  return cudaGetLastError();
+}
+#undef DISCOS_X_DISPATCH
+
+// z transforms: fz_tk x-mode columns per block (rounded up to whole warps).
+template <typename T, int G>
+void fft_z_dispatch(const Params& P, dim3 grid, int threads, cplx<T>* data, int Nyr, int inv, const cplx<T>* tw,
+                    size_t field_stride, int mac, cudaStream_t s) {
+  switch (P.Nz / G) {
+    case 1: k_fft_z_w<T, G, 1><<<grid, threads, 0, s>>>(data, Nyr, P.Px, P.Nxh, inv, tw, field_stride, mac); break;
+    case 2: k_fft_z_w<T, G, 2><<<grid, threads, 0, s>>>(data, Nyr, P.Px, P.Nxh, inv, tw, field_stride, mac); break;
+    case 4: k_fft_z_w<T, G, 4><<<grid, threads, 0, s>>>(data, Nyr, P.Px, P.Nxh, inv, tw, field_stride, mac); break;
+    case 8: k_fft_z_w<T, G, 8><<<grid, threads, 0, s>>>(data, Nyr, P.Px, P.Nxh, inv, tw, field_stride, mac); break;
+    case 16: k_fft_z_w<T, G, 16><<<grid, threads, 0, s>>>(data, Nyr, P.Px, P.Nxh, inv, tw, field_stride, mac); break;
+    default: k_fft_z_w<T, G, 32><<<grid, threads, 0, s>>>(data, Nyr, P.Px, P.Nxh, inv, tw, field_stride, mac); break;
+  }
+}
+
+template <typename T>
+cudaError_t fft_z_launch(const Params& P, cplx<T>* data, int Nyr, int grid_y, int nfields, size_t field_stride,
+                         bool inverse, const cplx<T>* tw, int mac, cudaStream_t s) {
+  // lanes per column: 8 (float, Nz <= 256), else 16; never more than Nz
+  int G = (sizeof(T) == 4 && P.Nz <= 256) ? 8 : 16;
+  if (G > P.Nz) G = P.Nz;
+  const int cpw = 32 / G;
+  const int wpb = P.fz_tk <= cpw ? 1 : P.fz_tk / cpw;
+  dim3 grid((P.Nxh + cpw * wpb - 1) / (cpw * wpb), grid_y, nfields);
+  const int inv = inverse ? 1 : 0;
+  probe_begin(PROBE_FFT_Z, s);
+  if (G == 8) fft_z_dispatch<T, 8>(P, grid, 32 * wpb, data, Nyr, inv, tw, field_stride, mac, s);
+  else fft_z_dispatch<T, 16>(P, grid, 32 * wpb, data, Nyr, inv, tw, field_stride, mac, s);
+  count_launches(1);
+  probe_end(PROBE_FFT_Z, s);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t fft_z(const Params& P, cplx<T>* data, int Nyr, int nfields, size_t field_stride, bool inverse,
                   const cplx<T>* tw, cudaStream_t s) {
-  int Nz = P.Nz, logNz = 31 - __builtin_clz((unsigned)Nz);
-  const int TK = P.fz_tk;
-  size_t sm = (2 * (size_t)TK * (Nz + 1) + Nz / 2) * sizeof(cplx<T>);
-  ensure_fft_z_attr<T>();
-  dim3 grid((P.Nxh + TK - 1) / TK, Nyr, nfields);
-  probe_begin(PROBE_FFT_Z, s);
-  k_fft_z<T><<<grid, fz_threads(TK, Nz), sm, s>>>(data, Nz, logNz, Nyr, P.Px, P.Nxh, inverse ? 1 : 0, tw,
-                                                   field_stride, 0, TK);
-  count_launches(1);
-  probe_end(PROBE_FFT_Z, s);
-  return cudaGetLastError();
+  return fft_z_launch<T>(P, data, Nyr, Nyr, nfields, field_stride, inverse, tw, 0, s);
 }
 
 template <typename T>
 cudaError_t fft_z_mac(const Params& P, cplx<T>* data, bool inverse, const cplx<T>* tw, cudaStream_t s) {
-  int Nz = P.Nz, logNz = 31 - __builtin_clz((unsigned)Nz);
-  const int TK = P.fz_tk;
-  size_t sm = (2 * (size_t)TK * (Nz + 1) + Nz / 2) * sizeof(cplx<T>);
-  ensure_fft_z_attr<T>();
-  dim3 grid((P.Nxh + TK - 1) / TK, P.Ny + 1, 3);
-  probe_begin(PROBE_FFT_Z, s);
-  k_fft_z<T><<<grid, fz_threads(TK, Nz), sm, s>>>(data, Nz, logNz, P.Ny, P.Px, P.Nxh, inverse ? 1 : 0, tw, 0,
-                                                   1, TK);
-  count_launches(1);
-  probe_end(PROBE_FFT_Z, s);
-  return cudaGetLastError();
+  return fft_z_launch<T>(P, data, P.Ny, P.Ny + 1, 3, 0, inverse, tw, 1, s);
 }
 
 // One transform-solve-transform pass: phi = A^-1 (scale rho + wall terms)
 // with the ghost-cell terms add0 / add1 on the wall rows.
 template <typename T>
 cudaError_t poisson_pass(const Params& P, Workspace& W, const T* rho, T* phi, T scale, T add0, T add1,
-                         cudaStream_t s) {
+                         cudaStream_t s, const T* add0x) {
   const int Ny = P.Ny, Nz = P.Nz;
   cplx<T>* S = reinterpret_cast<cplx<T>*>(W.spec);
   const cplx<T>* twx = reinterpret_cast<const cplx<T>*>(W.tw_x);
   const cplx<T>* twz = reinterpret_cast<const cplx<T>*>(W.tw_z);
-  cudaError_t e = fft_x_forward<T>(P, rho, Nz * Ny, S, scale, Ny, add0, add1, twx, s);
+  cudaError_t e = fft_x_forward<T>(P, rho, Nz * Ny, S, scale, Ny, add0, add1, twx, s, add0x);
   if (e != cudaSuccess) return e;
   e = fft_z<T>(P, S, Ny, 1, 0, false, twz, s);
   if (e != cudaSuccess) return e;
@@ -332,22 +512,27 @@ cudaError_t launch_poisson(const Params& P, Workspace& W, const T* rho, T* phi, 
   // ghost-cell terms of the wall rows (Eqs. esbc1, esbc3)
   const T add0 = P.bc[0] == DISCOS_BC_DIRICHLET ? T(2.0 * P.phi_b[0]) : T(-P.slope[0]);
   const T add1 = P.bc[1] == DISCOS_BC_DIRICHLET ? T(2.0 * P.phi_b[1]) : T(P.slope[1]);
+  if (P.strip) return launch_poisson_strip<T>(P, W, rho, phi, T(fourpi_lB), add1, s);
   const int sweeps = (sizeof(T) == sizeof(float) && W.rref) ? P.max_refine : 0;
-  if (sweeps == 0) return poisson_pass<T>(P, W, rho, phi, T(fourpi_lB), add0, add1, s);
+  if (sweeps == 0) return poisson_pass<T>(P, W, rho, phi, T(fourpi_lB), add0, add1, s, static_cast<const T*>(nullptr));
   // mixed precision with residual refinement: keep rho (phi may alias it),
-  // solve, then correct with the double-precision residual (k_refine.cu)
+  // solve, then correct with the double-precision residual (k_refine.cu); the
+  // corrections accumulate in double, so the residual can fall below the
+  // rounding of a single-precision potential
   const size_t G = (size_t)P.Nx * P.Ny * P.Nz;
   T* rho_keep = reinterpret_cast<T*>(W.rref);
   T* res = reinterpret_cast<T*>(W.rres);
   cudaError_t e = cudaMemcpyAsync(rho_keep, rho, sizeof(T) * G, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = launch_fill_zero<double>(W.rnorm, 2 * (DISCOS_MAX_REFINE + 1), s);
-  if (e == cudaSuccess) e = poisson_pass<T>(P, W, rho_keep, phi, T(fourpi_lB), add0, add1, s);
+  if (e == cudaSuccess) e = poisson_pass<T>(P, W, rho_keep, phi, T(fourpi_lB), add0, add1, s, static_cast<const T*>(nullptr));
+  if (e == cudaSuccess) e = launch_convert<double, T>(W.phi64, phi, G, s);
   for (int it = 0; it < sweeps && e == cudaSuccess; ++it) {
-    e = launch_poisson_residual<T>(P, rho_keep, phi, res, W.rnorm + 2 * it, s);
-    if (e == cudaSuccess) e = poisson_pass<T>(P, W, res, res, T(1), T(0), T(0), s);
-    if (e == cudaSuccess) e = launch_add_inplace<T>(phi, res, G, s);
+    e = launch_poisson_residual<T, double>(P, rho_keep, W.phi64, res, W.rnorm + 2 * it, s);
+    if (e == cudaSuccess) e = poisson_pass<T>(P, W, res, res, T(1), T(0), T(0), s, static_cast<const T*>(nullptr));
+    if (e == cudaSuccess) e = launch_accumulate<T>(W.phi64, res, G, s);
   }
-  if (e == cudaSuccess) e = launch_poisson_residual<T>(P, rho_keep, phi, nullptr, W.rnorm + 2 * sweeps, s);
+  if (e == cudaSuccess) e = launch_poisson_residual<T, double>(P, rho_keep, W.phi64, (T*)nullptr, W.rnorm + 2 * sweeps, s);
+  if (e == cudaSuccess) e = launch_convert<T, double>(phi, W.phi64, G, s);
   return e;
 }
 
@@ -389,7 +574,7 @@ cudaError_t tune_transforms_t(Params& P, Workspace& W, cudaStream_t s, float* be
     th = th < 32 ? 32 : (th > 256 ? 256 : th);
     Q.fx_pp = pp;
     Q.fx_threads = th;
-    const float ms = time_it([&] { return fft_x_forward<T>(Q, grid, R, S, T(1), P.Ny, T(0), T(0), twx, s); });
+    const float ms = time_it([&] { return fft_x_forward<T>(Q, grid, R, S, T(1), P.Ny, T(0), T(0), twx, s, nullptr); });
     if (ms < bx) { bx = ms; best_pp = pp; best_th = th; }
   }
   Q = P;
@@ -415,8 +600,10 @@ cudaError_t tune_transforms(Params& P, Workspace& W, bool mixed, cudaStream_t s,
 
 template cudaError_t launch_poisson<float>(const Params&, Workspace&, const float*, float*, cudaStream_t);
 template cudaError_t launch_poisson<double>(const Params&, Workspace&, const double*, double*, cudaStream_t);
-template cudaError_t fft_x_forward<float>(const Params&, const float*, int, cplx<float>*, float, int, float, float, const cplx<float>*, cudaStream_t);
-template cudaError_t fft_x_forward<double>(const Params&, const double*, int, cplx<double>*, double, int, double, double, const cplx<double>*, cudaStream_t);
+template cudaError_t fft_x_forward<float>(const Params&, const float*, int, cplx<float>*, float, int, float, float, const cplx<float>*, cudaStream_t, const float*);
+template cudaError_t fft_x_forward<double>(const Params&, const double*, int, cplx<double>*, double, int, double, double, const cplx<double>*, cudaStream_t, const double*);
+template cudaError_t poisson_pass<float>(const Params&, Workspace&, const float*, float*, float, float, float, cudaStream_t, const float*);
+template cudaError_t poisson_pass<double>(const Params&, Workspace&, const double*, double*, double, double, double, cudaStream_t, const double*);
 template cudaError_t fft_x_inverse<float>(const Params&, const cplx<float>*, int, float*, float, const cplx<float>*, cudaStream_t);
 template cudaError_t fft_x_inverse<double>(const Params&, const cplx<double>*, int, double*, double, const cplx<double>*, cudaStream_t);
 template cudaError_t fft_z<float>(const Params&, cplx<float>*, int, int, size_t, bool, const cplx<float>*, cudaStream_t);

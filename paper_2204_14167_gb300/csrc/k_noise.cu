@@ -2,28 +2,31 @@
 // Eq. stokes_temporal on the MAC faces.  Z is symmetric: diagonal entries
 // sqrt(2) N(0,1) at cell centres, off-diagonal entries N(0,1) on the edges
 // (xy at (x=i, y=j), xz at (x=i, z=k), yz at (y=j, z=k), j = 0..Ny), the
-// off-diagonal entries on the wall edges scaled by sqrt(2) so that the noise
-// covariance matches the no-slip viscous operator (discrete fluctuation-
-// dissipation balance).  Normals come from Philox counters
+// off-diagonal entries on the wall edges scaled by sqrt(2) at a no-slip wall
+// and by 0 at a slip wall, so that the noise covariance matches the viscous
+// operator with those walls (discrete fluctuation-dissipation balance).  Normals come from Philox counters
 // (cell of an Nx x (Ny+1) x Nz lattice, step, 0, tag 3 / tag 4).
 //
-// Each block generates Z for a 32 x 4 x 4 tile of cells plus a one-cell halo
-// in shared memory (two Philox draws per halo cell) and then forms the three
-// face divergences of its cells, adding them to the force grids.
+// Each block generates Z for a 32 x 8 x 8 tile of cells plus a one-cell halo
+// in shared memory (two Philox draws per halo cell; of the second only the
+// two normals that are used) and then forms the three face divergences of
+// its cells, adding them to the force grids.
+#include <atomic>
 #include "internal.h"
 
 namespace discos {
 
 namespace {
 
-constexpr int TX = 32, TY = 4, TZ = 4;
+constexpr int TX = 32, TY = 8, TZ = 8;
 constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
 constexpr int HN = HX * HY * HZ;
 
 template <typename T>
 __global__ void k_stress_noise(T* __restrict__ f, Params P, long long step, T amp, int overwrite) {
-  __shared__ T Zd[3][HN];     // xx, yy, zz
-  __shared__ T Ze[3][HN];     // xy, xz, yz
+  extern __shared__ unsigned char smem_raw[];
+  T (*Zd)[HN] = reinterpret_cast<T (*)[HN]>(smem_raw);            // xx, yy, zz
+  T (*Ze)[HN] = reinterpret_cast<T (*)[HN]>(smem_raw) + 3;        // xy, xz, yz
   const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * TZ;
   const int tid = threadIdx.x;
@@ -37,10 +40,11 @@ __global__ void k_stress_noise(T* __restrict__ f, Params P, long long step, T am
     if (j >= 0 && j <= Ny) {
       uint32_t cell = (uint32_t)(((size_t)k * (Ny + 1) + j) * Nx + i);
       normals4(u32x4{cell, (uint32_t)step, 0u, (uint32_t)TAG_STRESS_A}, P.seed, a);
-      normals4(u32x4{cell, (uint32_t)step, 0u, (uint32_t)TAG_STRESS_B}, P.seed, b);
+      normals2(u32x4{cell, (uint32_t)step, 0u, (uint32_t)TAG_STRESS_B}, P.seed, b);
     }
     bool centre = j >= 0 && j < Ny;
-    T wall = (j == 0 || j == Ny) ? r2 : T(1);
+    // wall edges: sqrt 2 at a no-slip wall, no shear stress at a slip wall
+    T wall = j == 0 ? (P.slip[0] ? T(0) : r2) : (j == Ny ? (P.slip[1] ? T(0) : r2) : T(1));
     Zd[0][h] = centre ? r2 * a[0] : T(0);
     Zd[1][h] = centre ? r2 * a[1] : T(0);
     Zd[2][h] = centre ? r2 * a[2] : T(0);
@@ -82,8 +86,17 @@ template <typename T>
 cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_t s, bool overwrite) {
   dim3 grid((P.Nx + TX - 1) / TX, (P.Ny + TY - 1) / TY, (P.Nz + TZ - 1) / TZ);
   T amp = T(sqrt(2.0 * P.kT * P.eta / P.dt));
+  const size_t sm = 6 * (size_t)HN * sizeof(T);
+  // the attribute belongs to the current device: set it once per device
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !(done.load() & (1ull << dev))) {
+    cudaError_t e = cudaFuncSetAttribute(k_stress_noise<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    done.fetch_or(1ull << dev);
+  }
   probe_begin(PROBE_NOISE, s);
-  k_stress_noise<T><<<grid, 256, 0, s>>>(f, P, (long long)step, amp, overwrite ? 1 : 0);
+  k_stress_noise<T><<<grid, 256, sm, s>>>(f, P, (long long)step, amp, overwrite ? 1 : 0);
   count_launches(1);
   probe_end(PROBE_NOISE, s);
   return cudaGetLastError();

@@ -1,7 +1,7 @@
 // Spreading (Eq. kernel2) of charges onto cell centres and of forces onto the
 // MAC faces, with the wall image construction of Sec. II.A (Fig. folded) and
 // Sec. II.B.1 applied as an index fold: a stencil point outside the channel
-// is mapped to its mirror inside with the image sign.
+// is mapped to its mirror inside with the image sign.  Also the fill kernels.
 //
 // Thread layout: a group of 8 lanes per ion (4 ions per warp); lane l owns
 // x-offset l of the stencil, so each warp-wide atomic touches 4 short runs of
@@ -13,13 +13,23 @@ namespace discos {
 
 namespace {
 
+// Ions in cell order put the stencils of neighbouring lanes on the same grid
+// points, and their atomics then serialise.  Spreading visits the ions in
+// the order ion(g) = g * stride mod N (stride coprime with N, so the map is
+// a bijection; see spread_stride), which scatters each warp's ions over the
+// channel; stride 0 keeps the given order.
+__device__ __forceinline__ int spread_ion(int g, int N, unsigned long long stride) {
+  if (!stride || g >= N) return g;
+  return (int)(((unsigned long long)g * stride) % (unsigned long long)N);
+}
+
 template <typename T>
 __global__ void k_spread_charge(const T* __restrict__ x, const T* __restrict__ q, int N, Params P,
-                                T* __restrict__ rho) {
+                                T* __restrict__ rho, unsigned long long stride) {
   const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
   const KernelParams kp = P.kes;
   const int w = kp.w;
-  int ion = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  int ion = spread_ion((blockIdx.x * blockDim.x + threadIdx.x) >> 3, N, stride);
   int l = threadIdx.x & 7;
   int gbase = (threadIdx.x & 31) & ~7;
   bool valid = ion < N;
@@ -44,26 +54,29 @@ __global__ void k_spread_charge(const T* __restrict__ x, const T* __restrict__ q
       T sg = T(1);
       if (iy < 0) { iy = -1 - iy; sg = s0; }
       else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = s1; }
+      if (P.strip && y0 + jy < 0) sg = on_strip(P, ix) ? T(-1) : T(1);
       if (valid && l < w && iy >= 0 && iy < Ny)
         atomicAdd(&rho[((size_t)iz * Ny + iy) * Nx + ix], qq * sg * wzj * wyj * wx);
     }
   }
 }
 
-// Force spreading for one MAC component c (blockIdx.y), no-slip images
-// (sign -1 for every component).  With rfd, adds the thermal forcing of
+// Force spreading for one MAC component c (blockIdx.y), with images of sign
+// -1 for the normal component and for the tangential ones at a no-slip wall,
+// +1 for the tangential ones at a slip wall.  With rfd, adds the thermal forcing of
 // Eq. thermforce: the random finite difference
 //   (kT/delta) [S(x + delta W/2) W - S(x - delta W/2) W]
 // in its delta -> 0 form kT W_c (W . grad_x) S, which equals the finite
 // difference to O(delta^2) and has no cancellation in single precision.
 template <typename T>
 __global__ void k_spread_force(const T* __restrict__ x, const T* __restrict__ F, int N, Params P,
-                               T* __restrict__ f, long long step, int rfd) {
+                               T* __restrict__ f, long long step, int rfd, const int* __restrict__ noise_index,
+                               unsigned long long stride) {
   const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
   const KernelParams kp = P.khy;
   const int w = kp.w;
   const int c = blockIdx.y;
-  int ion = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  int ion = spread_ion((blockIdx.x * blockDim.x + threadIdx.x) >> 3, N, stride);
   int l = threadIdx.x & 7;
   int gbase = (threadIdx.x & 31) & ~7;
   bool valid = ion < N;
@@ -75,7 +88,8 @@ __global__ void k_spread_force(const T* __restrict__ x, const T* __restrict__ F,
     Fc = F[(size_t)c * N + ion];
     if (rfd) {
       T g[4];
-      normals4(u32x4{(uint32_t)ion, (uint32_t)step, 0u, (uint32_t)TAG_RFD}, P.seed, g);
+      const int key = noise_index ? noise_index[ion] : ion;
+      normals4(u32x4{(uint32_t)key, (uint32_t)step, 0u, (uint32_t)TAG_RFD}, P.seed, g);
       Wr[0] = g[0]; Wr[1] = g[1]; Wr[2] = g[2];
     }
   }
@@ -112,9 +126,9 @@ __global__ void k_spread_force(const T* __restrict__ x, const T* __restrict__ F,
         if (iy < 0) { iy = -iy; sg = T(-1); }
         else if (iy > Ny) { iy = 2 * Ny - iy; sg = T(-1); }
         ok = iy > 0 && iy < Ny;
-      } else {                  // cell-centred in y
-        if (iy < 0) { iy = -1 - iy; sg = T(-1); }
-        else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = T(-1); }
+      } else {                  // cell-centred in y: tangential, like image at a slip wall
+        if (iy < 0) { iy = -1 - iy; sg = P.slip[0] ? T(1) : T(-1); }
+        else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = P.slip[1] ? T(1) : T(-1); }
         ok = iy >= 0 && iy < Ny;
       }
       T val = Fc * wv[0] * wyj * wzj;
@@ -124,16 +138,16 @@ __global__ void k_spread_force(const T* __restrict__ x, const T* __restrict__ F,
   }
 }
 
-// The two spreads with the stencil width W fixed at compile time (4 and 6
+// The charge spread with the stencil width W fixed at compile time (4 and 6
 // points): the y and z weights of the group are fetched once, the image fold
-// of the W rows is resolved once per ion (and component), and the stencil
-// loops unroll into independent atomics.
+// of the W rows is resolved once per ion, and the stencil loops unroll into
+// independent atomics.
 template <typename T, int W>
 __global__ void k_spread_charge_w(const T* __restrict__ x, const T* __restrict__ q, int N, Params P,
-                                  T* __restrict__ rho) {
+                                  T* __restrict__ rho, unsigned long long stride) {
   const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
   const KernelParams kp = P.kes;
-  int ion = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  int ion = spread_ion((blockIdx.x * blockDim.x + threadIdx.x) >> 3, N, stride);
   int l = threadIdx.x & 7;
   int gbase = (threadIdx.x & 31) & ~7;
   bool valid = ion < N;
@@ -163,24 +177,28 @@ __global__ void k_spread_charge_w(const T* __restrict__ x, const T* __restrict__
   if (valid && l < W) {
     const int ix = (x0 + l) & (Nx - 1);
     const T qx = qq * wx;
+    // a metal strip in the (dielectric) bottom wall: rows below the wall take
+    // the conducting wall's sign in the strip's columns
+    const T cs = on_strip(P, ix) ? T(-1) : T(1);
 #pragma unroll
     for (int jz = 0; jz < W; ++jz) {
       const size_t zoff = (size_t)((z0 + jz) & (Nz - 1)) * Ny * Nx + ix;
       const T qz = qx * wz[jz];
 #pragma unroll
       for (int jy = 0; jy < W; ++jy)
-        if (wy[jy] != T(0)) atomicAdd(&rho[zoff + roff[jy]], qz * wy[jy]);
+        if (wy[jy] != T(0)) atomicAdd(&rho[zoff + roff[jy]], qz * (y0 + jy < 0 ? cs : T(1)) * wy[jy]);
     }
   }
 }
 
 template <typename T, int W>
 __global__ void k_spread_force_w(const T* __restrict__ x, const T* __restrict__ F, int N, Params P,
-                                 T* __restrict__ f, long long step, int rfd) {
+                                 T* __restrict__ f, long long step, int rfd, const int* __restrict__ noise_index,
+                                 unsigned long long stride) {
   const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
   const KernelParams kp = P.khy;
   const int c = blockIdx.y;
-  int ion = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  int ion = spread_ion((blockIdx.x * blockDim.x + threadIdx.x) >> 3, N, stride);
   int l = threadIdx.x & 7;
   int gbase = (threadIdx.x & 31) & ~7;
   bool valid = ion < N;
@@ -192,7 +210,8 @@ __global__ void k_spread_force_w(const T* __restrict__ x, const T* __restrict__ 
     Fc = F[(size_t)c * N + ion];
     if (rfd) {
       T g[4];
-      normals4(u32x4{(uint32_t)ion, (uint32_t)step, 0u, (uint32_t)TAG_RFD}, P.seed, g);
+      const int key = noise_index ? noise_index[ion] : ion;
+      normals4(u32x4{(uint32_t)key, (uint32_t)step, 0u, (uint32_t)TAG_RFD}, P.seed, g);
       Wr[0] = g[0]; Wr[1] = g[1]; Wr[2] = g[2];
     }
   }
@@ -228,8 +247,8 @@ __global__ void k_spread_force_w(const T* __restrict__ x, const T* __restrict__ 
       else if (iy > Ny) { iy = 2 * Ny - iy; sg = T(-1); }
       ok = iy > 0 && iy < Ny;
     } else {                  // cell-centred in y
-      if (iy < 0) { iy = -1 - iy; sg = T(-1); }
-      else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = T(-1); }
+      if (iy < 0) { iy = -1 - iy; sg = P.slip[0] ? T(1) : T(-1); }
+      else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = P.slip[1] ? T(1) : T(-1); }
       ok = iy >= 0 && iy < Ny;
     }
     roff[j] = ok ? iy * Nx : 0;
@@ -256,27 +275,50 @@ __global__ void k_spread_force_w(const T* __restrict__ x, const T* __restrict__ 
 }
 
 template <typename T>
-__global__ void k_fill(T* __restrict__ p, size_t n) {
+__global__ void k_fill(T* __restrict__ p, size_t n, T value) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (; i < n; i += stride) p[i] = T(0);
+  for (; i < n; i += stride) p[i] = value;
 }
 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_fill_zero(T* p, size_t n, cudaStream_t s) {
+cudaError_t launch_fill_value(T* p, size_t n, T value, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   int bs = 256;
   size_t nb = (n + bs - 1) / bs;
   if (nb > 152 * 16) nb = 152 * 16;
-  k_fill<T><<<(unsigned)nb, bs, 0, s>>>(p, n);
+  k_fill<T><<<(unsigned)nb, bs, 0, s>>>(p, n, value);
   count_launches(1);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N, T* rho, cudaStream_t s) {
+cudaError_t launch_fill_zero(T* p, size_t n, cudaStream_t s) {
+  return launch_fill_value<T>(p, n, T(0), s);
+}
+
+// A prime near 0.618 N that does not divide N: g * stride mod N is then a
+// bijection that sends consecutive g about 0.618 N apart (Fibonacci
+// hashing).  0 (the given order) for N < 3.
+static unsigned long long spread_stride(int N) {
+  if (N < 3) return 0ull;
+  auto prime = [](unsigned long long v) {
+    if (v < 2) return false;
+    for (unsigned long long d = 2; d * d <= v; ++d)
+      if (v % d == 0) return false;
+    return true;
+  };
+  unsigned long long p = (unsigned long long)(0.6180339887498949 * N);
+  if (p < 2) p = 2;
+  while (!prime(p) || (unsigned long long)N % p == 0) ++p;
+  return p;
+}
+
+template <typename T>
+cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N, T* rho, cudaStream_t s,
+                                 bool decorrelate) {
   probe_begin(PROBE_SPREAD_CHARGE, s);
   cudaError_t e = launch_fill_zero(rho, (size_t)P.Nx * P.Ny * P.Nz, s);
   if (e != cudaSuccess || N <= 0) {
@@ -285,9 +327,10 @@ cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N,
   }
   int bs = 256;
   int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
-  if (P.kes.w == 4) k_spread_charge_w<T, 4><<<nb, bs, 0, s>>>(x, q, N, P, rho);
-  else if (P.kes.w == 6) k_spread_charge_w<T, 6><<<nb, bs, 0, s>>>(x, q, N, P, rho);
-  else k_spread_charge<T><<<nb, bs, 0, s>>>(x, q, N, P, rho);
+  const unsigned long long st = decorrelate ? spread_stride(N) : 0ull;
+  if (P.kes.w == 4) k_spread_charge_w<T, 4><<<nb, bs, 0, s>>>(x, q, N, P, rho, st);
+  else if (P.kes.w == 6) k_spread_charge_w<T, 6><<<nb, bs, 0, s>>>(x, q, N, P, rho, st);
+  else k_spread_charge<T><<<nb, bs, 0, s>>>(x, q, N, P, rho, st);
   count_launches(1);
   probe_end(PROBE_SPREAD_CHARGE, s);
   return cudaGetLastError();
@@ -295,7 +338,7 @@ cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N,
 
 template <typename T>
 cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, T* f, int64_t step, bool rfd,
-                                cudaStream_t s, bool accumulate) {
+                                cudaStream_t s, bool accumulate, const int* noise_index, bool decorrelate) {
   size_t n = (size_t)P.Nx * P.Nz * (3 * P.Ny + 1);
   probe_begin(PROBE_SPREAD_FORCE, s);
   cudaError_t e = accumulate ? cudaSuccess : launch_fill_zero(f, n, s);
@@ -305,19 +348,24 @@ cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, 
   }
   int bs = 256;
   dim3 grid((unsigned)(((size_t)N * 8 + bs - 1) / bs), 3);
-  if (P.khy.w == 4) k_spread_force_w<T, 4><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0);
-  else if (P.khy.w == 6) k_spread_force_w<T, 6><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0);
-  else k_spread_force<T><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0);
+  if (P.khy.w == 4) k_spread_force_w<T, 4><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0, noise_index,
+                                                                   decorrelate ? spread_stride(N) : 0ull);
+  else if (P.khy.w == 6) k_spread_force_w<T, 6><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0, noise_index,
+                                                                   decorrelate ? spread_stride(N) : 0ull);
+  else k_spread_force<T><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0, noise_index,
+                                             decorrelate ? spread_stride(N) : 0ull);
   count_launches(1);
   probe_end(PROBE_SPREAD_FORCE, s);
   return cudaGetLastError();
 }
 
+template cudaError_t launch_fill_value<float>(float*, size_t, float, cudaStream_t);
+template cudaError_t launch_fill_value<double>(double*, size_t, double, cudaStream_t);
 template cudaError_t launch_fill_zero<float>(float*, size_t, cudaStream_t);
 template cudaError_t launch_fill_zero<double>(double*, size_t, cudaStream_t);
-template cudaError_t launch_spread_charge<float>(const Params&, const float*, const float*, int, float*, cudaStream_t);
-template cudaError_t launch_spread_charge<double>(const Params&, const double*, const double*, int, double*, cudaStream_t);
-template cudaError_t launch_spread_force<float>(const Params&, const float*, const float*, int, float*, int64_t, bool, cudaStream_t, bool);
-template cudaError_t launch_spread_force<double>(const Params&, const double*, const double*, int, double*, int64_t, bool, cudaStream_t, bool);
+template cudaError_t launch_spread_charge<float>(const Params&, const float*, const float*, int, float*, cudaStream_t, bool);
+template cudaError_t launch_spread_charge<double>(const Params&, const double*, const double*, int, double*, cudaStream_t, bool);
+template cudaError_t launch_spread_force<float>(const Params&, const float*, const float*, int, float*, int64_t, bool, cudaStream_t, bool, const int*, bool);
+template cudaError_t launch_spread_force<double>(const Params&, const double*, const double*, int, double*, int64_t, bool, cudaStream_t, bool, const int*, bool);
 
 }  // namespace discos

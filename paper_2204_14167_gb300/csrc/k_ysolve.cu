@@ -20,6 +20,7 @@
 // precision (error well below 1e-5); the modes with K^2 < 0.5 (a few percent,
 // the ill-conditioned ones and the singular K = 0 mode) are solved in double.
 // The FP64 path solves every mode in double.
+#include <atomic>
 #include <type_traits>
 #include "internal.h"
 
@@ -111,19 +112,14 @@ template <typename TS> __device__ __forceinline__ C<double> ldc(const cplx<TS>* 
 // ------------------------------------------------------------------ Poisson
 // piv [M][Ny]: reciprocal Thomas pivots.  Forward y_j = piv_j (b_j + y_{j-1}),
 // backward x_j = y_j + piv_j x_{j+1}.  The singular K = 0 mode of two
-// Neumann walls: phi_0 = 0, phi_{j+1} = 2 phi_j - phi_{j-1} - b_j (the last
-// equation is redundant for a neutral system), then the mean is removed.
+// Neumann walls: the right-hand side's mean is removed (so the last equation
+// is redundant), phi_0 = 0, phi_{j+1} = 2 phi_j - phi_{j-1} - b_j, then the
+// mean of phi is removed.
+// One mode's solve; col points at its column (rows cs apart).
 template <typename TS, typename TC, int R>
-__global__ void k_poisson_scan(cplx<TS>* __restrict__ S, const TC* __restrict__ piv, const int* __restrict__ list,
-                               int n_list, const unsigned char* __restrict__ skip, int Ny, int Nz, int Nxh, int Px,
-                               int singular, TC norm) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void poisson_mode(cplx<TS>* __restrict__ col, size_t cs, const TC* __restrict__ piv,
+                                             int mode, int Ny, int singular, TC norm) {
   const int lane = threadIdx.x & 31;
-  if (w >= n_list) return;
-  const int mode = list ? list[w] : w;
-  if (skip && skip[mode]) return;
-  const int kz = mode / Nxh, kx = mode - kz * Nxh;
-  cplx<TS>* col = S + (size_t)kz * Ny * Px + kx;
   const TC* pv = piv + (size_t)mode * Ny;
   const int j0 = lane * R;
   C<TC> b[R];
@@ -132,7 +128,7 @@ __global__ void k_poisson_scan(cplx<TS>* __restrict__ S, const TC* __restrict__ 
   for (int r = 0; r < R; ++r) {
     int j = j0 + r;
     if (j < Ny) {
-      cplx<TS> v = col[(size_t)j * Px];
+      cplx<TS> v = col[(size_t)j * cs];
       b[r] = C<TC>{(TC)v.re, (TC)v.im};
       m[r] = pv[j];
     } else {
@@ -142,6 +138,22 @@ __global__ void k_poisson_scan(cplx<TS>* __restrict__ S, const TC* __restrict__ 
   }
   C<TC> x[R];
   if (singular && mode == 0) {
+    // the right-hand side projected onto the operator's range (mean over y
+    // removed): the result is the mean-zero (minimum-norm) solution, also
+    // for a non-neutral right-hand side
+    C<TC> bs = cz<TC>();
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (j0 + r < Ny) bs = cadd2(bs, b[r]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      bs.r += __shfl_xor_sync(0xffffffffu, bs.r, o);
+      bs.i += __shfl_xor_sync(0xffffffffu, bs.i, o);
+    }
+    const C<TC> bm = cscale(TC(1) / TC(Ny), bs);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (j0 + r < Ny) b[r] = csub2(b[r], bm);
     // state (phi_j, phi_{j-1}); row j maps it to (phi_{j+1}, phi_j)
     M2<TC> loc = m2_id<TC>();
 #pragma unroll
@@ -210,7 +222,53 @@ __global__ void k_poisson_scan(cplx<TS>* __restrict__ S, const TC* __restrict__ 
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     int j = j0 + r;
-    if (j < Ny) col[(size_t)j * Px] = cplx<TS>{(TS)(x[r].r * norm), (TS)(x[r].i * norm)};
+    if (j < Ny) col[(size_t)j * cs] = cplx<TS>{(TS)(x[r].r * norm), (TS)(x[r].i * norm)};
+  }
+}
+
+
+template <typename TS, typename TC, int R>
+__global__ void k_poisson_scan(cplx<TS>* __restrict__ S, const TC* __restrict__ piv, const int* __restrict__ list,
+                               int n_list, const unsigned char* __restrict__ skip, int Ny, int Nz, int Nxh, int Px,
+                               int singular, TC norm) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n_list) return;
+  const int mode = list ? list[w] : w;
+  if (skip && skip[mode]) return;
+  const int kz = mode / Nxh, kx = mode - kz * Nxh;
+  poisson_mode<TS, TC, R>(S + (size_t)kz * Ny * Px + kx, (size_t)Px, piv, mode, Ny, singular, norm);
+}
+
+// The same over tiles of TM consecutive x-modes at one kz staged in shared
+// memory (coalesced row loads and stores; modes in `skip` are left alone).
+template <typename TS, typename TC, int R, int TM>
+__global__ void k_poisson_scan_staged(cplx<TS>* __restrict__ S, const TC* __restrict__ piv,
+                                      const unsigned char* __restrict__ skip, int Ny, int Nxh, int Px, int singular,
+                                      TC norm) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<TS>* tile = reinterpret_cast<cplx<TS>*>(smem_raw);     // [TM][Ny + 1]
+  const int PR = Ny + 1;
+  const int ntx = (Nxh + TM - 1) / TM;
+  const int kz = blockIdx.x / ntx, kx0 = (blockIdx.x - kz * ntx) * TM;
+  cplx<TS>* base = S + (size_t)kz * Ny * Px;
+  for (int idx = threadIdx.x; idx < TM * Ny; idx += blockDim.x) {
+    const int c = idx % TM, row = idx / TM;
+    tile[c * PR + row] = kx0 + c < Nxh ? base[(size_t)row * Px + kx0 + c] : cplx<TS>{TS(0), TS(0)};
+  }
+  __syncthreads();
+  const int wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = wib; c < TM; c += nw) {
+    const int kx = kx0 + c;
+    if (kx >= Nxh) break;
+    const int mode = kz * Nxh + kx;
+    if (skip && skip[mode]) continue;
+    poisson_mode<TS, TC, R>(tile + c * PR, 1, piv, mode, Ny, singular, norm);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < TM * Ny; idx += blockDim.x) {
+    const int c = idx % TM, row = idx / TM;
+    const int kx = kx0 + c;
+    if (kx < Nxh && !(skip && skip[kz * Nxh + kx])) base[(size_t)row * Px + kx] = tile[c * PR + row];
   }
 }
 
@@ -226,24 +284,20 @@ __global__ void k_poisson_scan(cplx<TS>* __restrict__ S, const TC* __restrict__ 
 // MC [M][5] = (g_x, g_z, -1/K^2; 0 for K = 0).  The K = 0 mode (all-zero
 // pentadiagonal factors) gives v = 0 and p = 0 here; its pressure, needed only
 // for output, is p_j = sum_{f=1..j} f_y,f with the mean removed.
+// The four sweeps of one mode.  Su, Sv, Sw point at the mode's column of
+// the u, v, w spectra, rows cs apart (the spectrum itself, or a staged copy
+// in shared memory); Sp (rows P.Px apart, the spectrum's layout) may be NULL.
+// sg, sv: the warp's shared-memory rows of g and v.
 template <typename TS, typename TC, int R>
-__global__ void k_stokes_scan(cplx<TS>* __restrict__ S, cplx<TS>* __restrict__ Sp, Params P,
-                              const TC* __restrict__ L1, const TC* __restrict__ L2, const TC* __restrict__ DI,
-                              const TC* __restrict__ CI, const TC* __restrict__ MC, const int* __restrict__ list,
-                              int n_list, const unsigned char* __restrict__ skip) {
-  extern __shared__ unsigned char smem_raw[];
-  const int Ny = P.Ny, Nz = P.Nz, Px = P.Px, Nxh = P.Nxh;
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int w = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (w >= n_list) return;
-  const int mode = list ? list[w] : w;
-  if (skip && skip[mode]) return;
-  C<TC>* sg = reinterpret_cast<C<TC>*>(smem_raw) + (size_t)wib * (2 * Ny + 1);   // g [Ny]
-  C<TC>* sv = sg + Ny;                                                              // v [Ny + 1]
+__device__ __forceinline__ void stokes_mode(cplx<TS>* __restrict__ Su, cplx<TS>* __restrict__ Sv,
+                                            cplx<TS>* __restrict__ Sw, size_t cs, cplx<TS>* __restrict__ Sp,
+                                            int mode, const Params& P, const TC* __restrict__ L1,
+                                            const TC* __restrict__ L2, const TC* __restrict__ DI,
+                                            const TC* __restrict__ CI, const TC* __restrict__ MC, C<TC>* sg,
+                                            C<TC>* sv) {
+  const int Ny = P.Ny, Px = P.Px, Nxh = P.Nxh;
+  const int lane = threadIdx.x & 31;
   const int kz = mode / Nxh, kx = mode - kz * Nxh;
-  cplx<TS>* Su = S + (size_t)kz * Ny * Px + kx;
-  cplx<TS>* Sv = S + (size_t)Nz * Ny * Px + (size_t)kz * (Ny + 1) * Px + kx;
-  cplx<TS>* Sw = S + (size_t)Nz * (2 * Ny + 1) * Px + (size_t)kz * Ny * Px + kx;
   const TC* l1 = L1 + (size_t)mode * Ny;
   const TC* l2 = L2 + (size_t)mode * Ny;
   const TC* di = DI + (size_t)mode * Ny;
@@ -261,7 +315,7 @@ __global__ void k_stokes_scan(cplx<TS>* __restrict__ S, cplx<TS>* __restrict__ S
   for (int r = 0; r < R; ++r) {
     int j = j0 + r;
     if (j < Ny) {
-      cplx<TS> a = Su[(size_t)j * Px], b = Sw[(size_t)j * Px], c = Sv[(size_t)j * Px];
+      cplx<TS> a = Su[(size_t)j * cs], b = Sw[(size_t)j * cs], c = Sv[(size_t)j * cs];
       fx[r] = C<TC>{(TC)a.re, (TC)a.im};
       fz[r] = C<TC>{(TC)b.re, (TC)b.im};
       fy[r] = C<TC>{(TC)c.re, (TC)c.im};
@@ -372,10 +426,10 @@ __global__ void k_stokes_scan(cplx<TS>* __restrict__ S, cplx<TS>* __restrict__ S
     int f = j0 + r;
     if (f < Ny + 1) {
       C<TC> vv = (f >= 1 && f < Ny) ? v[r] : cz<TC>();
-      Sv[(size_t)f * Px] = cplx<TS>{(TS)(vv.r * norm), (TS)(vv.i * norm)};
+      Sv[(size_t)f * cs] = cplx<TS>{(TS)(vv.r * norm), (TS)(vv.i * norm)};
     }
   }
-  if (lane == 0) Sv[(size_t)Ny * Px] = cplx<TS>{TS(0), TS(0)};
+  if (lane == 0) Sv[(size_t)Ny * cs] = cplx<TS>{TS(0), TS(0)};
   // ---- C: pressure (row-local) and the forward sweeps for u and w
   C<TC> bu[R], bw[R];
   TC cm[R];
@@ -435,10 +489,84 @@ __global__ void k_stokes_scan(cplx<TS>* __restrict__ S, cplx<TS>* __restrict__ S
         TC a = j < Ny - 1 ? cm[r] : TC(0);
         xu = cfma(a, xu, bu[r]);
         xw = cfma(a, xw, bw[r]);
-        Su[(size_t)j * Px] = cplx<TS>{(TS)(xu.r * norm), (TS)(xu.i * norm)};
-        Sw[(size_t)j * Px] = cplx<TS>{(TS)(xw.r * norm), (TS)(xw.i * norm)};
+        Su[(size_t)j * cs] = cplx<TS>{(TS)(xu.r * norm), (TS)(xu.i * norm)};
+        Sw[(size_t)j * cs] = cplx<TS>{(TS)(xw.r * norm), (TS)(xw.i * norm)};
       }
     }
+  }
+}
+
+
+template <typename TS, typename TC, int R>
+__global__ void k_stokes_scan(cplx<TS>* __restrict__ S, cplx<TS>* __restrict__ Sp, Params P,
+                              const TC* __restrict__ L1, const TC* __restrict__ L2, const TC* __restrict__ DI,
+                              const TC* __restrict__ CI, const TC* __restrict__ MC, const int* __restrict__ list,
+                              int n_list, const unsigned char* __restrict__ skip) {
+  extern __shared__ unsigned char smem_raw[];
+  const int Ny = P.Ny, Nz = P.Nz, Px = P.Px, Nxh = P.Nxh;
+  const int wib = threadIdx.x >> 5;
+  const int w = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (w >= n_list) return;
+  const int mode = list ? list[w] : w;
+  if (skip && skip[mode]) return;
+  C<TC>* sg = reinterpret_cast<C<TC>*>(smem_raw) + (size_t)wib * (2 * Ny + 1);   // g [Ny]
+  C<TC>* sv = sg + Ny;                                                              // v [Ny + 1]
+  const int kz = mode / Nxh, kx = mode - kz * Nxh;
+  cplx<TS>* Su = S + (size_t)kz * Ny * Px + kx;
+  cplx<TS>* Sv = S + (size_t)Nz * Ny * Px + (size_t)kz * (Ny + 1) * Px + kx;
+  cplx<TS>* Sw = S + (size_t)Nz * (2 * Ny + 1) * Px + (size_t)kz * Ny * Px + kx;
+  stokes_mode<TS, TC, R>(Su, Sv, Sw, (size_t)Px, Sp, mode, P, L1, L2, DI, CI, MC, sg, sv);
+}
+
+// The same solve over a tile of TM consecutive x-modes at one kz, staged in
+// shared memory: the block reads the tile's rows of the three spectra with
+// coalesced loads (TM consecutive modes of a row are contiguous), each warp
+// solves its modes from the staged columns, and the block writes the tile
+// back, leaving the modes in `skip` (solved by the double-precision launch
+// on the side stream) untouched.  Pressure is not produced.
+template <typename TS, typename TC, int R, int TM>
+__global__ void k_stokes_scan_staged(cplx<TS>* __restrict__ S, Params P, const TC* __restrict__ L1,
+                                     const TC* __restrict__ L2, const TC* __restrict__ DI,
+                                     const TC* __restrict__ CI, const TC* __restrict__ MC,
+                                     const unsigned char* __restrict__ skip) {
+  extern __shared__ unsigned char smem_raw[];
+  const int Ny = P.Ny, Nz = P.Nz, Px = P.Px, Nxh = P.Nxh;
+  const int PR = Ny + 1;                                 // staged column pitch (rows)
+  cplx<TS>* tile = reinterpret_cast<cplx<TS>*>(smem_raw);                 // [3][TM][PR]
+  C<TC>* wbuf = reinterpret_cast<C<TC>*>(tile + 3 * TM * PR);              // per warp: g [Ny], v [Ny + 1]
+  const int ntx = (Nxh + TM - 1) / TM;
+  const int kz = blockIdx.x / ntx, kx0 = (blockIdx.x - kz * ntx) * TM;
+  const int wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  cplx<TS>* const b0 = S + (size_t)kz * Ny * Px;
+  cplx<TS>* const b1 = S + (size_t)Nz * Ny * Px + (size_t)kz * (Ny + 1) * Px;
+  cplx<TS>* const b2 = S + (size_t)Nz * (2 * Ny + 1) * Px + (size_t)kz * Ny * Px;
+  const int total = 3 * TM * PR;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int c = idx % TM, row = (idx / TM) % PR, f = idx / (TM * PR);
+    const int nrow = f == 1 ? Ny + 1 : Ny;
+    cplx<TS> v{TS(0), TS(0)};
+    if (row < nrow && kx0 + c < Nxh) v = (f == 0 ? b0 : (f == 1 ? b1 : b2))[(size_t)row * Px + kx0 + c];
+    tile[(f * TM + c) * PR + row] = v;
+  }
+  __syncthreads();
+  C<TC>* sg = wbuf + (size_t)wib * (2 * Ny + 1);
+  C<TC>* sv = sg + Ny;
+  for (int c = wib; c < TM; c += nw) {
+    const int kx = kx0 + c;
+    if (kx >= Nxh) break;
+    const int mode = kz * Nxh + kx;
+    if (skip && skip[mode]) continue;
+    stokes_mode<TS, TC, R>(tile + (0 * TM + c) * PR, tile + (1 * TM + c) * PR, tile + (2 * TM + c) * PR, 1,
+                           nullptr, mode, P, L1, L2, DI, CI, MC, sg, sv);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int c = idx % TM, row = (idx / TM) % PR, f = idx / (TM * PR);
+    const int nrow = f == 1 ? Ny + 1 : Ny;
+    const int kx = kx0 + c;
+    if (row < nrow && kx < Nxh && !(skip && skip[kz * Nxh + kx]))
+      (f == 0 ? b0 : (f == 1 ? b1 : b2))[(size_t)row * Px + kx] = tile[(f * TM + c) * PR + row];
   }
 }
 
@@ -451,10 +579,53 @@ cudaError_t poisson_scan_launch(const Params& P, cplx<TS>* S, const TC* piv, con
   const int bs = 256;
   const int nb = (n * 32 + bs - 1) / bs;
   if (n <= 0) return cudaSuccess;
+  if (!list) {
+    // every mode in order: the shared-memory staged kernel, 32 modes per block
+    constexpr int TM = 32;
+    const int nbs = P.Nz * ((P.Nxh + TM - 1) / TM);
+    const size_t sm = (size_t)TM * (Ny + 1) * sizeof(cplx<TS>);
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    if (sm > 48 * 1024 && cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !(done.load() & (1ull << dev))) {
+      cudaError_t e = cudaSuccess;
+      e = Ny <= 32 ? cudaFuncSetAttribute(k_poisson_scan_staged<TS, TC, 1, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)
+        : Ny <= 64 ? cudaFuncSetAttribute(k_poisson_scan_staged<TS, TC, 2, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)
+        : Ny <= 128 ? cudaFuncSetAttribute(k_poisson_scan_staged<TS, TC, 4, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)
+        : cudaFuncSetAttribute(k_poisson_scan_staged<TS, TC, 8, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e != cudaSuccess) return e;
+      done.fetch_or(1ull << dev);
+    }
+    if (Ny <= 32) k_poisson_scan_staged<TS, TC, 1, TM><<<nbs, bs, sm, s>>>(S, piv, skip, Ny, P.Nxh, P.Px, singular, norm);
+    else if (Ny <= 64) k_poisson_scan_staged<TS, TC, 2, TM><<<nbs, bs, sm, s>>>(S, piv, skip, Ny, P.Nxh, P.Px, singular, norm);
+    else if (Ny <= 128) k_poisson_scan_staged<TS, TC, 4, TM><<<nbs, bs, sm, s>>>(S, piv, skip, Ny, P.Nxh, P.Px, singular, norm);
+    else k_poisson_scan_staged<TS, TC, 8, TM><<<nbs, bs, sm, s>>>(S, piv, skip, Ny, P.Nxh, P.Px, singular, norm);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   if (Ny <= 32) k_poisson_scan<TS, TC, 1><<<nb, bs, 0, s>>>(S, piv, list, n, skip, Ny, P.Nz, P.Nxh, P.Px, singular, norm);
   else if (Ny <= 64) k_poisson_scan<TS, TC, 2><<<nb, bs, 0, s>>>(S, piv, list, n, skip, Ny, P.Nz, P.Nxh, P.Px, singular, norm);
   else if (Ny <= 128) k_poisson_scan<TS, TC, 4><<<nb, bs, 0, s>>>(S, piv, list, n, skip, Ny, P.Nz, P.Nxh, P.Px, singular, norm);
   else k_poisson_scan<TS, TC, 8><<<nb, bs, 0, s>>>(S, piv, list, n, skip, Ny, P.Nz, P.Nxh, P.Px, singular, norm);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename TS, typename TC, int R, int TM>
+cudaError_t stokes_staged_launch(const Params& P, cplx<TS>* S, const TC* L1, const TC* L2, const TC* DI,
+                                 const TC* CI, const TC* MC, const unsigned char* skip, cudaStream_t s) {
+  const int warps = 8;
+  const size_t sm = 3 * (size_t)TM * (P.Ny + 1) * sizeof(cplx<TS>) + warps * (size_t)(2 * P.Ny + 1) * sizeof(C<TC>);
+  // the attribute belongs to the current device: set it once per device
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !(done.load() & (1ull << dev))) {
+    cudaError_t e = cudaFuncSetAttribute(k_stokes_scan_staged<TS, TC, R, TM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    done.fetch_or(1ull << dev);
+  }
+  const int nb = P.Nz * ((P.Nxh + TM - 1) / TM);
+  k_stokes_scan_staged<TS, TC, R, TM><<<nb, 32 * warps, sm, s>>>(S, P, L1, L2, DI, CI, MC, skip);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -465,6 +636,14 @@ cudaError_t stokes_scan_launch(const Params& P, cplx<TS>* S, cplx<TS>* Sp, const
                                const unsigned char* skip, cudaStream_t s) {
   const int Ny = P.Ny;
   if (n <= 0) return cudaSuccess;
+  // every mode in order and no pressure wanted: the shared-memory staged kernel
+  if (!list && !Sp) {
+    constexpr int TM = sizeof(TS) == 4 ? 16 : 8;
+    if (Ny <= 32) return stokes_staged_launch<TS, TC, 1, TM>(P, S, L1, L2, DI, CI, MC, skip, s);
+    if (Ny <= 64) return stokes_staged_launch<TS, TC, 2, TM>(P, S, L1, L2, DI, CI, MC, skip, s);
+    if (Ny <= 128) return stokes_staged_launch<TS, TC, 4, TM>(P, S, L1, L2, DI, CI, MC, skip, s);
+    return stokes_staged_launch<TS, TC, 8, TM>(P, S, L1, L2, DI, CI, MC, skip, s);
+  }
   const size_t per_warp = (size_t)(2 * Ny + 1) * sizeof(C<TC>);
   int warps = 8;
   while (warps > 1 && warps * per_warp > 48 * 1024) --warps;   // stay within the default shared-memory limit

@@ -15,6 +15,33 @@ __device__ __forceinline__ int cell_coord(T v, int k, int nc) {
   return c < nc ? c : nc - 1;
 }
 
+// A periodic coordinate (x or z) moved into [0, L): one shift by L for the
+// positions a step can produce, a floor-based wrap (then a clamp against the
+// rounding of v - L floor(v / L)) for anything further out.  Positions
+// already inside are returned unchanged.
+template <typename T>
+__device__ __forceinline__ T wrap_coord(T v, int Li) {
+  const T L = T(Li);
+  if (v >= T(0) && v < L) return v;
+  T w = v < T(0) ? v + L : v - L;
+  if (!(w >= T(0) && w < L)) w = v - L * floor(v / L);
+  return (w >= T(0) && w < L) ? w : T(0);
+}
+
+// Packed (x, y, z, q) of one ion, one vector load in the pair loop.
+struct alignas(32) double4a { double x, y, z, w; };
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { typedef float4 type; };
+template <> struct Vec4<double> { typedef double4a type; };
+__device__ __forceinline__ float4 make_vec4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+__device__ __forceinline__ double4a make_vec4(double a, double b, double c, double d) { return double4a{a, b, c, d}; }
+__device__ __forceinline__ void load_vec4(const float4& v, float& a, float& b, float& c, float& d) {
+  a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void load_vec4(const double4a& v, double& a, double& b, double& c, double& d) {
+  a = v.x; b = v.y; c = v.z; d = v.w;
+}
+
 template <typename T>
 __device__ __forceinline__ T min_image(T d, T L, T half) {
   if (d > half) return sub_rn(d, L);

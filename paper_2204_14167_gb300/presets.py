@@ -101,6 +101,22 @@ def iceo_channel_256x128x256(precision=MIXED):
     return cfg, dict(n_pos=200000, n_neg=200000, ymargin=1.0, min_sep=0.9 * 0.6, seed=20220503)
 
 
+def iceo_strip_256x128x256(precision=MIXED):
+    """The 256 x 128 x 256 channel in the paper's ICEO geometry (Sec. IV.B,
+    Fig. EOgeometry): both walls dielectric (Neumann, no surface charge) and a
+    metal strip centred in the bottom wall, its width the paper's ratio
+    L_m / P_x = 5.272 / 26.36 = 0.2 of the box (51.2 cells), held at total
+    potential 0 (phi + phi_E constant on the metal under E_x = 0.02); ions,
+    physics and time step as iceo_channel_256x128x256."""
+    cfg, rec = iceo_channel_256x128x256(precision)
+    cfg.bc = (BC_NEUMANN, BC_NEUMANN)
+    cfg.strip = True
+    w = 0.2 * cfg.Nx
+    cfg.strip_x = (0.5 * (cfg.Nx - w), 0.5 * (cfg.Nx + w))
+    cfg.strip_phi = 0.0
+    return cfg, dict(rec, seed=rec["seed"] + 7)
+
+
 def batched_channels_32(R=512, precision=MIXED, seed=20220502):
     """R independent replicas of dry_channel_32's channel (Dirichlet phi = 0
     walls, l_B = 7, 6-point kernel, dt = 0.001), replica r holding an even,
@@ -129,4 +145,5 @@ PRESETS = {
     "wet_channel_128x64x128": wet_channel_128x64x128,
     "energy_channel_64": energy_channel_64,
     "iceo_channel_256x128x256": iceo_channel_256x128x256,
+    "iceo_strip_256x128x256": iceo_strip_256x128x256,
 }

@@ -26,7 +26,7 @@ def _cuda():
     torch.cuda.init()
 
 
-def _setup(prec, bc=(1, 1), n=301):
+def _setup(prec, bc=(1, 1), n=300):
     cfg, rec = presets.dry_channel_32(prec)
     cfg.Nx, cfg.Ny, cfg.Nz = 32, 16, 32
     cfg.bc = bc
@@ -80,3 +80,72 @@ def test_device_fault_word(prec):
     h.step(x, q, step0=3, nsteps=1)
     torch.cuda.synchronize()
     assert h.fault(sync=True) == 0
+
+
+@pytest.mark.parametrize("prec", [dg.FP64, dg.MIXED])
+def test_non_neutral_neumann_channel_rejected(prec):
+    """Two Neumann walls fix the potential only up to a constant and need
+    charge + surface charge = 0 (Sec. II.B.1).  discos_forces and
+    discos_solve_poisson check it in double before any solve is launched
+    (status 3); discos_step checks it on the device every step and refuses the
+    next call.  A neutral channel with surface charge passes."""
+    cfg, x, q = _setup(prec, bc=(1, 1))
+    h = dg.Discos(cfg)
+    h.forces(x, q)                                   # neutral: accepted
+    q2 = q.clone()
+    q2[0] += 1.0                                     # net charge +1 (or 0 -> 2, 1 -> 2)
+    with pytest.raises(dg.DiscosError) as ei:
+        h.forces(x, q2)
+    assert ei.value.status == 3
+    rho = h.spread_charge(x, q2)
+    with pytest.raises(dg.DiscosError) as ei:
+        h.solve_poisson(rho)
+    assert ei.value.status == 3
+    h.step(x.clone(), q2, step0=0, nsteps=1)         # enqueued; the device flags bit 2
+    torch.cuda.synchronize()
+    assert h.fault(sync=True) & 4
+    with pytest.raises(dg.DiscosError) as ei:
+        h.step(x.clone(), q2, step0=1, nsteps=1)
+    assert ei.value.status == 3
+    h.fault(sync=True, clear=True)
+    # surface charge balancing the ions' net charge: neutral again
+    Nx, Ny, Nz = cfg.dims
+    net = float(q2.double().sum())
+    cfg.surf_charge = (-0.5 * net / (Nx * Nz), -0.5 * net / (Nx * Nz))
+    h2 = dg.Discos(cfg)
+    h2.forces(x, q2)
+    h2.solve_poisson(h2.spread_charge(x, q2))
+    h2.step(x.clone(), q2, step0=0, nsteps=1)
+    assert h2.fault(sync=True) == 0
+
+
+def test_failing_allocator_gives_oom():
+    """A discos_alloc_fn that returns NULL: discos_create frees what it got,
+    returns DISCOS_ERR_OOM (2) and no handle; the free hook sees every
+    pointer the alloc hook handed out."""
+    import ctypes
+    from paper_2204_14167_gb300 import _lib
+    lib = _lib.load()
+    cfg, _, _ = _setup(dg.FP64)
+    c = cfg.to_c()
+    ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+    FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+    given, freed = [], []
+    budget = [3]            # three allocations succeed, then the device is "full"
+
+    def alloc(nbytes, ctx):
+        if budget[0] <= 0:
+            return None
+        budget[0] -= 1
+        t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+        given.append(t)
+        return t.data_ptr()
+
+    def free(ptr, ctx):
+        freed.append(ptr)
+    a, f = ALLOC(alloc), FREE(free)
+    hnd = ctypes.c_void_p()
+    st = lib.discos_create(ctypes.byref(c), a, f, None, ctypes.byref(hnd))
+    assert st == _lib.ERR_OOM
+    assert not hnd.value
+    assert sorted(freed) == sorted(t.data_ptr() for t in given)

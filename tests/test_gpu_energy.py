@@ -159,3 +159,42 @@ def test_energy_full_size(prec):
     # the P3M, wall and external parts are not in U: compare with the grid force
     Fg = qd * h.interpolate_efield(xd, h.solve_poisson(h.spread_charge(xd, qd)))
     assert rel_l2(-x.grad.double().cpu().numpy(), Fg.double().cpu().numpy()) < 5e-2
+
+
+def test_energy_gradients_full_size_fd():
+    """The 64^3 Dirichlet channel with 4096 ions and wall potentials
+    +0.5 / -0.5: the hand-written backward against FP64 central differences
+    (h = 1e-4) of the forward energy on a 32-ion subset, for positions,
+    charges and both wall potentials.  The forward is itself compared with the
+    oracle's energy on this channel (test_energy_full_size)."""
+    cfg, rec = presets.energy_channel_64(dg.FP64)
+    xd, qd, pos, q = _ions(cfg, rec)
+    h = dg.Discos(cfg)
+    phi_b = torch.tensor(cfg.phi_b, dtype=torch.float64, requires_grad=True)
+    x = xd.clone().requires_grad_(True)
+    qq = qd.clone().requires_grad_(True)
+    U = denergy(h, x, qq, phi_b)
+    U.backward()
+    hh = 1e-4
+    ions = list(range(0, 4096, 128))
+
+    def Uof(xv, qv, pb=None):
+        return float(h.energy(xv, qv, pb))
+    gx = np.zeros((3, len(ions)))
+    gq = np.zeros(len(ions))
+    for k, i in enumerate(ions):
+        for d in range(3):
+            a = xd.clone(); a[d, i] += hh
+            b = xd.clone(); b[d, i] -= hh
+            gx[d, k] = (Uof(a, qd) - Uof(b, qd)) / (2 * hh)
+        a = qd.clone(); a[i] += hh
+        b = qd.clone(); b[i] -= hh
+        gq[k] = (Uof(xd, a) - Uof(xd, b)) / (2 * hh)
+    gb = np.zeros(2)
+    for w in range(2):
+        a = list(cfg.phi_b); a[w] += hh
+        b = list(cfg.phi_b); b[w] -= hh
+        gb[w] = (Uof(xd, qd, a) - Uof(xd, qd, b)) / (2 * hh)
+    assert rel_l2(x.grad.double().cpu().numpy()[:, ions], gx) < 1e-6
+    assert rel_l2(qq.grad.double().cpu().numpy()[ions], gq) < 1e-6
+    assert rel_l2(phi_b.grad.numpy(), gb) < 1e-6

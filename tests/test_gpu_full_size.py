@@ -10,6 +10,10 @@ make one sample at a time, or that hold at any size.
   stated single-precision target), and one full wet step from the same state
   (same Philox noise): displacements within 1e-4 relative plus one float ulp
   of the coordinates (the MIXED path stores positions in float).
+- Stokes on the 128 x 64 x 128 and 256 x 128 x 256 grids under white-noise
+  forcing: the GPU velocity and pressure in the oracle's MAC operator
+  (Eq. disc_stokes, applied by stencils): momentum residual and divergence
+  <= 1e-10 relative (FP64) / 2e-5 (MIXED: float storage of v and p).
 """
 import numpy as np
 import pytest
@@ -100,3 +104,38 @@ def test_full_size_mixed_against_fp64(state):
     rms = lambda a: float(np.sqrt(np.mean(np.square(a))))
     ulp = float(np.spacing(np.float32(max(c64.dims))))
     assert rms(dm - d64) <= 1e-4 * rms(d64) + ulp
+
+
+# Stokes at the two single-channel sizes the bench runs: white-noise forcing
+# (the hardest case: every mode excited), the GPU velocity and pressure put
+# into the oracle's MAC operator (stencils, no solve).
+STOKES_SIZES = {"128x64x128": ("wet_channel_128x64x128", 1e-10, 2e-5),
+                "256x128x256": ("iceo_channel_256x128x256", 1e-10, 2e-5)}
+
+
+@pytest.mark.parametrize("prec", [dg.FP64, dg.MIXED])
+@pytest.mark.parametrize("size", sorted(STOKES_SIZES))
+def test_full_size_stokes_residual(prec, size):
+    from helpers import mac_split, mac_join
+    from oracle import stokes
+    preset, tol64, tol32 = STOKES_SIZES[size]
+    c, _ = getattr(presets, preset)(prec)
+    h = dg.Discos(c)
+    Nx, Ny, Nz = c.dims
+    rng = np.random.default_rng(21)
+    fx = rng.normal(size=(Nz, Ny, Nx)); fz = rng.normal(size=(Nz, Ny, Nx))
+    fy = rng.normal(size=(Nz, Ny + 1, Nx)); fy[:, 0] = 0.0; fy[:, Ny] = 0.0
+    dt = torch.float64 if prec == dg.FP64 else torch.float32
+    fd = torch.tensor(mac_join(fx, fy, fz), dtype=dt, device="cuda")
+    v, p = h.solve_stokes(fd.clone(), pressure=True)
+    fh = mac_split(fd.double().cpu().numpy(), c.dims)
+    u_, v_, w_ = mac_split(v.double().cpu().numpy(), c.dims)
+    (rx, ry, rz), div = stokes.residual(u_, v_, w_, p.double().cpu().numpy().reshape(Nz, Ny, Nx), *fh, c.eta)
+    nf = np.sqrt(sum(np.sum(a ** 2) for a in fh))
+    rel = np.sqrt(np.sum(rx ** 2) + np.sum(ry ** 2) + np.sum(rz ** 2)) / nf
+    # divergence relative to the velocity's own differences
+    vscale = np.sqrt(sum(np.sum(a ** 2) for a in (u_, v_, w_)) / (3 * Nx * Ny * Nz))
+    drel = float(np.sqrt(np.mean(div ** 2)) / vscale)
+    tol = tol64 if prec == dg.FP64 else tol32
+    assert rel <= tol, (rel, drel)
+    assert drel <= tol, (rel, drel)

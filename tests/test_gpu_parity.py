@@ -99,15 +99,15 @@ def test_transform_shapes(prec, shape):
     phi = h.solve_poisson(rd).double().cpu().numpy()
     ref = poisson.solve(rd.double().cpu().numpy(), cfg.bc, cfg.lB, cfg.phi_b, cfg.surf_charge)
     assert rel_l2(phi, ref) < TOL[prec]["phi"]
-    h0 = dg.Discos(cfg)
     f = torch.tensor(rng.normal(size=Nx * Nz * (3 * Ny + 1)), dtype=_dtype(prec), device="cuda")
     u, v, w = mac_split(f.cpu().numpy(), cfg.dims)
     v[:, 0, :] = 0.0
     v[:, -1, :] = 0.0
     f = torch.tensor(mac_join(u, v, w), dtype=_dtype(prec), device="cuda")
     vel = h.solve_stokes(f.clone()).double().cpu().numpy()
-    vel0 = h0.solve_stokes(f.clone()).double().cpu().numpy()
-    assert rel_l2(vel, vel0) < TOL[prec]["vel"]
+    fh = mac_split(f.double().cpu().numpy(), cfg.dims)
+    ref = stokes.solve(fh[0], fh[1], fh[2], cfg.eta)[:3]
+    assert rel_l2(vel, mac_join(*ref)) < TOL[prec]["vel"]
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -235,6 +235,36 @@ def test_near_field(prec, bc):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_near_field_periodic_images_of_positions(prec):
+    """x and z are periodic: positions handed in outside [0, L) (shifted by
+    +-L) give the near field of their images inside the box.  Coordinates on
+    a 1/1024 lattice make every shift exact in both precisions, so the
+    partner counts stay bit-exact against the oracle on the wrapped
+    positions."""
+    cfg, rec = _small_dry((0, 1), n=419)
+    xd, qd, pos, q, sp = _setup(cfg, rec, prec)
+    pos = np.round(pos * 1024.0) / 1024.0
+    pos[1] = np.clip(pos[1], 1.0 / 1024.0, cfg.Ny - 1.0 / 1024.0)
+    rng = np.random.default_rng(3)
+    shifted = pos.copy()
+    for ax, L in ((0, cfg.Nx), (2, cfg.Nz)):
+        shifted[ax] += L * rng.integers(-1, 2, size=pos.shape[1])
+    h = dg.Discos(cfg)
+    xs = torch.tensor(shifted, dtype=_dtype(prec), device="cuda").contiguous()
+    F, cnt = h.near_field(xs, qd)
+    p = oracle_params(cfg)
+    pair_dt = np.float64 if prec == dg.FP64 else np.float32
+    ref, ref_cnt = particles.near_field(pos, q, sp, p, p["fp_table"], pair_dtype=pair_dt)
+    ref[1] += particles.wall_force(pos, sp, p)
+    assert np.array_equal(cnt.cpu().numpy(), ref_cnt)
+    assert rel_l2(F.double().cpu().numpy(), ref) < TOL[prec]["force"]
+    start, perm = h.cell_list(xs)
+    k = int(np.ceil(max(cfg.psi, max(max(r) for r in cfg.lj_rc))))
+    _, ref_start, ref_perm = particles.cell_list(pos, cfg.dims, k)
+    assert np.array_equal(start.cpu().numpy(), ref_start) and np.array_equal(perm.cpu().numpy(), ref_perm)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("bc", [(0, 0), (1, 1), (0, 1)])
 def test_total_forces(prec, bc):
     cfg, rec = _small_dry(bc, n=300, phi_b=(0.2, -0.1))
@@ -267,10 +297,16 @@ def test_spread_force(prec, kernel):
     assert rel_l2(f, ref) < TOL[prec]["grid"]
 
 
+# thin, tall boxes reach every rows-per-lane variant of the wall-normal
+# solves (Ny <= 32, 64, 128, 256)
+STOKES_DIMS = [(16, 8, 16), (32, 30, 16), (16, 64, 16), (16, 128, 16), (16, 160, 16)]
+
+
 @pytest.mark.parametrize("prec", PRECS)
-def test_stokes(prec):
+@pytest.mark.parametrize("dims", STOKES_DIMS)
+def test_stokes(prec, dims):
     cfg, rec = _small_dry((0, 0), kernel=dg.KERNEL_PESKIN4)
-    cfg.Nx, cfg.Ny, cfg.Nz = 16, 8, 16
+    cfg.Nx, cfg.Ny, cfg.Nz = dims
     cfg.eta = 0.7
     cfg.wet = True
     cfg.precision = prec
@@ -285,6 +321,40 @@ def test_stokes(prec):
     u, vv, w, p = stokes.solve(fh[0], fh[1], fh[2], cfg.eta)
     assert rel_l2(v.double().cpu().numpy(), mac_join(u, vv, w)) < TOL[prec]["vel"]
     assert rel_l2(pr.double().cpu().numpy(), p) < TOL[prec]["vel"]
+
+
+def test_stokes_refinement():
+    """Mixed precision with double-precision residual refinement of the MAC
+    system (Eq. disc_stokes): the residual, measured with the velocity and
+    pressure carried in double, falls by orders of magnitude per sweep, below
+    the rounding of a single-precision velocity; the rounded result is at
+    least as close to the oracle as the plain single-precision solve, to
+    within that rounding."""
+    cfg, rec = _small_dry((0, 0), kernel=dg.KERNEL_PESKIN4)
+    cfg.Nx, cfg.Ny, cfg.Nz = 32, 16, 32
+    cfg.eta = 0.7
+    cfg.wet = True
+    cfg.precision = dg.MIXED
+    rng = np.random.default_rng(24)
+    Nx, Ny, Nz = cfg.dims
+    fx = rng.normal(size=(Nz, Ny, Nx)); fz = rng.normal(size=(Nz, Ny, Nx))
+    fy = rng.normal(size=(Nz, Ny + 1, Nx)); fy[:, 0] = 0; fy[:, Ny] = 0
+    fd = torch.tensor(mac_join(fx, fy, fz), dtype=torch.float32, device="cuda")
+    h0 = dg.Discos(cfg)
+    cfg.max_refine = 2
+    h2 = dg.Discos(cfg)
+    v0, p0 = h0.solve_stokes(fd.clone(), pressure=True)
+    v2, p2 = h2.solve_stokes(fd.clone(), pressure=True)
+    hist = h2.refine_history_stokes()
+    assert h0.refine_history_stokes() == []
+    assert len(hist) == 3 and hist[1] < 1e-2 * hist[0] and hist[2] <= 1.5 * hist[1] and hist[2] < 1e-8, hist
+    fh = mac_split(fd.double().cpu().numpy(), cfg.dims)
+    u, vv, w, p = stokes.solve(fh[0], fh[1], fh[2], cfg.eta)
+    ref = mac_join(u, vv, w)
+    e0 = rel_l2(v0.double().cpu().numpy(), ref)
+    e2 = rel_l2(v2.double().cpu().numpy(), ref)
+    assert e2 <= max(e0, 1e-7), (e0, e2)
+    assert rel_l2(p2.double().cpu().numpy(), p) <= max(rel_l2(p0.double().cpu().numpy(), p), 1e-7)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -342,6 +412,28 @@ def test_wet_step(prec, drift):
     p = oracle_params(cfg)
     pair_dt = np.float64 if prec == dg.FP64 else np.float32
     new, F, cnt, parts = integrate.wet_step(p, pos, q, sp, 3, pair_dtype=pair_dt)
+    assert rel_l2(F_gpu.double().cpu().numpy(), F) < TOL[prec]["force"]
+    d_gpu = min_image_disp(xd.double().cpu().numpy(), x0.double().cpu().numpy(), cfg.dims)
+    d_ref = min_image_disp(new, pos, cfg.dims)
+    assert rel_l2(d_gpu, d_ref) < TOL[prec]["step"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("Ny", [64, 128])
+def test_wet_step_tall(prec, Ny):
+    """The wet step on thin, tall channels (16 x Ny x 16, 200 ions): the
+    wall-normal solves with 2 and 4 rows per lane, as on the 128 x 64 x 128
+    and 256 x 128 x 256 channels, against the oracle's step."""
+    cfg, rec = presets.wet_channel_small(prec, Nx=16, Ny=Ny, Nz=16, n=200)
+    xd, qd, pos, q, sp = _setup(cfg, rec, prec)
+    h = dg.Discos(cfg)
+    F_gpu = torch.empty_like(xd)
+    x0 = xd.clone()
+    h.step(xd, qd, step0=5, nsteps=1, F_out=F_gpu)
+    torch.cuda.synchronize()
+    p = oracle_params(cfg)
+    pair_dt = np.float64 if prec == dg.FP64 else np.float32
+    new, F, cnt, parts = integrate.wet_step(p, pos, q, sp, 5, pair_dtype=pair_dt)
     assert rel_l2(F_gpu.double().cpu().numpy(), F) < TOL[prec]["force"]
     d_gpu = min_image_disp(xd.double().cpu().numpy(), x0.double().cpu().numpy(), cfg.dims)
     d_ref = min_image_disp(new, pos, cfg.dims)

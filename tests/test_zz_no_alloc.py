@@ -68,3 +68,51 @@ def test_noalloc_rejects_oversize():
     c = cfg.to_c()
     st = lib.discos_cell_list_noalloc(ctypes.byref(c), None, (1 << 20) + 1, None, None, None, None)
     assert st == _lib.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_many_scan_tiles_then_fewer_cells(prec):
+    """32,768 list cells (a 64^3 channel, cutoff 2): the scan runs over 32
+    tiles of 1024 counts, so the tile sums kept in the static array take part;
+    then a call with 512 cells must not see the first call's leftovers."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2204_14167_gb300 as dg
+    from paper_2204_14167_gb300 import presets, synth, _lib
+    lib = _lib.load()
+    dt = torch.float64 if prec == dg.FP64 else torch.float32
+    for dims, psi, n in (((64, 64, 64), 2.0, 5001), ((32, 32, 32), 4.0, 777)):
+        cfg, rec = presets.dry_channel_32()
+        cfg.Nx, cfg.Ny, cfg.Nz = dims
+        cfg.psi = psi
+        cfg.lj_sigma, cfg.lj_rc = [[1.0]], [[1.1]]
+        cfg.precision = prec
+        cfg.max_ions = n
+        h = dg.Discos(cfg)
+        pos, q, sp = synth.ions(cfg.dims, n // 2, n - n // 2, 11, 0.05, 0.0)
+        x = torch.tensor(pos, dtype=dt, device="cuda").contiguous()
+        ref_start, ref_perm = h.cell_list(x)
+        torch.cuda.synchronize()
+        start, perm = _noalloc(lib, cfg, x)
+        assert len(start) - 1 == (dims[0] // int(psi)) * (dims[1] // int(psi)) * (dims[2] // int(psi))
+        assert np.array_equal(start, ref_start.cpu().numpy())
+        assert np.array_equal(perm, ref_perm.cpu().numpy())
+
+
+def test_noalloc_nonfinite_positions_return_quickly():
+    """Ions at NaN all land in one list cell; the binning flags them and the
+    per-cell sort stands down instead of going quadratic.  The call returns
+    and the list still holds every ion exactly once."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import time
+    from paper_2204_14167_gb300 import presets, _lib
+    lib = _lib.load()
+    cfg, rec = presets.dry_channel_32()
+    cfg.precision = 1
+    N = 200000
+    x = torch.full((3, N), float("nan"), dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    start, perm = _noalloc(lib, cfg, x)
+    assert time.perf_counter() - t0 < 30.0
+    assert start[-1] == N and np.array_equal(np.sort(perm), np.arange(N))
