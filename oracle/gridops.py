@@ -215,6 +215,21 @@ def spread_force(kernel, pos, F, dims, slip=(False, False)):
     return fx, fy, fz
 
 
+def spread_force_species(kernels, species, pos, F, dims, slip=(False, False)):
+    """S^hy F with a hydrodynamic kernel per species (App. B: one kernel for
+    the cations, another for the anions, on one grid): every ion spreads with
+    its own species' kernel, and the grid holds the sum."""
+    Nx, Ny, Nz = dims
+    species = np.asarray(species)
+    out = (np.zeros((Nz, Ny, Nx)), np.zeros((Nz, Ny + 1, Nx)), np.zeros((Nz, Ny, Nx)))
+    for s, kernel in enumerate(kernels):
+        m = species == s
+        if m.any():
+            part = spread_force(kernel, pos[:, m], F[:, m], dims, slip)
+            out = tuple(a + b for a, b in zip(out, part))
+    return out
+
+
 def interp_velocity(kernel, pos, u, v, w, slip=(False, False)):
     """V = J^hy v (Eq. kernel1) with ghost fill from the wall conditions:
     tangential ghosts are the negated mirror values at a no-slip wall and the
@@ -230,3 +245,15 @@ def interp_velocity(kernel, pos, u, v, w, slip=(False, False)):
     Vy = interpolate(kernel, pos, ve, y0v, (0.5, 0.0, 0.5))
     Vz = interpolate(kernel, pos, we, y0, (0.5, 0.5, 0.0))
     return np.stack([Vx, Vy, Vz])
+
+
+def interp_velocity_species(kernels, species, pos, u, v, w, slip=(False, False)):
+    """J^hy v with a hydrodynamic kernel per species (App. B): every ion
+    interpolates with its own species' kernel."""
+    species = np.asarray(species)
+    V = np.zeros((3, pos.shape[1]))
+    for s, kernel in enumerate(kernels):
+        m = species == s
+        if m.any():
+            V[:, m] = interp_velocity(kernel, pos[:, m], u, v, w, slip)
+    return V

@@ -9,6 +9,8 @@ eps = 1/(4 pi l_B)):
   fp_table; lj_sigma/lj_xi/lj_rc [ns][ns]; wall_sigma/wall_xi/wall_rc [ns];
   wall_type; E_ext (3,); gamma_coef [ns][2][2][7]; D_tot, D_wet [ns];
   wet, drift (bools); seed; slip (bottom, top) hydrodynamic slip walls;
+  kernel_hy_species: None, or a list of per-species hydrodynamic kernels
+  that replaces kernel_hy (App. B);
   strip (x0, x1, phi_total) or None.
 
 Stage 1: rho = S^es q, Poisson (Eq. poisson).  Stage 2: E^P = J^es(-grad phi)
@@ -88,13 +90,33 @@ def dry_step(p, pos, q, species, step, pair_dtype=np.float64, replica=0):
     return new, F, counts
 
 
-def fluid_forcing(p, pos, F, step):
+def spread_hy(p, pos, F, species):
+    """S^hy F with the run's hydrodynamic kernel, or each species' own."""
+    slip = p.get('slip', (False, False))
+    ks = p.get('kernel_hy_species')
+    if ks is None:
+        return gridops.spread_force(p['kernel_hy'], pos, F, p['dims'], slip)
+    return gridops.spread_force_species(ks, species, pos, F, p['dims'], slip)
+
+
+def interp_hy(p, pos, u, v, w, species):
+    """J^hy v with the run's hydrodynamic kernel, or each species' own."""
+    slip = p.get('slip', (False, False))
+    ks = p.get('kernel_hy_species')
+    if ks is None:
+        return gridops.interp_velocity(p['kernel_hy'], pos, u, v, w, slip)
+    return gridops.interp_velocity_species(ks, species, pos, u, v, w, slip)
+
+
+def fluid_forcing(p, pos, F, step, species=None):
     """f = S^hy F + f_th + stochastic stress (each optional by flags)."""
     dims = p['dims']
     slip = p.get('slip', (False, False))
-    fx, fy, fz = gridops.spread_force(p['kernel_hy'], pos, F, dims, slip)
+    fx, fy, fz = spread_hy(p, pos, F, species)
     if p.get('drift', True) and p['kT'] > 0:
-        tx, ty, tz = stokes.rfd_forcing(p['kernel_hy'], pos, dims, p['kT'], step, 0, p['seed'], slip=slip)
+        ks = p.get('kernel_hy_species')
+        tx, ty, tz = stokes.rfd_forcing(p['kernel_hy'] if ks is None else ks, pos, dims, p['kT'], step, 0,
+                                        p['seed'], slip=slip, species=None if ks is None else species)
         fx, fy, fz = fx + tx, fy + ty, fz + tz
     if p['kT'] > 0:
         nx, ny, nz = stokes.noise_forcing(dims, p['eta'], p['kT'], p['dt'], step, 0, p['seed'], slip)
@@ -113,12 +135,12 @@ def wet_increment(p, pos, species, F, step):
     false the RFD term is left out and the update is single stage (V = J(x) v).
     Returns (increment (3, N), fluid fields dict)."""
     slip = p.get('slip', (False, False))
-    fx, fy, fz = fluid_forcing(p, pos, F, step)
+    fx, fy, fz = fluid_forcing(p, pos, F, step, species)
     u, v, w, pr = stokes.solve(fx, fy, fz, p['eta'], slip=slip)
-    V1 = gridops.interp_velocity(p['kernel_hy'], pos, u, v, w, slip)
+    V1 = interp_hy(p, pos, u, v, w, species)
     if p.get('drift', True):
         xs = pos + 0.5 * p['dt'] * V1
-        V = gridops.interp_velocity(p['kernel_hy'], xs, u, v, w, slip)
+        V = interp_hy(p, xs, u, v, w, species)
     else:
         V = V1
     inc = p['dt'] * V + dry_increment(p, pos, species, F, step)

@@ -22,13 +22,14 @@ replica, tag): tag 3 gives (Zxx, Zyy, Zzz, Zxy), tag 4 gives (Zxz, Zyz, -, -).
 
 Thermal forcing, Eq. thermforce, by random finite differences (only cited;
 reading): f_th = (kT/delta) [S(x + delta W/2) W - S(x - delta W/2) W] with W
-from Philox tag 2 per ion and delta = 1e-4.
+from Philox tag 2 per ion and delta = 1e-4 (1e-6 for the ES kernel: see
+rfd_forcing).
 """
 import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from . import gridops, philox
+from . import gridops, kernels, philox
 
 
 def _ops(dims, slip=(False, False)):
@@ -208,10 +209,30 @@ def noise_forcing(dims, eta, kT, dt, step, replica, seed, slip=(False, False)):
     return amp * dx, amp * dy, amp * dz
 
 
-def rfd_forcing(kernel, pos, dims, kT, step, replica, seed, delta=1e-4, first_index=0, slip=(False, False)):
-    """Thermal forcing f_th by random finite differences (reading above)."""
+def rfd_forcing(kernel, pos, dims, kT, step, replica, seed, delta=None, first_index=0, slip=(False, False),
+                species=None):
+    """Thermal forcing f_th by random finite differences (reading above).
+    With species given, `kernel` is a list of per-species kernels and every
+    ion spreads with its own (App. B); the draws W stay keyed by ion index.
+
+    The RFD is read as its delta -> 0 limit.  delta = 1e-4 reaches it to
+    O(delta^2) for the Peskin kernels, whose first derivative is continuous.
+    The ES kernel (Eq. eskernel) drops from exp(-beta) to 0 at the edge of
+    its support, and a finite difference that straddles the edge picks up
+    that jump divided by delta; for ES kernels delta = 1e-6 (in double: the
+    rounding error of the difference stays near 1e-10 relative), which keeps
+    the stencil points of a few hundred ions clear of the edge."""
+    ks = kernel if isinstance(kernel, (list, tuple)) else [kernel]
+    if delta is None:
+        delta = 1e-6 if any(k.kind == kernels.ES for k in ks) else 1e-4
     N = pos.shape[1]
     W = philox.ion_normals(N, step, replica, philox.TAG_RFD, seed, first_index)
-    plus = gridops.spread_force(kernel, pos + 0.5 * delta * W, W, dims, slip)
-    minus = gridops.spread_force(kernel, pos - 0.5 * delta * W, W, dims, slip)
+    if species is None:
+        def spread(x):
+            return gridops.spread_force(kernel, x, W, dims, slip)
+    else:
+        def spread(x):
+            return gridops.spread_force_species(kernel, species, x, W, dims, slip)
+    plus = spread(pos + 0.5 * delta * W)
+    minus = spread(pos - 0.5 * delta * W)
     return tuple((kT / delta) * (a - b) for a, b in zip(plus, minus))

@@ -17,7 +17,9 @@ def oracle_params(cfg):
         E_ext=tuple(cfg.E_ext), gamma_coef=cfg.gamma_coef, D_tot=cfg.D_tot, D_wet=cfg.D_wet,
         wet=bool(cfg.wet), drift=bool(cfg.drift), seed=cfg.seed,
         strip=(float(cfg.strip_x[0]), float(cfg.strip_x[1]), float(cfg.strip_phi)) if cfg.strip else None,
-        slip=(bool(cfg.bc_hy[0]), bool(cfg.bc_hy[1])))
+        slip=(bool(cfg.bc_hy[0]), bool(cfg.bc_hy[1])),
+        kernel_hy_species=([okernels.Kernel(cfg.kernel_hy_s[s], cfg.hy_w_s[s], cfg.hy_beta_s[s])
+                            for s in range(cfg.nspecies)] if cfg.hy_species else None))
 
 
 def rel_l2(a, b):

@@ -26,7 +26,8 @@ from oracle import gridops, integrate, kernels, mobility, particles, stokes
 
 
 # ------------------------------------------------------------------ RFD
-@pytest.mark.parametrize("kind,pos0", [(kernels.PESKIN4, (3.3, 1.7, 4.1)), (kernels.PESKIN6, (2.6, 6.2, 5.45))])
+@pytest.mark.parametrize("kind,pos0", [(kernels.PESKIN4, (3.3, 1.7, 4.1)), (kernels.PESKIN6, (2.6, 6.2, 5.45)),
+                                      ((kernels.ES, 7, 7.0), (3.3, 1.7, 4.1))])
 def test_rfd_mean_is_kT_div_S(kind, pos0):
     """E_W[f_th] = kT sum_c d/dx_c (S e_c)(x): the mean of Eq. thermforce's
     random finite difference over many directions W (one per ion copy, from
@@ -34,7 +35,7 @@ def test_rfd_mean_is_kT_div_S(kind, pos0):
     force along each axis.  Near a wall, so the image terms take part."""
     dims = (8, 8, 8)
     kT = 1.7
-    kern = kernels.Kernel(kind)
+    kern = kernels.Kernel(*kind) if isinstance(kind, tuple) else kernels.Kernel(kind)
     M = 120000
     pos = np.tile(np.asarray(pos0, dtype=np.float64)[:, None], (1, M))
     fth = stokes.rfd_forcing(kern, pos, dims, kT, 3, 0, 20220428)
