@@ -531,7 +531,10 @@ def run_profile(args):
     cfg, rec = getattr(presets, args.workload)(dg.MIXED)
     pos, q, sp = synth.ions(cfg.dims, rec["n_pos"], rec["n_neg"], rec["seed"], rec["ymargin"], rec["min_sep"])
     h = dg.Discos(cfg)
-    h.tune_transforms()
+    if args.transform_shape:
+        h.set_transform_shape(*[int(v) for v in args.transform_shape.split(",")])
+    else:
+        h.tune_transforms()
     x = torch.tensor(pos, dtype=torch.float32, device="cuda").contiguous()
     qd = torch.tensor(q, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
@@ -598,14 +601,17 @@ def algorithmic_bytes(family, cfg, N):
         return (G * 4 + G // Nx * (Nx // 2 + 1) * 8 + Gf * 4 + Gf // Nx * (Nx // 2 + 1) * 8) // 2
     if family == "noise":
         return Gf * 4
-    if family == "interp_v":      # 3 components x w^3 face values + position in, velocity out
-        return N * (3 * w ** 3 * 4 + 24)
-    if family == "interp_e":
-        return N * ((we + 1) ** 3 * 4 + 28 + 12)
-    if family == "spread_force":  # zero-fill skipped in the step (noise initialises the grid)
-        return N * (3 * w ** 3 * 4 * 2 + 24)
-    if family == "spread_charge":
-        return G * 4 + N * (we ** 3 * 4 * 2 + 16)
+    # gathers and scatters: each grid value read (or read and written) once,
+    # plus the per-ion data; a stencil point shared by several ions is
+    # counted once (the rest is L2 reuse, not DRAM traffic)
+    if family == "interp_v":      # velocity grid in; position, index in; velocity out
+        return Gf * 4 + N * (12 + 4 + 12)
+    if family == "interp_e":      # potential in; position, charge, near-field force, index in; force out
+        return G * 4 + N * (12 + 4 + 12 + 4 + 12)
+    if family == "spread_force":  # accumulates into the noise-initialised forcing: read and write it
+        return 2 * Gf * 4 + N * (12 + 12 + 4 + 4)
+    if family == "spread_charge":  # density written; position and charge in
+        return G * 4 + N * 16
     if family == "near_field":
         return N * (16 + 12 + 12)
     if family == "cell_list":
@@ -645,6 +651,8 @@ def main():
                     help="run only batched-replica steps (for ncu)")
     ap.add_argument("--profile", action="store_true",
                     help="only W warm-up steps and K steps of the workload (for ncu), no timing output")
+    ap.add_argument("--transform-shape", default="",
+                    help="with --profile: x pairs, x threads, z tile (as tuned by the bench) instead of tuning")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

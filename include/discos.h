@@ -119,6 +119,18 @@ typedef struct discos_config {
      viscous operator, no stochastic stress on the wall edges).  At most one
      slip wall: with two, uniform flow along the walls is undamped. */
   int bc_hy[2];
+  /* Hydrodynamic kernel per species (App. B: on one hydrodynamic grid the
+     cations spread and interpolate with the ES kernel of w = 7, beta = 7 and
+     the anions with w = 4, beta = 8).  hy_species = 1: species s uses
+     (kernel_hy_s[s], hy_w_s[s], hy_beta_s[s]) in S^hy, J^hy and the thermal
+     forcing instead of (kernel_hy, es_w[1], es_beta[1]); force spreading and
+     velocity interpolation then take the species of each ion
+     (discos_spread_species, discos_interpolate_species; the calls without
+     species treat every ion as species 0). */
+  int hy_species;
+  int kernel_hy_s[DISCOS_MAX_SPECIES];
+  int hy_w_s[DISCOS_MAX_SPECIES];
+  double hy_beta_s[DISCOS_MAX_SPECIES];
 } discos_config;
 
 typedef struct discos_handle discos_handle;
@@ -174,6 +186,14 @@ discos_status discos_probe_read(discos_handle* h, double* total_ms, int* launche
 discos_status discos_spread(discos_handle* h, const void* x, const void* val, int N, int which,
                             void* grid, void* stream);
 
+/* discos_spread with the species of each ion (int32 [N], values in
+ * [0, nspecies); may be NULL = all species 0): with cfg.hy_species = 1,
+ * DISCOS_SPREAD_FORCE spreads every ion with its own species' hydrodynamic
+ * kernel (App. B); otherwise identical to discos_spread.  Species outside
+ * [0, nspecies) are not spread (no error is raised on the device). */
+discos_status discos_spread_species(discos_handle* h, const void* x, const void* val, const int* species, int N,
+                                    int which, void* grid, void* stream);
+
 /* Poisson solve -eps lap_h phi = rho (Eq. poisson) with the wall conditions
  * of Eqs. esbc1 / esbc3, periodic in x and z: DFTs in x and z and a double
  * precision tridiagonal solve per (kx, kz) mode in y (with a metal strip,
@@ -198,6 +218,13 @@ discos_status discos_solve_stokes(discos_handle* h, const void* f, void* v, void
  * which = DISCOS_INTERP_VELOCITY: grid = u|v|w; out[3][N] = J^hy v. */
 discos_status discos_interpolate(discos_handle* h, const void* x, int N, int which,
                                  const void* grid, void* out, void* stream);
+
+/* discos_interpolate with the species of each ion (as in
+ * discos_spread_species): with cfg.hy_species = 1, DISCOS_INTERP_VELOCITY
+ * interpolates every ion with its own species' hydrodynamic kernel; out
+ * entries of ions with a species outside [0, nspecies) are left untouched. */
+discos_status discos_interpolate_species(discos_handle* h, const void* x, const int* species, int N, int which,
+                                         const void* grid, void* out, void* stream);
 
 /* Cell list of Sec. II.B.1's neighbour sets: list cells of k grid cells per
  * axis (k = ceil(max(psi, largest LJ cutoff))), cell = min(floor(x) div k,
@@ -349,8 +376,10 @@ discos_status discos_energy_backward(discos_handle* h, const void* x, const void
 /* The device fault word.  Kernels that move ions set bit 0 when a new
  * position is not finite and bit 1 when an ion ends outside the channel (a
  * displacement larger than the channel); the step sets bit 2 for a
- * non-neutral channel between two Neumann walls.  None stops the kernels,
- * whose indexing stays in bounds for any position.  discos_step copies the
+ * non-neutral channel between two Neumann walls; a kernel whose bounded wait
+ * on an asynchronous bulk copy ran out sets bit 3 (its results are then
+ * incomplete).  None stops the other kernels, whose indexing stays in bounds
+ * for any position.  discos_step copies the
  * word to the host behind its steps, and the next discos_step call returns
  * DISCOS_ERR_NOT_NEUTRAL (bit 2) or DISCOS_ERR_DEVICE_FAULT, before
  * enqueueing anything, once that copy shows a set bit.  discos_fault returns the word (sync != 0: read now, waiting for
@@ -382,18 +411,24 @@ discos_status discos_refine_history_stokes(discos_handle* h, double* rel, int* n
 
 /* Launch-shape autotuner of the x and z transforms (used by every Poisson
  * and Stokes solve of the handle): times each candidate shape (x: 128 to
- * 2048 grid values per block, i.e. 1..2048/Nx row pairs; z: 1..16 columns
- * per block within the shared-memory limit) on the handle's own buffers at
- * the Poisson sizes, keeps the fastest, and returns it (out pointers may be
- * NULL; ms[2] = the x and z times per launch).  Overwrites the handle's
- * potential and spectrum workspace; blocks until done. */
+ * 2048 grid values per block, i.e. 1..2048/Nx row pairs, and, for Nx >= 32,
+ * the bulk-staged persistent kernel, reported as fx_pairs = 0; z: 4..16
+ * columns per block in single precision, 2..16 in double, within the
+ * shared-memory limit) on the handle's own
+ * buffers at the Poisson sizes, keeps the fastest, and returns it (out
+ * pointers may be NULL; ms[2] = the x and z times per launch).  Overwrites
+ * the handle's potential and spectrum workspace; blocks until done.  A new
+ * handle starts with the staged x kernel (Nx >= 32) and 8 z columns. */
 discos_status discos_tune_transforms(discos_handle* h, int* fx_pairs, int* fx_threads, int* fz_tile,
                                      float* ms, void* stream);
 
 /* Sets the transform launch shape directly: fx_pairs row pairs per x block
  * (fx_pairs * Nx <= 2048, within 48 KB of shared memory), fx_threads (a
- * multiple of 32), fz_tile columns per z block (a power of two).
- * Errors: INVALID_ARG outside those limits. */
+ * multiple of 32), fz_tile columns per z block (a power of two); fx_pairs = 0
+ * selects the bulk-staged persistent x kernel (Nx >= 32; fx_threads is then
+ * ignored).  The staged kernel reads and writes whole rows with bulk copies
+ * and needs 16-byte aligned grids: a caller's grid that is not falls back to
+ * the per-row kernel.  Errors: INVALID_ARG outside those limits. */
 discos_status discos_set_transform_shape(discos_handle* h, int fx_pairs, int fx_threads, int fz_tile);
 
 /* Host-only (no GPU needed): the F^P pair-force table that discos_create

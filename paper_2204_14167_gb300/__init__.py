@@ -67,6 +67,12 @@ class RunConfig:
     strip_phi: float = 0.0
     # hydrodynamic wall conditions (bottom, top): HY_NOSLIP or HY_SLIP
     bc_hy: tuple = (0, 0)
+    # hydrodynamic kernel per species (App. B): with hy_species, species s
+    # spreads and interpolates with (kernel_hy_s[s], hy_w_s[s], hy_beta_s[s])
+    hy_species: bool = False
+    kernel_hy_s: list = field(default_factory=lambda: [KERNEL_PESKIN4])
+    hy_w_s: list = field(default_factory=lambda: [4])
+    hy_beta_s: list = field(default_factory=lambda: [0.0])
 
     @property
     def dims(self):
@@ -112,6 +118,12 @@ class RunConfig:
         c.strip_x[0], c.strip_x[1] = float(self.strip_x[0]), float(self.strip_x[1])
         c.strip_phi = float(self.strip_phi)
         c.bc_hy[0], c.bc_hy[1] = int(self.bc_hy[0]), int(self.bc_hy[1])
+        c.hy_species = int(bool(self.hy_species))
+        if self.hy_species:
+            for a in range(self.nspecies):
+                c.kernel_hy_s[a] = int(self.kernel_hy_s[a])
+                c.hy_w_s[a] = int(self.hy_w_s[a])
+                c.hy_beta_s[a] = float(self.hy_beta_s[a])
         return c
 
 
@@ -216,12 +228,17 @@ class Discos:
         _lib.check(self._lib.discos_spread(self._h, _ptr(x), _ptr(q), N, SPREAD_CHARGE, _ptr(rho), _stream(stream)))
         return rho
 
-    def spread_force(self, x, F, out=None, stream=None):
+    def spread_force(self, x, F, out=None, stream=None, species=None):
+        """S^hy F; with species (int32 (N,)) and a per-species kernel run,
+        each ion spreads with its own species' kernel."""
+        import torch
         N = self._check_ions(x)
         self._need(F, 3 * N, self.dtype, "F")
         self._need(out, self._Gf(), self.dtype, "out")
+        self._need(species, N, torch.int32, "species")
         f = self.empty_grid("mac") if out is None else out
-        _lib.check(self._lib.discos_spread(self._h, _ptr(x), _ptr(F), N, SPREAD_FORCE, _ptr(f), _stream(stream)))
+        _lib.check(self._lib.discos_spread_species(self._h, _ptr(x), _ptr(F), _ptr(species), N, SPREAD_FORCE,
+                                                   _ptr(f), _stream(stream)))
         return f
 
     def solve_poisson(self, rho, out=None, stream=None):
@@ -248,13 +265,16 @@ class Discos:
                                                 _stream(stream)))
         return out
 
-    def interpolate_velocity(self, x, v, stream=None):
+    def interpolate_velocity(self, x, v, stream=None, species=None):
+        """J^hy v; with species (int32 (N,)) and a per-species kernel run,
+        each ion interpolates with its own species' kernel."""
         import torch
         N = self._check_ions(x)
         self._need(v, self._Gf(), self.dtype, "v")
-        out = torch.empty((3, N), dtype=self.dtype, device=self.device)
-        _lib.check(self._lib.discos_interpolate(self._h, _ptr(x), N, INTERP_VELOCITY, _ptr(v), _ptr(out),
-                                                _stream(stream)))
+        self._need(species, N, torch.int32, "species")
+        out = torch.zeros((3, N), dtype=self.dtype, device=self.device)
+        _lib.check(self._lib.discos_interpolate_species(self._h, _ptr(x), _ptr(species), N, INTERP_VELOCITY,
+                                                        _ptr(v), _ptr(out), _stream(stream)))
         return out
 
     def cell_list(self, x, stream=None):

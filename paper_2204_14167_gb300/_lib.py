@@ -53,6 +53,10 @@ class Config(ctypes.Structure):
         ("strip_x", D * 2),
         ("strip_phi", D),
         ("bc_hy", ctypes.c_int * 2),
+        ("hy_species", ctypes.c_int),
+        ("kernel_hy_s", ctypes.c_int * MAX_SPECIES),
+        ("hy_w_s", ctypes.c_int * MAX_SPECIES),
+        ("hy_beta_s", D * MAX_SPECIES),
     ]
 
 
@@ -80,7 +84,7 @@ EXPORTS = [
     "discos_probe", "discos_probe_read", "discos_energy", "discos_energy_backward",
     "discos_step_batched", "discos_tune_batched", "discos_set_batched_shape", "discos_refine_history",
     "discos_fault", "discos_diagnostics", "discos_tune_transforms", "discos_set_transform_shape",
-    "discos_refine_history_stokes",
+    "discos_refine_history_stokes", "discos_spread_species", "discos_interpolate_species",
 ]
 PROBE_FAMILIES = ["cell_list", "near_field", "noise", "spread_charge", "fft_x", "fft_z", "poisson_y", "interp_e",
                   "spread_force", "stokes_y", "interp_v", "update"]
@@ -102,9 +106,11 @@ def load():
     lib.discos_destroy.argtypes = [vp]
     lib.discos_last_error.restype = ctypes.c_char_p
     lib.discos_spread.argtypes = [vp, vp, vp, i32, i32, vp, vp]
+    lib.discos_spread_species.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp]
     lib.discos_solve_poisson.argtypes = [vp, vp, vp, vp]
     lib.discos_solve_stokes.argtypes = [vp, vp, vp, vp, vp]
     lib.discos_interpolate.argtypes = [vp, vp, i32, i32, vp, vp, vp]
+    lib.discos_interpolate_species.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp]
     lib.discos_cell_list.argtypes = [vp, vp, i32, vp, vp, ctypes.POINTER(i32), vp]
     lib.discos_near_field.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp]
     lib.discos_forces.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp]

@@ -182,11 +182,17 @@ void upload_stokes_factors(discos_handle* h) {
   cudaMemcpy(W.st_ci, ci.data(), sizeof(double) * ci.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(W.st_mc, mc.data(), sizeof(double) * mc.size(), cudaMemcpyHostToDevice);
   if (h->mixed) {
-    auto up = [](float* dst, const std::vector<double>& v) {
-      std::vector<float> f(v.begin(), v.end());
+    // single-precision copies for the sweeps, which read the factors row by
+    // row across modes: [Ny][M] (the mode constants stay [M][5])
+    auto up_t = [&](float* dst, const std::vector<double>& v) {
+      std::vector<float> f(v.size());
+      for (size_t m = 0; m < M; ++m)
+        for (int j = 0; j < Ny; ++j) f[(size_t)j * M + m] = (float)v[m * Ny + j];
       cudaMemcpy(dst, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice);
     };
-    up(W.st_l1f, l1); up(W.st_l2f, l2); up(W.st_dif, di); up(W.st_cif, ci); up(W.st_mcf, mc);
+    up_t(W.st_l1f, l1); up_t(W.st_l2f, l2); up_t(W.st_dif, di); up_t(W.st_cif, ci);
+    std::vector<float> mcf(mc.begin(), mc.end());
+    cudaMemcpy(W.st_mcf, mcf.data(), sizeof(float) * mcf.size(), cudaMemcpyHostToDevice);
   }
 }
 
@@ -302,7 +308,7 @@ void setup_strip(discos_handle* h, std::vector<double>& add0, std::vector<double
 void free_workspace(discos_handle* h) {
   free_batch(h);
   Workspace& W = h->W;
-  void* ptrs[] = {W.phi, W.spec, W.fgrid, W.piv64, W.piv32, W.tw_x, W.tw_z, W.fptab, W.cell_of, W.counts, W.fill,
+  void* ptrs[] = {W.phi, W.spec, W.fgrid, W.piv64, W.piv32, W.piv32t, W.tw_x, W.tw_z, W.fptab, W.cell_of, W.counts, W.fill,
                   W.cell_start, W.perm, W.tile_sums, W.xs, W.qs, W.sps, W.xq, W.F, W.xstar, W.V,
                   W.st_l1, W.st_l2, W.st_di, W.st_ci, W.st_mc,
                   W.lo_modes, W.is_lo, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf, W.Fn, W.edata, W.rref, W.rres, W.rnorm,
@@ -345,14 +351,16 @@ discos_status check_neutral_sync(discos_handle* h, const T* v, size_t n, cudaStr
 
 // The single-operation entry points work on the ions in the caller's order.
 template <typename T>
-cudaError_t spread_impl(discos_handle* h, const T* x, const T* val, int N, int which, T* grid, cudaStream_t s) {
+cudaError_t spread_impl(discos_handle* h, const T* x, const T* val, const int* species, int N, int which, T* grid,
+                        cudaStream_t s) {
   if (which == DISCOS_SPREAD_CHARGE) return launch_spread_charge<T>(h->P, x, val, N, grid, s);
-  return launch_spread_force<T>(h->P, x, val, N, grid, 0, false, s, false, nullptr, false);
+  return launch_spread_force<T>(h->P, x, val, N, grid, 0, false, s, false, nullptr, false, species);
 }
 
 template <typename T>
-cudaError_t interp_impl(discos_handle* h, const T* x, int N, int which, const T* grid, T* out, cudaStream_t s) {
-  if (which == DISCOS_INTERP_VELOCITY) return launch_interp_velocity<T>(h->P, x, N, grid, out, s, nullptr);
+cudaError_t interp_impl(discos_handle* h, const T* x, const int* species, int N, int which, const T* grid, T* out,
+                        cudaStream_t s) {
+  if (which == DISCOS_INTERP_VELOCITY) return launch_interp_velocity<T>(h->P, x, N, grid, out, s, nullptr, species);
   return launch_interp_efield<T>(h->P, x, static_cast<const T*>(nullptr), N, grid, out, false, s,
                                  static_cast<const T*>(nullptr), nullptr);
 }
@@ -432,12 +440,12 @@ discos_status step_impl(discos_handle* h, T* x, const T* q, const int* species, 
     if (st != DISCOS_OK) return st;
     cudaError_t e = cudaSuccess;
     if (wet) {
-      e = launch_spread_force<T>(P, xsrt, F, N, fg, step, drift && thermal, s, true, W.perm, true);
+      e = launch_spread_force<T>(P, xsrt, F, N, fg, step, drift && thermal, s, true, W.perm, true, W.sps);
       if (e == cudaSuccess) e = launch_stokes<T>(P, W, fg, fg, nullptr, s);
-      if (e == cudaSuccess) e = launch_interp_velocity<T>(P, xsrt, N, fg, V, s, nullptr);
+      if (e == cudaSuccess) e = launch_interp_velocity<T>(P, xsrt, N, fg, V, s, nullptr, W.sps);
       if (drift) {
         if (e == cudaSuccess) e = launch_midpoint<T>(P, xsrt, V, N, xs, s);
-        if (e == cudaSuccess) e = launch_interp_velocity<T>(P, xs, N, fg, V, s, nullptr);
+        if (e == cudaSuccess) e = launch_interp_velocity<T>(P, xs, N, fg, V, s, nullptr, W.sps);
       }
       if (e == cudaSuccess) e = launch_dry_update<T>(P, x, W.sps, F, V, N, step, s, xsrt, W.perm);
     } else {
@@ -567,6 +575,16 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   int why = kernel_width(c.kernel_hy, c.es_w[1]);
   if (wes < 4 || wes > 7 || why < 4 || why > 7) return invalid("kernel must be PESKIN4, PESKIN6 or ES with width 4..7");
   if (wes > c.Ny - 2 || why > c.Ny - 2) return invalid("kernel wider than the channel");
+  if (c.hy_species != 0 && c.hy_species != 1) return invalid("hy_species must be 0 or 1");
+  if (c.hy_species) {
+    if (c.nspecies < 1 || c.nspecies > DISCOS_MAX_SPECIES) return invalid("nspecies must be 1..4");
+    for (int a = 0; a < c.nspecies; ++a) {
+      const int wa = kernel_width(c.kernel_hy_s[a], c.hy_w_s[a]);
+      if (wa < 4 || wa > 7) return invalid("per-species kernel must be PESKIN4, PESKIN6 or ES with width 4..7");
+      if (wa > c.Ny - 2) return invalid("per-species kernel wider than the channel");
+      if (c.kernel_hy_s[a] == DISCOS_KERNEL_ES && !(c.hy_beta_s[a] > 0.0)) return invalid("ES kernel beta must be positive");
+    }
+  }
   if (!(c.psi > 0.0) || c.n_tab < 2) return invalid("psi > 0 and n_tab >= 2 required");
   if (c.nspecies < 1 || c.nspecies > DISCOS_MAX_SPECIES) return invalid("nspecies must be 1..4");
   if (c.max_refine < 0 || c.max_refine > DISCOS_MAX_REFINE) return invalid("max_refine must be 0..DISCOS_MAX_REFINE");
@@ -619,6 +637,10 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
   P.slope[1] = 4.0 * M_PI * c.lB * c.surf_charge[1];
   P.kes = make_kernel(c.kernel_es, c.es_w[0], c.es_beta[0]);
   P.khy = make_kernel(c.kernel_hy, c.es_w[1], c.es_beta[1]);
+  P.hy_species = c.hy_species;
+  P.hy_filter = -1;
+  if (c.hy_species)
+    for (int a = 0; a < c.nspecies; ++a) P.khy_s[a] = make_kernel(c.kernel_hy_s[a], c.hy_w_s[a], c.hy_beta_s[a]);
   P.lB = c.lB; P.eta = c.eta; P.kT = c.kT; P.dt = c.dt; P.psi = c.psi;
   P.n_tab = c.n_tab;
   P.tab_scale = c.n_tab / c.psi;
@@ -645,6 +667,7 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
     const size_t elem = c.precision == DISCOS_MIXED ? 2 * sizeof(float) : 2 * sizeof(double);
     P.fx_pp = default_fx_pairs(c.Nx);
     P.fx_threads = 256;
+    P.fx_staged = c.Nx >= 32 ? 1 : 0;
     P.fz_tk = default_tile_z(c.Nz, elem);
   }
   {
@@ -755,6 +778,7 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
     W.is_lo = (unsigned char*)dalloc(h, modes, &ok);
     W.lo_modes = (int*)dalloc(h, sizeof(int) * modes, &ok);
     W.piv32 = (float*)dalloc(h, sizeof(float) * modes * c.Ny, &ok);
+    W.piv32t = (float*)dalloc(h, sizeof(float) * modes * c.Ny, &ok);
     if (c.wet) {
       W.st_l1f = (float*)dalloc(h, sizeof(float) * c.Ny * modes, &ok);
       W.st_l2f = (float*)dalloc(h, sizeof(float) * c.Ny * modes, &ok);
@@ -825,6 +849,11 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
         }
       W.n_lo = (int)list.size();
       std::vector<float> inv32(inv.begin(), inv.end());
+      // the single-precision sweeps read the pivots row by row across modes: [Ny][M]
+      std::vector<float> inv32t(inv.size());
+      for (size_t m = 0; m < modes; ++m)
+        for (int j = 0; j < c.Ny; ++j) inv32t[(size_t)j * modes + m] = (float)inv[m * c.Ny + j];
+      cudaMemcpy(W.piv32t, inv32t.data(), sizeof(float) * inv32t.size(), cudaMemcpyHostToDevice);
       cudaMemcpy(W.is_lo, lo.data(), lo.size(), cudaMemcpyHostToDevice);
       if (!list.empty()) cudaMemcpy(W.lo_modes, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice);
       cudaMemcpy(W.piv32, inv32.data(), sizeof(float) * inv32.size(), cudaMemcpyHostToDevice);
@@ -888,6 +917,11 @@ discos_status discos_destroy(discos_handle* h) {
 
 discos_status discos_spread(discos_handle* h, const void* x, const void* val, int N, int which, void* grid,
                             void* stream) {
+  return discos_spread_species(h, x, val, nullptr, N, which, grid, stream);
+}
+
+discos_status discos_spread_species(discos_handle* h, const void* x, const void* val, const int* species, int N,
+                                    int which, void* grid, void* stream) {
   ProbeScope probe_scope(h);
   discos_status st = check_n(h, N);
   if (st) return st;
@@ -895,8 +929,9 @@ discos_status discos_spread(discos_handle* h, const void* x, const void* val, in
   if (which != DISCOS_SPREAD_CHARGE && which != DISCOS_SPREAD_FORCE)
     return invalid("which must be DISCOS_SPREAD_CHARGE or DISCOS_SPREAD_FORCE");
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = h->mixed ? spread_impl<float>(h, (const float*)x, (const float*)val, N, which, (float*)grid, s)
-                           : spread_impl<double>(h, (const double*)x, (const double*)val, N, which, (double*)grid, s);
+  cudaError_t e = h->mixed
+      ? spread_impl<float>(h, (const float*)x, (const float*)val, species, N, which, (float*)grid, s)
+      : spread_impl<double>(h, (const double*)x, (const double*)val, species, N, which, (double*)grid, s);
   return cuda_status(e, "discos_spread");
 }
 
@@ -931,6 +966,11 @@ discos_status discos_solve_stokes(discos_handle* h, const void* f, void* v, void
 
 discos_status discos_interpolate(discos_handle* h, const void* x, int N, int which, const void* grid, void* out,
                                  void* stream) {
+  return discos_interpolate_species(h, x, nullptr, N, which, grid, out, stream);
+}
+
+discos_status discos_interpolate_species(discos_handle* h, const void* x, const int* species, int N, int which,
+                                         const void* grid, void* out, void* stream) {
   ProbeScope probe_scope(h);
   discos_status st = check_n(h, N);
   if (st) return st;
@@ -938,8 +978,9 @@ discos_status discos_interpolate(discos_handle* h, const void* x, int N, int whi
   if (which != DISCOS_INTERP_EFIELD && which != DISCOS_INTERP_VELOCITY)
     return invalid("which must be DISCOS_INTERP_EFIELD or DISCOS_INTERP_VELOCITY");
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = h->mixed ? interp_impl<float>(h, (const float*)x, N, which, (const float*)grid, (float*)out, s)
-                           : interp_impl<double>(h, (const double*)x, N, which, (const double*)grid, (double*)out, s);
+  cudaError_t e = h->mixed
+      ? interp_impl<float>(h, (const float*)x, species, N, which, (const float*)grid, (float*)out, s)
+      : interp_impl<double>(h, (const double*)x, species, N, which, (const double*)grid, (double*)out, s);
   return cuda_status(e, "discos_interpolate");
 }
 
@@ -1110,7 +1151,7 @@ discos_status discos_tune_transforms(discos_handle* h, int* fx_pairs, int* fx_th
   float best[2] = {0.f, 0.f};
   cudaError_t e = tune_transforms(h->P, h->W, h->mixed, (cudaStream_t)stream, best);
   if (e != cudaSuccess) return cuda_status(e, "discos_tune_transforms");
-  if (fx_pairs) *fx_pairs = h->P.fx_pp;
+  if (fx_pairs) *fx_pairs = h->P.fx_staged ? 0 : h->P.fx_pp;
   if (fx_threads) *fx_threads = h->P.fx_threads;
   if (fz_tile) *fz_tile = h->P.fz_tk;
   if (ms) { ms[0] = best[0]; ms[1] = best[1]; }
@@ -1121,6 +1162,14 @@ discos_status discos_set_transform_shape(discos_handle* h, int fx_pairs, int fx_
   if (!h) return invalid("null handle");
   const size_t elem = h->mixed ? 2 * sizeof(float) : 2 * sizeof(double);
   const int N = h->P.Nx;
+  if (fx_pairs == 0) {
+    if (N < 32) return invalid("the staged x transform (fx_pairs = 0) needs Nx >= 32");
+    if (fz_tile < 1 || (fz_tile & (fz_tile - 1)) || fz_tile > max_tile_z(h->P.Nz, elem))
+      return invalid("fz_tile: a power of two up to the shared-memory limit");
+    h->P.fx_staged = 1;
+    h->P.fz_tk = fz_tile;
+    return DISCOS_OK;
+  }
   if (fx_pairs < 1 || (size_t)fx_pairs * N > 2048 ||
       (2 * (size_t)fx_pairs * N + N / 2) * elem + 2 * (size_t)fx_pairs * elem > 48 * 1024)
     return invalid("fx_pairs: 1 .. 2048 / Nx row pairs within 48 KB of shared memory");
@@ -1129,6 +1178,7 @@ discos_status discos_set_transform_shape(discos_handle* h, int fx_pairs, int fx_
     return invalid("fz_tile: a power of two up to the shared-memory limit");
   h->P.fx_pp = fx_pairs;
   h->P.fx_threads = fx_threads;
+  h->P.fx_staged = 0;
   h->P.fz_tk = fz_tile;
   return DISCOS_OK;
 }

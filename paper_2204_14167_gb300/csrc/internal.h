@@ -34,6 +34,10 @@ struct Params {
   double phi_b[2];
   double slope[2];             // dphi/dy on Neumann walls (bottom, top)
   KernelParams kes, khy;
+  // hydrodynamic kernel per species (App. B): with hy_species, S^hy and J^hy run once per species s with
+  // khy = khy_s[s] and hy_filter = s (ions of other species skipped); hy_filter < 0 takes every ion
+  int hy_species, hy_filter;
+  KernelParams khy_s[DISCOS_MAX_SPECIES];
   double lB, eta, kT, dt, psi;
   int n_tab;
   double tab_scale;            // n_tab / psi
@@ -51,6 +55,7 @@ struct Params {
   uint64_t seed;
   int max_refine;              // residual refinement sweeps of the mixed Poisson solve
   int fx_pp, fx_threads, fz_tk;  // transform launch shapes (k_fft.cu; discos_tune_transforms)
+  int fx_staged;               // 1: bulk-staged persistent x transforms (fx_pp, fx_threads unused)
   // metal strip in the bottom wall (k_strip.cu): Dirichlet on the cell columns [strip_i0, strip_i1) with
   // phi_m(x) = strip_phi + E_ext[0] (x - strip_xc); strip_singular: the all-dielectric base operator is
   // singular (top wall Neumann); strip_walls: the sum of the base solve's wall terms over the grid
@@ -58,7 +63,8 @@ struct Params {
   int slip[2];                 // hydrodynamic slip walls (bottom, top): tangential images and ghosts +1, else -1
   double strip_phi, strip_xc, strip_walls;
   unsigned* fault;             // device fault word: bit 0 non-finite position, bit 1 escaped ion,
-                               // bit 2 a non-neutral channel between two Neumann walls
+                               // bit 2 a non-neutral channel between two Neumann walls,
+                               // bit 3 a bounded wait on a bulk copy ran out (bulk.cuh)
   double inv_D_dry[DISCOS_MAX_SPECIES], inv_kT;
   double inv_eta, inv_nxnz;    // 1 / eta (0 without a fluid), 1 / (Nx Nz): the transforms' normalisation
   PhysF f;
@@ -105,7 +111,8 @@ struct Workspace {
   void* spec = nullptr;        // 3 spectra [Nz][Ny+1][Px] complex real
   void* fgrid = nullptr;       // fx|fy|fz real
   double* piv64 = nullptr;     // Poisson Thomas reciprocal pivots [M][Ny]
-  float* piv32 = nullptr;      // single-precision copy (mixed path)
+  float* piv32 = nullptr;      // single-precision copy (mixed path; the batched replicas)
+  float* piv32t = nullptr;     // single-precision copy [Ny][M] (mixed path; the sweeps of k_ysolve.cu)
   void* tw_x = nullptr;        // twiddles exp(-2 pi i k / Nx), k < Nx/2
   void* tw_z = nullptr;        // twiddles exp(-2 pi i k / Nz), k < Nz/2
   void* fptab = nullptr;       // F^P table [n_tab + 1] real
@@ -136,7 +143,7 @@ struct Workspace {
   int n_lo = 0;
   int* lo_modes = nullptr;       // [n_lo] mode indices kz * Nxh + kx
   unsigned char* is_lo = nullptr;  // [M]
-  float* st_l1f = nullptr;       // single-precision copies of the Stokes factors
+  float* st_l1f = nullptr;       // single-precision copies of the Stokes factors, [Ny][M] (mc: [M][5])
   float* st_l2f = nullptr;
   float* st_dif = nullptr;
   float* st_cif = nullptr;
@@ -284,14 +291,33 @@ template <typename T> cudaError_t launch_scatter3(const T* src, const int* index
 // visit the ions in a scattered order (atomics of ions in cell order collide);
 // noise_index: the caller's index of each ion (the RFD noise key); out_index:
 // where each ion's result goes.
+// Runs f(Q) once with the run's hydrodynamic kernel (Q.hy_filter = -1: every
+// ion), or, with a kernel per species (App. B), once per species s with
+// Q.khy = that species' kernel and Q.hy_filter = s when the ions' species are
+// known; without them every ion counts as species 0.
+template <typename Fn>
+inline void for_each_hy_kernel(const Params& P, const int* species, Fn&& f) {
+  Params Q = P;
+  Q.hy_filter = -1;
+  if (!P.hy_species) { f(Q); return; }
+  if (!species) { Q.khy = P.khy_s[0]; f(Q); return; }
+  for (int s = 0; s < P.nspecies; ++s) {
+    Q.khy = P.khy_s[s];
+    Q.hy_filter = s;
+    f(Q);
+  }
+}
+
 template <typename T> cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, T* f,
                                                       int64_t step, bool rfd, cudaStream_t s, bool accumulate,
-                                                      const int* noise_index, bool decorrelate);
+                                                      const int* noise_index, bool decorrelate,
+                                                      const int* species = nullptr);
 template <typename T> cudaError_t launch_interp_efield(const Params& P, const T* x, const T* q, int N, const T* phi,
                                                        T* out, bool as_force, cudaStream_t s, const T* F_add,
                                                        const int* out_index);
 template <typename T> cudaError_t launch_interp_velocity(const Params& P, const T* x, int N, const T* v, T* out,
-                                                         cudaStream_t s, const int* out_index);
+                                                         cudaStream_t s, const int* out_index,
+                                                         const int* species = nullptr);
 template <typename T> cudaError_t launch_midpoint(const Params& P, const T* x, const T* V, int N, T* xstar,
                                                   cudaStream_t s);
 template <typename T> cudaError_t launch_fill_zero(T* p, size_t n, cudaStream_t s);

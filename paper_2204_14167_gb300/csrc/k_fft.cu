@@ -11,6 +11,7 @@
 #include <atomic>
 #include <type_traits>
 #include "internal.h"
+#include "bulk.cuh"
 
 namespace discos {
 
@@ -312,6 +313,234 @@ __global__ void k_irfft_x_w(const cplx<T>* __restrict__ in, int R, int Px, T* __
   }
 }
 
+
+
+// The twiddles that one lane of a 32 P-point row transform uses, loaded
+// once per thread by the persistent staged kernels (the per-row kernels read
+// them from the table each time): the register stages (W_N^(j N / 2h) in the
+// loop order of reg_dft), the inter-stage twiddles W_N^(lane bitrev(p)), and
+// one per lane stage of lane_dft.
+template <typename T, int P>
+struct LaneTwiddles {
+  static constexpr int NR = P > 1 ? P - 1 : 1;
+  cplx<T> r[NR], m[P], l[5];
+  __device__ __forceinline__ void load(const cplx<T>* __restrict__ tw, int lane, bool inverse) {
+    constexpr int N = 32 * P;
+    int k = 0;
+#pragma unroll
+    for (int half = P / 2; half >= 1; half >>= 1)
+#pragma unroll
+      for (int j = 1; j < half; ++j) r[k++] = twid(tw, j * (N / (2 * half)), N, inverse);
+#pragma unroll
+    for (int p = 0; p < P; ++p) m[p] = twid(tw, lane * brev_c<P>(p), N, inverse);
+    int st = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) l[st++] = twid(tw, (lane & (s - 1)) * (N / (2 * s)), N, inverse);
+  }
+};
+
+// reg_dft, lane twiddle, lane_dft with the twiddles in registers (G = 32).
+template <typename T, int P>
+__device__ __forceinline__ void row_dft(cplx<T> (&v)[P], const LaneTwiddles<T, P>& t, int lane) {
+  int k = 0;
+#pragma unroll
+  for (int half = P / 2; half >= 1; half >>= 1) {
+#pragma unroll
+    for (int i = 0; i < P; i += 2 * half) {
+#pragma unroll
+      for (int j = 0; j < half; ++j) {
+        const cplx<T> a = v[i + j], b = v[i + j + half];
+        v[i + j] = cadd(a, b);
+        const cplx<T> d = csub(a, b);
+        v[i + j + half] = j == 0 ? d : cmul(d, t.r[k + j - 1]);
+      }
+    }
+    k += half > 1 ? half - 1 : 0;
+  }
+#pragma unroll
+  for (int p = 1; p < P; ++p) v[p] = cmul(v[p], t.m[p]);
+  int st = 0;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1, ++st) {
+    const bool hi = (lane & s) != 0;
+    const cplx<T> w = t.l[st];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const cplx<T> u{__shfl_xor_sync(0xffffffffu, v[p].re, s), __shfl_xor_sync(0xffffffffu, v[p].im, s)};
+      v[p] = hi ? cmul(csub(u, v[p]), w) : cadd(v[p], u);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// Bulk-staged x transforms.  The rows of one transform launch lie back to
+// back in memory, so a chunk of C = 2 W rows (W warps, one row pair each) is
+// a single bulk copy into shared memory (the TMA engine's untiled form).  The
+// CTAs are persistent (as many as fit on the SMs) and walk the chunks with
+// the grid as stride, keeping XS_NB chunks in flight: while the warps
+// transform chunk i out of shared memory, the next XS_NB - 1 chunks stream
+// in.  The transform of a row pair is that of k_rfft_x_w / k_irfft_x_w.
+// Shared memory: XS_NB barriers (32 bytes), XS_NB chunk buffers, and the
+// per-warp real-pair scratch.
+constexpr int XS_NB = 3;
+
+// On a wait that ran out: flag it, let the copies still in flight land (each
+// wait again bounded), and leave.
+__device__ __forceinline__ void staged_abort(uint64_t* bar, int it, int nchunks, unsigned* fault) {
+  for (int j = it; j < it + XS_NB; ++j) {
+    const int cj = blockIdx.x + j * gridDim.x;
+    if (cj < nchunks) mbar_wait(&bar[j % XS_NB], (unsigned)((j / XS_NB) & 1));
+  }
+  if (threadIdx.x == 0 && fault) atomicOr(fault, FAULT_ASYNC_WAIT);
+}
+
+template <typename T, int P>
+__global__ void k_rfft_x_staged(const T* __restrict__ in, int R, int Px, cplx<T>* __restrict__ out, T scale,
+                                int Nyr, T add0, T add1, const cplx<T>* __restrict__ tw,
+                                const T* __restrict__ add0x, unsigned* __restrict__ fault) {
+  constexpr int N = 32 * P;
+  const int C = 2 * (blockDim.x >> 5);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  T* buf = reinterpret_cast<T*>(smem_raw + 32);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  cplx<T>* sz = reinterpret_cast<cplx<T>*>(buf + (size_t)XS_NB * C * N) + (size_t)wib * 32 * (P + 1);
+  const int nchunks = (R + C - 1) / C;
+  LaneTwiddles<T, P> twl;
+  twl.load(tw, lane, false);
+  auto load = [&](int c, int b) {
+    const int rows = min(C, R - c * C);
+    bulk_load(buf + (size_t)b * C * N, in + (size_t)c * C * N, (unsigned)((size_t)rows * N * sizeof(T)), &bar[b]);
+  };
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < XS_NB; ++b) mbar_init(&bar[b], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int b = 0; b < XS_NB; ++b)
+      if (blockIdx.x + b * (int)gridDim.x < nchunks) load(blockIdx.x + b * gridDim.x, b);
+  int it = 0;
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x, ++it) {
+    const int b = it % XS_NB;
+    const bool ok = mbar_wait(&bar[b], (unsigned)((it / XS_NB) & 1));
+    if (!__syncthreads_and(ok)) {
+      staged_abort(bar, it, nchunks, fault);
+      return;
+    }
+    const int ra = c * C + 2 * wib, rb = ra + 1;
+    if (ra < R) {
+      const bool hasb = rb < R;
+      const int ya = ra % Nyr, yb = rb % Nyr;
+      const T adda = (ya == 0 ? add0 : T(0)) + (ya == Nyr - 1 ? add1 : T(0));
+      const T addb = (yb == 0 ? add0 : T(0)) + (yb == Nyr - 1 ? add1 : T(0));
+      const T* pa = buf + (size_t)b * C * N + (size_t)(2 * wib) * N;
+      const T* pb = pa + N;
+      const bool xa = add0x && ya == 0, xb = add0x && yb == 0;
+      cplx<T> v[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const int n = lane + 32 * p;
+        v[p] = cplx<T>{scale * pa[n] + adda + (xa ? add0x[n] : T(0)),
+                       hasb ? scale * pb[n] + addb + (xb ? add0x[n] : T(0)) : T(0)};
+      }
+      row_dft<T, P>(v, twl, lane);
+      const int k1 = (int)(__brev((unsigned)lane) >> 27);
+#pragma unroll
+      for (int p = 0; p < P; ++p) sz[k1 * (P + 1) + brev_c<P>(p)] = v[p];
+      __syncwarp();
+      for (int k = lane; k <= N / 2; k += 32) {
+        const int kn = (N - k) & (N - 1);
+        const cplx<T> Zk = sz[(k / P) * (P + 1) + (k % P)];
+        const cplx<T> Zn = sz[(kn / P) * (P + 1) + (kn % P)];
+        out[(size_t)ra * Px + k] = cplx<T>{T(0.5) * (Zk.re + Zn.re), T(0.5) * (Zk.im - Zn.im)};
+        if (hasb) out[(size_t)rb * Px + k] = cplx<T>{T(0.5) * (Zk.im + Zn.im), T(-0.5) * (Zk.re - Zn.re)};
+      }
+    }
+    __syncthreads();   // every warp is done with buffer b (and with its scratch)
+    if (threadIdx.x == 0) {
+      const int cn = c + XS_NB * gridDim.x;
+      if (cn < nchunks) {
+        async_proxy_fence();
+        load(cn, b);
+      }
+    }
+  }
+}
+
+template <typename T, int P>
+__global__ void k_irfft_x_staged(const cplx<T>* __restrict__ in, int R, int Px, T* __restrict__ out, T scale,
+                                 const cplx<T>* __restrict__ tw, unsigned* __restrict__ fault) {
+  constexpr int N = 32 * P;
+  const int C = 2 * (blockDim.x >> 5);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw + 32);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  cplx<T>* sz = buf + (size_t)XS_NB * C * Px + (size_t)wib * 32 * (P + 1);
+  const int nchunks = (R + C - 1) / C;
+  LaneTwiddles<T, P> twl;
+  twl.load(tw, lane, true);
+  auto load = [&](int c, int b) {
+    const int rows = min(C, R - c * C);
+    bulk_load(buf + (size_t)b * C * Px, in + (size_t)c * C * Px, (unsigned)((size_t)rows * Px * sizeof(cplx<T>)),
+              &bar[b]);
+  };
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < XS_NB; ++b) mbar_init(&bar[b], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int b = 0; b < XS_NB; ++b)
+      if (blockIdx.x + b * (int)gridDim.x < nchunks) load(blockIdx.x + b * gridDim.x, b);
+  int it = 0;
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x, ++it) {
+    const int b = it % XS_NB;
+    const bool ok = mbar_wait(&bar[b], (unsigned)((it / XS_NB) & 1));
+    if (!__syncthreads_and(ok)) {
+      staged_abort(bar, it, nchunks, fault);
+      return;
+    }
+    const int ra = c * C + 2 * wib, rb = ra + 1;
+    if (ra < R) {
+      const bool hasb = rb < R;
+      const cplx<T>* ia = buf + (size_t)b * C * Px + (size_t)(2 * wib) * Px;
+      const cplx<T>* ib = ia + Px;
+      cplx<T> v[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const int k = lane + 32 * p;
+        const int kk = k <= N / 2 ? k : N - k;
+        cplx<T> A = ia[kk];
+        cplx<T> B = hasb ? ib[kk] : cplx<T>{T(0), T(0)};
+        if (k > N / 2) { A.im = -A.im; B.im = -B.im; }
+        v[p] = cplx<T>{A.re - B.im, A.im + B.re};      // Z = A + i B
+      }
+      row_dft<T, P>(v, twl, lane);
+      const int k1 = (int)(__brev((unsigned)lane) >> 27);
+#pragma unroll
+      for (int p = 0; p < P; ++p) sz[k1 * (P + 1) + brev_c<P>(p)] = v[p];
+      __syncwarp();
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const int n = lane + 32 * p;
+        const cplx<T> z = sz[(n / P) * (P + 1) + (n % P)];
+        out[(size_t)ra * N + n] = scale * z.re;
+        if (hasb) out[(size_t)rb * N + n] = scale * z.im;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int cn = c + XS_NB * gridDim.x;
+      if (cn < nchunks) {
+        async_proxy_fence();
+        load(cn, b);
+      }
+    }
+  }
+}
+
 // Complex transform along z, in place: 32 / G x-mode columns per warp, G
 // lanes per column (G = 8 for float: 4 columns x 8 bytes fill a 32-byte
 // sector per z row; G = 16 for double), M = Nz / G values per lane.
@@ -388,6 +617,83 @@ int x_warps_per_block(const Params& P) {
   return w;
 }
 
+
+// Staged x transforms: W warps per CTA so that a chunk (2 W rows) is about
+// 16 KB (1 <= W <= 8); as many CTAs as fit on the SMs, at most one per chunk.
+int staged_warps(size_t row_bytes) {
+  int w = (int)(8192 / row_bytes);
+  return w < 1 ? 1 : (w > 8 ? 8 : w);
+}
+
+// Persistent grid for kernel Kern with the given block and shared memory:
+// the opt-in shared-memory attribute is set once per device, and the CTAs
+// per SM come from the occupancy calculator.
+template <auto Kern>
+cudaError_t persistent_grid(int threads, size_t smem, int* grid) {
+  static std::atomic<unsigned long long> attr_done{0};
+  static int per_sm[64] = {0};
+  static int sms[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!(attr_done.load() & (1ull << dev))) {
+    e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[dev], Kern, threads, smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    attr_done.fetch_or(1ull << dev);
+  }
+  const int b = per_sm[dev] < 1 ? 1 : per_sm[dev];
+  *grid = b * (sms[dev] < 1 ? 1 : sms[dev]);
+  return cudaSuccess;
+}
+
+template <typename T, int PP>
+cudaError_t rfft_x_staged(const Params& P, const T* in, int R, cplx<T>* out, T scale, int Nyr, T add0, T add1,
+                          const cplx<T>* tw, const T* add0x, cudaStream_t s) {
+  constexpr int N = 32 * PP;
+  const int W = staged_warps(N * sizeof(T)), C = 2 * W;
+  const size_t sm = 32 + XS_NB * (size_t)C * N * sizeof(T) + (size_t)W * 32 * (PP + 1) * sizeof(cplx<T>);
+  int grid = 0;
+  cudaError_t e = persistent_grid<k_rfft_x_staged<T, PP>>(32 * W, sm, &grid);
+  if (e != cudaSuccess) return e;
+  const int nchunks = (R + C - 1) / C;
+  if (grid > nchunks) grid = nchunks;
+  k_rfft_x_staged<T, PP><<<grid, 32 * W, sm, s>>>(in, R, P.Px, out, scale, Nyr, add0, add1, tw, add0x, P.fault);
+  return cudaSuccess;
+}
+
+template <typename T, int PP>
+cudaError_t irfft_x_staged(const Params& P, const cplx<T>* in, int R, T* out, T scale, const cplx<T>* tw,
+                           cudaStream_t s) {
+  constexpr int N = 32 * PP;
+  const int W = staged_warps(P.Px * sizeof(cplx<T>)), C = 2 * W;
+  const size_t sm = 32 + XS_NB * (size_t)C * P.Px * sizeof(cplx<T>) + (size_t)W * 32 * (PP + 1) * sizeof(cplx<T>);
+  int grid = 0;
+  cudaError_t e = persistent_grid<k_irfft_x_staged<T, PP>>(32 * W, sm, &grid);
+  if (e != cudaSuccess) return e;
+  const int nchunks = (R + C - 1) / C;
+  if (grid > nchunks) grid = nchunks;
+  k_irfft_x_staged<T, PP><<<grid, 32 * W, sm, s>>>(in, R, P.Px, out, scale, tw, P.fault);
+  return cudaSuccess;
+}
+
+// The staged path needs 16-byte aligned rows in and out (always true for
+// the library's own buffers; a caller's grid may be offset).
+bool staged_ok(const Params& P, const void* a, const void* b) {
+  return P.fx_staged && P.Nx >= 32 && (((uintptr_t)a | (uintptr_t)b) & 15u) == 0;
+}
+
+#define DISCOS_X_STAGED(FN, ...)                                      \
+  switch (P.Nx) {                                                     \
+    case 32: e = FN<T, 1>(__VA_ARGS__); break;                        \
+    case 64: e = FN<T, 2>(__VA_ARGS__); break;                        \
+    case 128: e = FN<T, 4>(__VA_ARGS__); break;                       \
+    case 256: e = FN<T, 8>(__VA_ARGS__); break;                       \
+    default: e = FN<T, 16>(__VA_ARGS__); break;                       \
+  }
+
 #define DISCOS_X_DISPATCH(KERNEL, ...)                                                        \
   switch (P.Nx) {                                                                             \
     case 32: KERNEL<T, 1><<<nb, 32 * wpb, sm, s>>>(__VA_ARGS__); break;                       \
@@ -404,7 +710,14 @@ cudaError_t fft_x_forward(const Params& P, const T* in, int R, cplx<T>* out, T s
   int N = P.Nx, logN = 31 - __builtin_clz((unsigned)N);
   const int pairs = (R + 1) / 2;
   probe_begin(PROBE_FFT_X, s);
-  if (N >= 32) {
+  if (staged_ok(P, in, out)) {
+    cudaError_t e = cudaSuccess;
+    DISCOS_X_STAGED(rfft_x_staged, P, in, R, out, scale, Nyr, add0, add1, tw, add0x, s)
+    if (e != cudaSuccess) {
+      probe_end(PROBE_FFT_X, s);
+      return e;
+    }
+  } else if (N >= 32) {
     const int wpb = x_warps_per_block<T>(P);
     const int nb = (pairs + wpb - 1) / wpb;
     const size_t sm = (size_t)wpb * 32 * (N / 32 + 1) * sizeof(cplx<T>);
@@ -426,7 +739,14 @@ cudaError_t fft_x_inverse(const Params& P, const cplx<T>* in, int R, T* out, T s
   int N = P.Nx, logN = 31 - __builtin_clz((unsigned)N);
   const int pairs = (R + 1) / 2;
   probe_begin(PROBE_FFT_X, s);
-  if (N >= 32) {
+  if (staged_ok(P, in, out)) {
+    cudaError_t e = cudaSuccess;
+    DISCOS_X_STAGED(irfft_x_staged, P, in, R, out, scale, tw, s)
+    if (e != cudaSuccess) {
+      probe_end(PROBE_FFT_X, s);
+      return e;
+    }
+  } else if (N >= 32) {
     const int wpb = x_warps_per_block<T>(P);
     const int nb = (pairs + wpb - 1) / wpb;
     const size_t sm = (size_t)wpb * 32 * (N / 32 + 1) * sizeof(cplx<T>);
@@ -442,6 +762,7 @@ cudaError_t fft_x_inverse(const Params& P, const cplx<T>* in, int R, T* out, T s
   return cudaGetLastError();
 }
 #undef DISCOS_X_DISPATCH
+#undef DISCOS_X_STAGED
 
 // z transforms: fz_tk x-mode columns per block (rounded up to whole warps).
 template <typename T, int G>
@@ -562,6 +883,7 @@ cudaError_t tune_transforms_t(Params& P, Workspace& W, cudaStream_t s, float* be
     return ms / 10.0f;
   };
   Params Q = P;
+  Q.fx_staged = 0;
   float bx = 1e30f, bz = 1e30f;
   int best_pp = P.fx_pp, best_th = P.fx_threads, best_tk = P.fz_tk;
   int last_pp = 0;
@@ -577,8 +899,20 @@ cudaError_t tune_transforms_t(Params& P, Workspace& W, cudaStream_t s, float* be
     const float ms = time_it([&] { return fft_x_forward<T>(Q, grid, R, S, T(1), P.Ny, T(0), T(0), twx, s, nullptr); });
     if (ms < bx) { bx = ms; best_pp = pp; best_th = th; }
   }
+  // the bulk-staged kernel (launch shape fixed by its chunk size)
+  bool best_staged = false;
+  if (N >= 32 && e == cudaSuccess) {
+    Q = P;
+    Q.fx_staged = 1;
+    const float ms = time_it([&] { return fft_x_forward<T>(Q, grid, R, S, T(1), P.Ny, T(0), T(0), twx, s, nullptr); });
+    if (ms < bx) { bx = ms; best_staged = true; }
+  }
+  // z: at least one 32-byte sector of consecutive x-modes per row access
+  // (4 columns in float, 2 in double); narrower tiles can win on an
+  // L2-resident trial spectrum and lose on the step's larger ones
   Q = P;
-  for (int tk = 1; tk <= max_tile_z(P.Nz, sizeof(cplx<T>)) && e == cudaSuccess; tk *= 2) {
+  const int tk0 = (int)(32 / sizeof(cplx<T>));
+  for (int tk = tk0; tk <= max_tile_z(P.Nz, sizeof(cplx<T>)) && e == cudaSuccess; tk *= 2) {
     Q.fz_tk = tk;
     const float ms = time_it([&] { return fft_z<T>(Q, S, P.Ny, 1, 0, false, twz, s); });
     if (ms < bz) { bz = ms; best_tk = tk; }
@@ -588,6 +922,7 @@ cudaError_t tune_transforms_t(Params& P, Workspace& W, cudaStream_t s, float* be
   if (e != cudaSuccess) return e;
   P.fx_pp = best_pp;
   P.fx_threads = best_th;
+  P.fx_staged = best_staged ? 1 : 0;
   P.fz_tk = best_tk;
   best_ms[0] = bx;
   best_ms[1] = bz;

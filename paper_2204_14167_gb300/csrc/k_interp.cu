@@ -11,6 +11,8 @@
 // the group.  The step hands the ions over in cell order, so the ions of a
 // warp read neighbouring grid lines (L1 reuse); out_index maps each result
 // back to the caller's order.
+#include <cstdint>
+#include <type_traits>
 #include "internal.h"
 
 namespace discos {
@@ -108,14 +110,15 @@ __global__ void k_interp_efield(const T* __restrict__ x, const T* __restrict__ q
 
 template <typename T>
 __global__ void k_interp_velocity(const T* __restrict__ x, int N, Params P, const T* __restrict__ v,
-                                  T* __restrict__ out, const int* __restrict__ out_index) {
+                                  T* __restrict__ out, const int* __restrict__ out_index,
+                                  const int* __restrict__ sp) {
   const KernelParams kp = P.khy;
   const int w = kp.w;
   const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
   int ion = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
   int l = threadIdx.x & 7;
   int gbase = (threadIdx.x & 31) & ~7;
-  bool valid = ion < N;
+  bool valid = ion < N && (P.hy_filter < 0 || sp[ion] == P.hy_filter);
   T p[3] = {T(0.5), T(0.5), T(0.5)};
   if (valid) { p[0] = x[ion]; p[1] = x[N + ion]; p[2] = x[2 * N + ion]; }
   const size_t G = (size_t)Nx * Ny * Nz;
@@ -260,14 +263,15 @@ __global__ void k_interp_efield_w(const T* __restrict__ x, const T* __restrict__
 // LPI = lanes per ion, the stencil width rounded up to 4 or 8.
 template <typename T, int W, int LPI>
 __global__ void k_interp_velocity_w(const T* __restrict__ x, int N, Params P, const T* __restrict__ v,
-                                    T* __restrict__ out, const int* __restrict__ out_index) {
+                                    T* __restrict__ out, const int* __restrict__ out_index,
+                                    const int* __restrict__ sp) {
   constexpr int LOG = LPI == 4 ? 2 : 3;
   const KernelParams kp = P.khy;
   const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
   int ion = (blockIdx.x * blockDim.x + threadIdx.x) >> LOG;
   int l = threadIdx.x & (LPI - 1);
   int gbase = (threadIdx.x & 31) & ~(LPI - 1);
-  bool valid = ion < N;
+  bool valid = ion < N && (P.hy_filter < 0 || sp[ion] == P.hy_filter);
   T p[3] = {T(0.5), T(0.5), T(0.5)};
   if (valid) { p[0] = x[ion]; p[1] = x[N + ion]; p[2] = x[2 * N + ion]; }
   const size_t G = (size_t)Nx * Ny * Nz;
@@ -321,6 +325,113 @@ __global__ void k_interp_velocity_w(const T* __restrict__ x, int N, Params P, co
   }
 }
 
+// Single precision, 4-point kernels: the field E = -grad_h phi on the
+// faces, interpolated (Eq. efieldop), one thread per ion.  The thread
+// evaluates its weights once per axis; each of the 5 x 5 rows (y, z) of the
+// 5 x 5 x 5 block of cell values around the ion is read as the two aligned
+// quads of x that cover it (16-byte loads, 2 per row instead of 5 scalar
+// ones), and per row the x-weights of the centre (cw) and of the face
+// difference (ew) give the two partial sums that the three components need.
+// Ghost rows as in k_interp_efield_w.  Needs a 16-byte aligned potential and
+// Nx a multiple of 4.
+__device__ __forceinline__ void row5(const float* __restrict__ row, int ix0, int Nx, float (&v)[5]) {
+  const int o = ix0 & 3, q0 = ix0 - o;
+  const float4 a = __ldg(reinterpret_cast<const float4*>(row + q0));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(row + ((q0 + 4) & (Nx - 1))));
+  if (o == 0) { v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; }
+  else if (o == 1) { v[0] = a.y; v[1] = a.z; v[2] = a.w; v[3] = b.x; v[4] = b.y; }
+  else if (o == 2) { v[0] = a.z; v[1] = a.w; v[2] = b.x; v[3] = b.y; v[4] = b.z; }
+  else { v[0] = a.w; v[1] = b.x; v[2] = b.y; v[3] = b.z; v[4] = b.w; }
+}
+
+__global__ void k_interp_efield_t4(const float* __restrict__ x, const float* __restrict__ q, int N, Params P,
+                                   const float* __restrict__ phi, float* __restrict__ out, int as_force,
+                                   const float* __restrict__ F_add, const int* __restrict__ out_index) {
+  const int ion = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ion >= N) return;
+  const KernelParams kp = P.kes;
+  const int Nx = P.Nx, Ny = P.Ny;
+  const PhysF& Q = P.f;
+  const float p[3] = {x[ion], x[N + ion], x[2 * N + ion]};
+  int c0[3];
+  float cw[3][5], ew[3][5];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    c0[d] = stencil_start(p[d], 4) - 1;
+    float kprev = kval(p[d] - float(c0[d]), kp);
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+      const int c = c0[d] + l;
+      cw[d][l] = kval(p[d] - (float(c) + 0.5f), kp);
+      const float knext = kval(p[d] - float(c + 1), kp);
+      ew[d][l] = knext - kprev;
+      kprev = knext;
+    }
+  }
+  const int ix0 = c0[0] & (Nx - 1);
+  // a metal strip in the bottom wall: the rows below it take the Dirichlet
+  // rule with the strip potential of each column
+  bool sc[5];
+  float pm2[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int col = (ix0 + i) & (Nx - 1);
+    sc[i] = on_strip(P, col);
+    pm2[i] = sc[i] ? 2.f * strip_phi_m(P, col, 0.f) : 0.f;
+  }
+  float Ex = 0.f, Ey = 0.f, Ez = 0.f;
+#pragma unroll
+  for (int jy = 0; jy < 5; ++jy) {
+    // phi at row iy = rs * phi[row] + ra (ghost rows of Eqs. esbc1 / esbc3)
+    const int iy = c0[1] + jy;
+    int row = iy;
+    float rs = 1.f, ra = 0.f;
+    const bool below = iy < 0;
+    if (below) {
+      int m = -1 - iy;
+      m = m < Ny ? m : Ny - 1;
+      row = m;
+      if (P.bc[0] == DISCOS_BC_DIRICHLET) { rs = -1.f; ra = 2.f * Q.phi_b[0]; }
+      else ra = -Q.slope[0] * float(2 * m + 1);
+    } else if (iy >= Ny) {
+      int m = iy - Ny;
+      m = m < Ny ? m : Ny - 1;
+      row = Ny - 1 - m;
+      if (P.bc[1] == DISCOS_BC_DIRICHLET) { rs = -1.f; ra = 2.f * Q.phi_b[1]; }
+      else ra = Q.slope[1] * float(2 * m + 1);
+    }
+    float a1 = 0.f, a2 = 0.f, a3 = 0.f;     // sums over z: centre-x centre-z, centre-x edge-z, edge-x centre-z
+#pragma unroll
+    for (int jz = 0; jz < 5; ++jz) {
+      float vals[5];
+      row5(phi + ((size_t)((c0[2] + jz) & (P.Nz - 1)) * Ny + row) * Nx, ix0, Nx, vals);
+      float sc_c = 0.f, sc_e = 0.f;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        const float vv = (below && sc[i]) ? pm2[i] - vals[i] : rs * vals[i] + ra;
+        sc_c += vv * cw[0][i];
+        sc_e += vv * ew[0][i];
+      }
+      a1 += sc_c * cw[2][jz];
+      a2 += sc_c * ew[2][jz];
+      a3 += sc_e * cw[2][jz];
+    }
+    Ex += a3 * cw[1][jy];
+    Ey += a1 * ew[1][jy];
+    Ez += a2 * cw[1][jy];
+  }
+  const int o = out_index ? out_index[ion] : ion;
+  if (as_force) {
+    const float qq = q[ion];
+    const float f0 = F_add ? F_add[ion] : 0.f, f1 = F_add ? F_add[N + ion] : 0.f, f2 = F_add ? F_add[2 * N + ion] : 0.f;
+    out[o] = qq * (Ex + Q.E_ext[0]) + f0;
+    out[N + o] = qq * (Ey + Q.E_ext[1]) + f1;
+    out[2 * N + o] = qq * (Ez + Q.E_ext[2]) + f2;
+  } else {
+    out[o] = Ex; out[N + o] = Ey; out[2 * N + o] = Ez;
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -330,7 +441,11 @@ cudaError_t launch_interp_efield(const Params& P, const T* x, const T* q, int N,
   int bs = 256;
   int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
   probe_begin(PROBE_INTERP_E, s);
-  if (P.kes.w == 4) k_interp_efield_w<T, 4><<<nb, bs, 0, s>>>(x, q, N, P, phi, out, as_force ? 1 : 0, F_add, out_index);
+  if (std::is_same<T, float>::value && P.kes.w == 4 && ((uintptr_t)phi & 15u) == 0)
+    k_interp_efield_t4<<<(int)(((size_t)N + bs - 1) / bs), bs, 0, s>>>(
+        reinterpret_cast<const float*>(x), reinterpret_cast<const float*>(q), N, P, reinterpret_cast<const float*>(phi),
+        reinterpret_cast<float*>(out), as_force ? 1 : 0, reinterpret_cast<const float*>(F_add), out_index);
+  else if (P.kes.w == 4) k_interp_efield_w<T, 4><<<nb, bs, 0, s>>>(x, q, N, P, phi, out, as_force ? 1 : 0, F_add, out_index);
   else if (P.kes.w == 6) k_interp_efield_w<T, 6><<<nb, bs, 0, s>>>(x, q, N, P, phi, out, as_force ? 1 : 0, F_add, out_index);
   else k_interp_efield<T><<<nb, bs, 0, s>>>(x, q, N, P, phi, out, as_force ? 1 : 0, F_add, out_index);
   count_launches(1);
@@ -340,23 +455,26 @@ cudaError_t launch_interp_efield(const Params& P, const T* x, const T* q, int N,
 
 template <typename T>
 cudaError_t launch_interp_velocity(const Params& P, const T* x, int N, const T* v, T* out, cudaStream_t s,
-                                   const int* out_index) {
+                                   const int* out_index, const int* species) {
   if (N <= 0) return cudaSuccess;
   int bs = 256;
   int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
   probe_begin(PROBE_INTERP_V, s);
-  if (P.khy.w == 4)
-    k_interp_velocity_w<T, 4, 4><<<(int)(((size_t)N * 4 + bs - 1) / bs), bs, 0, s>>>(x, N, P, v, out, out_index);
-  else if (P.khy.w == 6) k_interp_velocity_w<T, 6, 8><<<nb, bs, 0, s>>>(x, N, P, v, out, out_index);
-  else k_interp_velocity<T><<<nb, bs, 0, s>>>(x, N, P, v, out, out_index);
-  count_launches(1);
+  auto one = [&](const Params& Q) {
+    if (Q.khy.w == 4)
+      k_interp_velocity_w<T, 4, 4><<<(int)(((size_t)N * 4 + bs - 1) / bs), bs, 0, s>>>(x, N, Q, v, out, out_index, species);
+    else if (Q.khy.w == 6) k_interp_velocity_w<T, 6, 8><<<nb, bs, 0, s>>>(x, N, Q, v, out, out_index, species);
+    else k_interp_velocity<T><<<nb, bs, 0, s>>>(x, N, Q, v, out, out_index, species);
+    count_launches(1);
+  };
+  for_each_hy_kernel(P, species, one);
   probe_end(PROBE_INTERP_V, s);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_interp_efield<float>(const Params&, const float*, const float*, int, const float*, float*, bool, cudaStream_t, const float*, const int*);
 template cudaError_t launch_interp_efield<double>(const Params&, const double*, const double*, int, const double*, double*, bool, cudaStream_t, const double*, const int*);
-template cudaError_t launch_interp_velocity<float>(const Params&, const float*, int, const float*, float*, cudaStream_t, const int*);
-template cudaError_t launch_interp_velocity<double>(const Params&, const double*, int, const double*, double*, cudaStream_t, const int*);
+template cudaError_t launch_interp_velocity<float>(const Params&, const float*, int, const float*, float*, cudaStream_t, const int*, const int*);
+template cudaError_t launch_interp_velocity<double>(const Params&, const double*, int, const double*, double*, cudaStream_t, const int*, const int*);
 
 }  // namespace discos

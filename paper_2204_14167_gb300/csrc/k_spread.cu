@@ -7,6 +7,8 @@
 // x-offset l of the stencil, so each warp-wide atomic touches 4 short runs of
 // consecutive addresses.  The y and z weights are computed by the lanes of
 // the group and broadcast with shuffles.
+#include <cstdint>
+#include <type_traits>
 #include "internal.h"
 
 namespace discos {
@@ -71,7 +73,7 @@ __global__ void k_spread_charge(const T* __restrict__ x, const T* __restrict__ q
 template <typename T>
 __global__ void k_spread_force(const T* __restrict__ x, const T* __restrict__ F, int N, Params P,
                                T* __restrict__ f, long long step, int rfd, const int* __restrict__ noise_index,
-                               unsigned long long stride) {
+                               unsigned long long stride, const int* __restrict__ sp) {
   const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
   const KernelParams kp = P.khy;
   const int w = kp.w;
@@ -79,7 +81,7 @@ __global__ void k_spread_force(const T* __restrict__ x, const T* __restrict__ F,
   int ion = spread_ion((blockIdx.x * blockDim.x + threadIdx.x) >> 3, N, stride);
   int l = threadIdx.x & 7;
   int gbase = (threadIdx.x & 31) & ~7;
-  bool valid = ion < N;
+  bool valid = ion < N && (P.hy_filter < 0 || sp[ion] == P.hy_filter);
   T p[3] = {T(0.5), T(0.5), T(0.5)};
   T Fc = T(0);
   T Wr[3] = {T(0), T(0), T(0)};
@@ -191,17 +193,19 @@ __global__ void k_spread_charge_w(const T* __restrict__ x, const T* __restrict__
   }
 }
 
-template <typename T, int W>
+// LPI = lanes per ion: 4 for 4-point stencils (no idle lanes), else 8.
+template <typename T, int W, int LPI>
 __global__ void k_spread_force_w(const T* __restrict__ x, const T* __restrict__ F, int N, Params P,
                                  T* __restrict__ f, long long step, int rfd, const int* __restrict__ noise_index,
-                                 unsigned long long stride) {
+                                 unsigned long long stride, const int* __restrict__ sp) {
+  constexpr int LOG = LPI == 4 ? 2 : 3;
   const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
   const KernelParams kp = P.khy;
   const int c = blockIdx.y;
-  int ion = spread_ion((blockIdx.x * blockDim.x + threadIdx.x) >> 3, N, stride);
-  int l = threadIdx.x & 7;
-  int gbase = (threadIdx.x & 31) & ~7;
-  bool valid = ion < N;
+  int ion = spread_ion((blockIdx.x * blockDim.x + threadIdx.x) >> LOG, N, stride);
+  int l = threadIdx.x & (LPI - 1);
+  int gbase = (threadIdx.x & 31) & ~(LPI - 1);
+  bool valid = ion < N && (P.hy_filter < 0 || sp[ion] == P.hy_filter);
   T p[3] = {T(0.5), T(0.5), T(0.5)};
   T Fc = T(0);
   T Wr[3] = {T(0), T(0), T(0)};
@@ -274,6 +278,81 @@ __global__ void k_spread_force_w(const T* __restrict__ x, const T* __restrict__ 
   }
 }
 
+// Single-precision spreading for 4-point stencils, one thread per ion.
+// The thread evaluates the 4 weights per axis once, walks the 16 x-rows
+// (jy, jz) of the 4 x 4 x 4 stencil, and adds each row's four values with
+// 16-byte vector reductions (red.global.add.v4.f32) on the aligned quads of
+// x that the row covers: one quad when the row starts on a multiple of 4,
+// else two, the other slots adding zero.  About 28 vector reductions per ion
+// and component instead of 64 scalar ones, and no work repeated across
+// lanes (the lane-group kernels above evaluate the weights and the thermal
+// draws once per lane).  Images, signs and thermal forcing are those of the
+// lane-group kernels.  Needs 16-byte aligned grids and Nx a multiple of 4
+// (quads never straddle the periodic wrap).
+__device__ __forceinline__ void red_row4(float* row, int ix0, int Nx, float v0, float v1, float v2, float v3) {
+  const int o = ix0 & 3;
+  const int q0 = ix0 - o;
+  float4* a = reinterpret_cast<float4*>(row + q0);
+  if (o == 0) {
+    atomicAdd(a, make_float4(v0, v1, v2, v3));
+    return;
+  }
+  float4* b = reinterpret_cast<float4*>(row + ((q0 + 4) & (Nx - 1)));
+  if (o == 1) {
+    atomicAdd(a, make_float4(0.f, v0, v1, v2));
+    atomicAdd(b, make_float4(v3, 0.f, 0.f, 0.f));
+  } else if (o == 2) {
+    atomicAdd(a, make_float4(0.f, 0.f, v0, v1));
+    atomicAdd(b, make_float4(v2, v3, 0.f, 0.f));
+  } else {
+    atomicAdd(a, make_float4(0.f, 0.f, 0.f, v0));
+    atomicAdd(b, make_float4(v1, v2, v3, 0.f));
+  }
+}
+
+__global__ void k_spread_charge_t4(const float* __restrict__ x, const float* __restrict__ q, int N, Params P,
+                                   float* __restrict__ rho, unsigned long long stride) {
+  const int ion = spread_ion(blockIdx.x * blockDim.x + threadIdx.x, N, stride);
+  if (ion >= N) return;
+  const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
+  const KernelParams kp = P.kes;
+  const float sx = x[ion] - 0.5f, sy = x[N + ion] - 0.5f, sz = x[2 * N + ion] - 0.5f, qq = q[ion];
+  const int x0 = stencil_start(sx, 4), y0 = stencil_start(sy, 4), z0 = stencil_start(sz, 4);
+  float wx[4], wy[4], wz[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    wx[j] = kval(sx - float(x0 + j), kp);
+    wy[j] = kval(sy - float(y0 + j), kp);
+    wz[j] = kval(sz - float(z0 + j), kp);
+  }
+  const int ix0 = x0 & (Nx - 1);
+  // a metal strip in the (dielectric) bottom wall: rows below the wall take
+  // the conducting wall's sign in the strip's columns
+  float cs[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) cs[i] = on_strip(P, (ix0 + i) & (Nx - 1)) ? -1.f : 1.f;
+  const float s0 = P.bc[0] == DISCOS_BC_DIRICHLET ? -1.f : 1.f;
+  const float s1 = P.bc[1] == DISCOS_BC_DIRICHLET ? -1.f : 1.f;
+#pragma unroll
+  for (int jy = 0; jy < 4; ++jy) {
+    int iy = y0 + jy;
+    float sg = 1.f;
+    const bool below = iy < 0;
+    if (below) { iy = -1 - iy; sg = s0; }
+    else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = s1; }
+    if (iy < 0 || iy >= Ny) continue;
+    const float a = qq * sg * wy[jy];
+    const float c0 = below ? cs[0] : 1.f, c1 = below ? cs[1] : 1.f, c2 = below ? cs[2] : 1.f,
+                c3 = below ? cs[3] : 1.f;
+#pragma unroll
+    for (int jz = 0; jz < 4; ++jz) {
+      const float b = a * wz[jz];
+      float* row = rho + ((size_t)((z0 + jz) & (Nz - 1)) * Ny + iy) * Nx;
+      red_row4(row, ix0, Nx, b * c0 * wx[0], b * c1 * wx[1], b * c2 * wx[2], b * c3 * wx[3]);
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_fill(T* __restrict__ p, size_t n, T value) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -298,6 +377,8 @@ template <typename T>
 cudaError_t launch_fill_zero(T* p, size_t n, cudaStream_t s) {
   return launch_fill_value<T>(p, n, T(0), s);
 }
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 // A prime near 0.618 N that does not divide N: g * stride mod N is then a
 // bijection that sends consecutive g about 0.618 N apart (Fibonacci
@@ -328,7 +409,10 @@ cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N,
   int bs = 256;
   int nb = (int)(((size_t)N * 8 + bs - 1) / bs);
   const unsigned long long st = decorrelate ? spread_stride(N) : 0ull;
-  if (P.kes.w == 4) k_spread_charge_w<T, 4><<<nb, bs, 0, s>>>(x, q, N, P, rho, st);
+  if (std::is_same<T, float>::value && P.kes.w == 4 && aligned16(rho))
+    k_spread_charge_t4<<<(unsigned)(((size_t)N + bs - 1) / bs), bs, 0, s>>>(
+        reinterpret_cast<const float*>(x), reinterpret_cast<const float*>(q), N, P, reinterpret_cast<float*>(rho), st);
+  else if (P.kes.w == 4) k_spread_charge_w<T, 4><<<nb, bs, 0, s>>>(x, q, N, P, rho, st);
   else if (P.kes.w == 6) k_spread_charge_w<T, 6><<<nb, bs, 0, s>>>(x, q, N, P, rho, st);
   else k_spread_charge<T><<<nb, bs, 0, s>>>(x, q, N, P, rho, st);
   count_launches(1);
@@ -338,7 +422,8 @@ cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N,
 
 template <typename T>
 cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, T* f, int64_t step, bool rfd,
-                                cudaStream_t s, bool accumulate, const int* noise_index, bool decorrelate) {
+                                cudaStream_t s, bool accumulate, const int* noise_index, bool decorrelate,
+                                const int* species) {
   size_t n = (size_t)P.Nx * P.Nz * (3 * P.Ny + 1);
   probe_begin(PROBE_SPREAD_FORCE, s);
   cudaError_t e = accumulate ? cudaSuccess : launch_fill_zero(f, n, s);
@@ -348,13 +433,15 @@ cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, 
   }
   int bs = 256;
   dim3 grid((unsigned)(((size_t)N * 8 + bs - 1) / bs), 3);
-  if (P.khy.w == 4) k_spread_force_w<T, 4><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0, noise_index,
-                                                                   decorrelate ? spread_stride(N) : 0ull);
-  else if (P.khy.w == 6) k_spread_force_w<T, 6><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0, noise_index,
-                                                                   decorrelate ? spread_stride(N) : 0ull);
-  else k_spread_force<T><<<grid, bs, 0, s>>>(x, F, N, P, f, (long long)step, rfd ? 1 : 0, noise_index,
-                                             decorrelate ? spread_stride(N) : 0ull);
-  count_launches(1);
+  const unsigned long long st = decorrelate ? spread_stride(N) : 0ull;
+  const dim3 grid4((unsigned)(((size_t)N * 4 + bs - 1) / bs), 3);
+  auto one = [&](const Params& Q) {
+    if (Q.khy.w == 4) k_spread_force_w<T, 4, 4><<<grid4, bs, 0, s>>>(x, F, N, Q, f, (long long)step, rfd ? 1 : 0, noise_index, st, species);
+    else if (Q.khy.w == 6) k_spread_force_w<T, 6, 8><<<grid, bs, 0, s>>>(x, F, N, Q, f, (long long)step, rfd ? 1 : 0, noise_index, st, species);
+    else k_spread_force<T><<<grid, bs, 0, s>>>(x, F, N, Q, f, (long long)step, rfd ? 1 : 0, noise_index, st, species);
+    count_launches(1);
+  };
+  for_each_hy_kernel(P, species, one);
   probe_end(PROBE_SPREAD_FORCE, s);
   return cudaGetLastError();
 }
@@ -365,7 +452,7 @@ template cudaError_t launch_fill_zero<float>(float*, size_t, cudaStream_t);
 template cudaError_t launch_fill_zero<double>(double*, size_t, cudaStream_t);
 template cudaError_t launch_spread_charge<float>(const Params&, const float*, const float*, int, float*, cudaStream_t, bool);
 template cudaError_t launch_spread_charge<double>(const Params&, const double*, const double*, int, double*, cudaStream_t, bool);
-template cudaError_t launch_spread_force<float>(const Params&, const float*, const float*, int, float*, int64_t, bool, cudaStream_t, bool, const int*, bool);
-template cudaError_t launch_spread_force<double>(const Params&, const double*, const double*, int, double*, int64_t, bool, cudaStream_t, bool, const int*, bool);
+template cudaError_t launch_spread_force<float>(const Params&, const float*, const float*, int, float*, int64_t, bool, cudaStream_t, bool, const int*, bool, const int*);
+template cudaError_t launch_spread_force<double>(const Params&, const double*, const double*, int, double*, int64_t, bool, cudaStream_t, bool, const int*, bool, const int*);
 
 }  // namespace discos

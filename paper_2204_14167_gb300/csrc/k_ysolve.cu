@@ -442,7 +442,9 @@ __device__ __forceinline__ void stokes_mode(cplx<TS>* __restrict__ Su, cplx<TS>*
       cm[r] = TC(1);
       if (j < Ny) {
         C<TC> e0 = csub2(sv[j + 1], sv[j]);
-        TC a = K2 + TC(2) + (j == 0 ? TC(1) : TC(0)) + (j == Ny - 1 ? TC(1) : TC(0));
+        // A_c's diagonal: the tangential ghost adds +1 at a no-slip wall, -1 at a slip wall
+        TC a = K2 + TC(2) + (j == 0 ? (P.slip[0] ? TC(-1) : TC(1)) : TC(0)) +
+               (j == Ny - 1 ? (P.slip[1] ? TC(-1) : TC(1)) : TC(0));
         C<TC> acd = cscale(a, e0);
         if (j >= 1) acd = csub2(acd, csub2(sv[j], sv[j - 1]));
         if (j <= Ny - 2) acd = csub2(acd, csub2(sv[j + 2], sv[j + 1]));
@@ -570,6 +572,144 @@ __global__ void k_stokes_scan_staged(cplx<TS>* __restrict__ S, Params P, const T
   }
 }
 
+
+// ------------------------------------------------------------------ sweeps
+// The single-precision bulk of the mixed path (every mode but the low ones,
+// which are solved in double on the side stream): one thread per mode, the
+// same recurrences as the scans above run sequentially along y, in place in
+// the spectra.  A warp takes 32 consecutive x-modes of one kz, so each of
+// its row accesses is one contiguous run of 256 bytes, and the factor tables
+// are stored [row][mode] for the same reason.  Per row and mode this is a
+// few dozen instructions, where a warp-wide scan spends log2(32) levels of
+// map compositions per mode; the modes run in parallel instead of the rows.
+// Threads are laid out over (kz, kx) with kx padded to a multiple of 32.
+__device__ __forceinline__ C<float> ldcf(const cplx<float>* p) {
+  const cplx<float> v = *p;
+  return C<float>{v.re, v.im};
+}
+__device__ __forceinline__ void stcf(cplx<float>* p, C<float> v, float s) { *p = cplx<float>{v.r * s, v.i * s}; }
+
+__global__ void k_poisson_sweep(cplx<float>* __restrict__ S, const float* __restrict__ piv,
+                                const unsigned char* __restrict__ skip, int Ny, int Nz, int Nxh, int Px,
+                                float norm) {
+  const int NxhP = (Nxh + 31) & ~31;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int kz = t / NxhP, kx = t - kz * NxhP;
+  if (kz >= Nz || kx >= Nxh) return;
+  const int mode = kz * Nxh + kx;
+  if (skip && skip[mode]) return;
+  const size_t M = (size_t)Nz * Nxh;
+  cplx<float>* col = S + (size_t)kz * Ny * Px + kx;
+  // forward y_j = piv_j (b_j + y_{j-1}), in place
+  C<float> y = cz<float>();
+  for (int j = 0; j < Ny; ++j) {
+    const float m = piv[(size_t)j * M + mode];
+    y = cscale(m, cadd2(ldcf(col + (size_t)j * Px), y));
+    stcf(col + (size_t)j * Px, y, 1.f);
+  }
+  // backward x_j = y_j + piv_j x_{j+1}, x_{Ny-1} = y_{Ny-1}
+  C<float> xn = cz<float>();
+  for (int j = Ny - 1; j >= 0; --j) {
+    const float a = j < Ny - 1 ? piv[(size_t)j * M + mode] : 0.f;
+    xn = cfma(a, xn, ldcf(col + (size_t)j * Px));
+    stcf(col + (size_t)j * Px, xn, norm);
+  }
+}
+
+__global__ void k_stokes_sweep(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Sp, Params P,
+                               const float* __restrict__ L1, const float* __restrict__ L2,
+                               const float* __restrict__ DI, const float* __restrict__ CI,
+                               const float* __restrict__ MC, const unsigned char* __restrict__ skip) {
+  const int Ny = P.Ny, Nz = P.Nz, Px = P.Px, Nxh = P.Nxh;
+  const int NxhP = (Nxh + 31) & ~31;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int kz = t / NxhP, kx = t - kz * NxhP;
+  if (kz >= Nz || kx >= Nxh) return;
+  const int mode = kz * Nxh + kx;
+  if (skip && skip[mode]) return;
+  const size_t M = (size_t)Nz * Nxh;
+  cplx<float>* Su = S + (size_t)kz * Ny * Px + kx;
+  cplx<float>* Sv = S + (size_t)Nz * Ny * Px + (size_t)kz * (Ny + 1) * Px + kx;
+  cplx<float>* Sw = S + (size_t)Nz * (2 * Ny + 1) * Px + (size_t)kz * Ny * Px + kx;
+  const float gxr = MC[5 * (size_t)mode], gxi = MC[5 * (size_t)mode + 1];
+  const float gzr = MC[5 * (size_t)mode + 2], gzi = MC[5 * (size_t)mode + 3];
+  const float mik2 = MC[5 * (size_t)mode + 4];
+  const float K2 = mik2 != 0.f ? -1.f / mik2 : 0.f;
+  const float eta = P.f.eta, ieta = P.f.inv_eta, norm = P.f.inv_nxnz;
+  const float wb = P.slip[0] ? -1.f : 1.f, wt = P.slip[1] ? -1.f : 1.f;
+  auto gsum = [&](C<float> fx, C<float> fz) {
+    return C<float>{gxr * fx.r - gxi * fx.i + gzr * fz.r - gzi * fz.i,
+                    gxr * fx.i + gxi * fx.r + gzr * fz.i + gzi * fz.r};
+  };
+  // A: y_f = ieta (K^2 fy_f + g_f - g_{f-1}) - l1_f y_{f-1} - l2_f y_{f-2}, f = 1..Ny-1 (over fy)
+  {
+    C<float> gprev = gsum(ldcf(Su), ldcf(Sw));
+    C<float> y1 = cz<float>(), y2 = cz<float>();
+    for (int f = 1; f < Ny; ++f) {
+      const C<float> g = gsum(ldcf(Su + (size_t)f * Px), ldcf(Sw + (size_t)f * Px));
+      const C<float> fy = ldcf(Sv + (size_t)f * Px);
+      const C<float> rhs = cscale(ieta, C<float>{K2 * fy.r + (g.r - gprev.r), K2 * fy.i + (g.i - gprev.i)});
+      const float l1 = L1[(size_t)f * M + mode], l2 = L2[(size_t)f * M + mode];
+      const C<float> y = csub2(csub2(rhs, cscale(l1, y1)), cscale(l2, y2));
+      stcf(Sv + (size_t)f * Px, y, 1.f);
+      y2 = y1; y1 = y; gprev = g;
+    }
+  }
+  // B: v_f = di_f y_f - l1_{f+1} v_{f+1} - l2_{f+2} v_{f+2}, f = Ny-1..1 (over y, unscaled)
+  {
+    C<float> v1 = cz<float>(), v2 = cz<float>();
+    for (int f = Ny - 1; f >= 1; --f) {
+      const float a1 = f + 1 < Ny ? L1[(size_t)(f + 1) * M + mode] : 0.f;
+      const float a2 = f + 2 < Ny ? L2[(size_t)(f + 2) * M + mode] : 0.f;
+      const C<float> v = csub2(csub2(cscale(DI[(size_t)f * M + mode], ldcf(Sv + (size_t)f * Px)), cscale(a1, v1)),
+                               cscale(a2, v2));
+      stcf(Sv + (size_t)f * Px, v, 1.f);
+      v2 = v1; v1 = v;
+    }
+  }
+  // C: the pressure row by row from a window (v_{j-1}, v_j, v_{j+1}, v_{j+2})
+  // (wall faces 0 and Ny carry v = 0), then the forward sweeps of the u and
+  // w tridiagonals, in place; face j of v is final (scaled) once row j is done
+  {
+    C<float> vm1 = cz<float>(), v0 = cz<float>();
+    C<float> vp1 = Ny >= 2 ? ldcf(Sv + (size_t)Px) : cz<float>();
+    C<float> vp2 = Ny >= 3 ? ldcf(Sv + 2 * (size_t)Px) : cz<float>();
+    C<float> yu = cz<float>(), yw = cz<float>();
+    for (int j = 0; j < Ny; ++j) {
+      const C<float> fx = ldcf(Su + (size_t)j * Px), fz = ldcf(Sw + (size_t)j * Px);
+      // A_c's diagonal: the tangential ghost adds +1 at a no-slip wall, -1 at a slip wall
+      const float a = K2 + 2.f + (j == 0 ? wb : 0.f) + (j == Ny - 1 ? wt : 0.f);
+      C<float> acd = cscale(a, csub2(vp1, v0));
+      if (j >= 1) acd = csub2(acd, csub2(v0, vm1));
+      if (j <= Ny - 2) acd = csub2(acd, csub2(vp2, vp1));
+      const C<float> p = cscale(mik2, cfma(eta, acd, gsum(fx, fz)));
+      if (Sp) Sp[(size_t)kz * Ny * Px + kx + (size_t)j * Px] = cplx<float>{p.r * norm, p.i * norm};
+      const C<float> bu = cscale(ieta, C<float>{fx.r + gxr * p.r + gxi * p.i, fx.i + gxr * p.i - gxi * p.r});
+      const C<float> bw = cscale(ieta, C<float>{fz.r + gzr * p.r + gzi * p.i, fz.i + gzr * p.i - gzi * p.r});
+      const float c = CI[(size_t)j * M + mode];
+      yu = cscale(c, cadd2(bu, yu));
+      yw = cscale(c, cadd2(bw, yw));
+      stcf(Su + (size_t)j * Px, yu, 1.f);
+      stcf(Sw + (size_t)j * Px, yw, 1.f);
+      stcf(Sv + (size_t)j * Px, v0, norm);
+      vm1 = v0; v0 = vp1; vp1 = vp2;
+      vp2 = j + 3 <= Ny - 1 ? ldcf(Sv + (size_t)(j + 3) * Px) : cz<float>();
+    }
+    Sv[(size_t)Ny * Px] = cplx<float>{0.f, 0.f};
+  }
+  // D: backward x_j = y_j + ci_j x_{j+1}, x_{Ny-1} = y_{Ny-1}
+  {
+    C<float> xu = cz<float>(), xw = cz<float>();
+    for (int j = Ny - 1; j >= 0; --j) {
+      const float a = j < Ny - 1 ? CI[(size_t)j * M + mode] : 0.f;
+      xu = cfma(a, xu, ldcf(Su + (size_t)j * Px));
+      xw = cfma(a, xw, ldcf(Sw + (size_t)j * Px));
+      stcf(Su + (size_t)j * Px, xu, norm);
+      stcf(Sw + (size_t)j * Px, xw, norm);
+    }
+  }
+}
+
 template <typename TS, typename TC>
 cudaError_t poisson_scan_launch(const Params& P, cplx<TS>* S, const TC* piv, const int* list, int n,
                                 const unsigned char* skip, cudaStream_t s) {
@@ -669,7 +809,13 @@ cudaError_t launch_poisson_y_impl(const Params& P, Workspace& W, cplx<T>* S, cud
     if (e == cudaSuccess) e = cudaStreamWaitEvent(W.ystream, W.yev0, 0);
     if (e == cudaSuccess) e = poisson_scan_launch<float, double>(P, S, W.piv64, W.lo_modes, W.n_lo, nullptr, W.ystream);
     if (e == cudaSuccess) e = cudaEventRecord(W.yev1, W.ystream);
-    if (e == cudaSuccess) e = poisson_scan_launch<float, float>(P, S, W.piv32, nullptr, M, W.is_lo, s);
+    if (e == cudaSuccess) {
+      const int nt = P.Nz * ((P.Nxh + 31) & ~31);
+      k_poisson_sweep<<<(nt + 127) / 128, 128, 0, s>>>(S, W.piv32t, W.is_lo, P.Ny, P.Nz, P.Nxh, P.Px,
+                                                      (float)P.inv_nxnz);
+      count_launches(1);
+      e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, W.yev1, 0);
     return e;
   } else {
@@ -695,9 +841,13 @@ cudaError_t launch_stokes_y_impl(const Params& P, Workspace& W, cplx<T>* S, cplx
       e = stokes_scan_launch<float, double>(P, S, Sp, W.st_l1, W.st_l2, W.st_di, W.st_ci, W.st_mc, W.lo_modes,
                                             W.n_lo, nullptr, W.ystream);
     if (e == cudaSuccess) e = cudaEventRecord(W.yev1, W.ystream);
-    if (e == cudaSuccess)
-      e = stokes_scan_launch<float, float>(P, S, Sp, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf, nullptr,
-                                           M, W.is_lo, s);
+    if (e == cudaSuccess) {
+      const int nt = P.Nz * ((P.Nxh + 31) & ~31);
+      k_stokes_sweep<<<(nt + 127) / 128, 128, 0, s>>>(S, Sp, P, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf,
+                                                     W.is_lo);
+      count_launches(1);
+      e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, W.yev1, 0);
     return e;
   } else {

@@ -6,11 +6,17 @@ kT = 1.  The near-field cutoff psi = 4 is where the grid pair force of the
 """
 import math
 
-from . import RunConfig, BC_DIRICHLET, BC_NEUMANN, KERNEL_PESKIN4, KERNEL_PESKIN6, FP64, MIXED
+from . import RunConfig, BC_DIRICHLET, BC_NEUMANN, KERNEL_PESKIN4, KERNEL_PESKIN6, KERNEL_ES, FP64, MIXED
 from . import mobility
 
 WCA = 2.0 ** (1.0 / 6.0)
 A_WET_PESKIN4 = 0.91     # hydrodynamic radius of the 4-point kernel in grid units
+# hydrodynamic radii of the two ES kernels of App. B (cations: w = 7,
+# beta = 7; anions: w = 4, beta = 8), in grid units, measured with this
+# library's Stokes solver (calibrate.hydrodynamic_radius on a 64 x 64 x 64
+# channel, mid-channel perpendicular mobility)
+A_WET_ES77 = 1.60
+A_WET_ES48 = 0.95
 
 
 def _wca(sigma):
@@ -140,10 +146,51 @@ def batched_ions(cfg, rec):
     return np.concatenate(pos, axis=1), np.concatenate(q), np.concatenate(sp), off
 
 
+def eo_two_species(precision=MIXED, Nx=64, Ny=56, Nz=64, n_pos=6400, n_neg=5600):
+    """Electro-osmotic channel of Sec. IV.A with a hydrodynamic kernel per
+    species (App. B): cations spread and interpolate with the ES kernel of
+    w = 7, beta = 7, anions with w = 4, beta = 8, on one hydrodynamic grid;
+    the 4-point kernel for the electrostatics.  Dielectric walls carry the
+    same surface charge, which balances the excess of cations (the channel
+    is neutral); E_x = 0.05; 85 % wet (Sec. IV.A runs 85 % wet on a coarser
+    grid); no-slip fluctuating Stokes with the midpoint scheme.  The paper's
+    grid is 56^3; x and z are powers of two here (64)."""
+    eta = 1.0 / (6.0 * math.pi)
+    radii = (A_WET_ES77, A_WET_ES48)
+    D_wet = [1.0 / a for a in radii]              # kT / (6 pi eta a_w)
+    D_tot = [d / 0.85 for d in D_wet]
+    gam = [mobility.gamma_table(0.85 * a, a, float(Ny)) for a in radii]
+    net = n_pos - n_neg
+    sigma_s = -net / (2.0 * Nx * Nz)
+    cfg = RunConfig(Nx=Nx, Ny=Ny, Nz=Nz, bc=(BC_NEUMANN, BC_NEUMANN), surf_charge=(sigma_s, sigma_s),
+                    kernel_es=KERNEL_PESKIN4, kernel_hy=KERNEL_ES, es_w=(6, 7), es_beta=(8.0, 7.0),
+                    lB=0.5, eta=eta, kT=1.0, dt=0.001, psi=4.0, n_tab=64, nspecies=2, D_tot=D_tot, D_wet=D_wet,
+                    gamma_coef=gam, E_ext=(0.05, 0.0, 0.0), wet=True, precision=precision,
+                    max_ions=n_pos + n_neg, hy_species=True, kernel_hy_s=[KERNEL_ES, KERNEL_ES], hy_w_s=[7, 4],
+                    hy_beta_s=[7.0, 8.0], lj_sigma=[[1.0, 1.0], [1.0, 1.0]], lj_xi=[[1.0, 1.0], [1.0, 1.0]],
+                    lj_rc=[[WCA, WCA], [WCA, WCA]], wall_sigma=[2.0 ** (-1.0 / 6.0)] * 2, wall_xi=[1.0, 1.0],
+                    wall_rc=[1.0, 1.0])
+    return cfg, dict(n_pos=n_pos, n_neg=n_neg, ymargin=1.0, min_sep=0.9, seed=20220504)
+
+
+def eo_two_species_small(precision=MIXED, Nx=32, Ny=16, Nz=32, n=300):
+    """eo_two_species on a grid the oracle finishes in seconds (n ions, a
+    cation excess of n / 15 balanced by the walls' surface charge)."""
+    n_neg = (n - n // 15) // 2
+    return eo_two_species(precision, Nx, Ny, Nz, n - n_neg, n_neg)
+
+
+def species_by_charge(q):
+    """Species of each ion for the two-species presets: 0 cation, 1 anion."""
+    import numpy as np
+    return (np.asarray(q) < 0).astype(np.int32)
+
+
 PRESETS = {
     "dry_channel_32": dry_channel_32,
     "wet_channel_128x64x128": wet_channel_128x64x128,
     "energy_channel_64": energy_channel_64,
     "iceo_channel_256x128x256": iceo_channel_256x128x256,
     "iceo_strip_256x128x256": iceo_strip_256x128x256,
+    "eo_two_species": eo_two_species,
 }

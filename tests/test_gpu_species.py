@@ -1,0 +1,86 @@
+"""A hydrodynamic kernel per species (App. B: ES kernel w = 7, beta = 7 for
+the cations, w = 4, beta = 8 for the anions, on one hydrodynamic grid)
+through the C ABI against the oracle: force spreading, velocity
+interpolation and one wet step of the two-species electro-osmotic channel.
+Tolerances as in test_gpu_parity.py."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from helpers import oracle_params, rel_l2, min_image_disp, mac_split, mac_join  # noqa: E402
+import paper_2204_14167_gb300 as dg  # noqa: E402
+from paper_2204_14167_gb300 import presets, synth  # noqa: E402
+from oracle import gridops, integrate  # noqa: E402
+
+TOL = {dg.FP64: dict(grid=1e-10, vel=1e-10, force=1e-10, step=1e-9),
+       dg.MIXED: dict(grid=1e-6, vel=1e-4, force=1e-4, step=1e-4)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+
+
+def _setup(prec, n=300, ymargin=None):
+    cfg, rec = presets.eo_two_species_small(prec, n=n)
+    ym = rec["ymargin"] if ymargin is None else ymargin
+    pos, q, _ = synth.ions(cfg.dims, rec["n_pos"], rec["n_neg"], rec["seed"], ym, rec["min_sep"])
+    sp = presets.species_by_charge(q)
+    dt = torch.float64 if prec == dg.FP64 else torch.float32
+    xd = torch.tensor(pos, dtype=dt, device="cuda").contiguous()
+    qd = torch.tensor(q, dtype=dt, device="cuda")
+    spd = torch.tensor(sp, dtype=torch.int32, device="cuda")
+    return cfg, xd, qd, spd, xd.double().cpu().numpy(), qd.double().cpu().numpy(), sp
+
+
+@pytest.mark.parametrize("prec", [dg.FP64, dg.MIXED])
+def test_species_spread_and_interpolation(prec):
+    cfg, xd, qd, spd, pos, q, sp = _setup(prec, n=241, ymargin=0.05)
+    rng = np.random.default_rng(41)
+    dt = xd.dtype
+    Fd = torch.tensor(rng.normal(size=(3, pos.shape[1])), dtype=dt, device="cuda")
+    h = dg.Discos(cfg)
+    p = oracle_params(cfg)
+    ks = p["kernel_hy_species"]
+    f = h.spread_force(xd, Fd, species=spd).double().cpu().numpy()
+    ref = mac_join(*gridops.spread_force_species(ks, sp, pos, Fd.double().cpu().numpy(), cfg.dims))
+    assert rel_l2(f, ref) < TOL[prec]["grid"]
+    Nx, Ny, Nz = cfg.dims
+    u = rng.normal(size=(Nz, Ny, Nx)); w = rng.normal(size=(Nz, Ny, Nx))
+    v = rng.normal(size=(Nz, Ny + 1, Nx)); v[:, 0] = 0; v[:, Ny] = 0
+    vd = torch.tensor(mac_join(u, v, w), dtype=dt, device="cuda")
+    V = h.interpolate_velocity(xd, vd, species=spd).double().cpu().numpy()
+    refV = gridops.interp_velocity_species(ks, sp, pos, *mac_split(vd.double().cpu().numpy(), cfg.dims))
+    assert rel_l2(V, refV) < TOL[prec]["vel"]
+    # the calls without species treat every ion as species 0
+    f0 = h.spread_force(xd, Fd).double().cpu().numpy()
+    ref0 = mac_join(*gridops.spread_force(ks[0], pos, Fd.double().cpu().numpy(), cfg.dims))
+    assert rel_l2(f0, ref0) < TOL[prec]["grid"]
+
+
+@pytest.mark.parametrize("prec", [dg.FP64, dg.MIXED])
+def test_species_wet_step(prec):
+    cfg, xd, qd, spd, pos, q, sp = _setup(prec)
+    h = dg.Discos(cfg)
+    x0 = xd.clone()
+    Fs = torch.empty_like(xd)
+    h.step(xd, qd, species=spd, step0=6, nsteps=1, F_out=Fs)
+    torch.cuda.synchronize()
+    p = oracle_params(cfg)
+    pair_dt = np.float64 if prec == dg.FP64 else np.float32
+    new, Fr, _, _ = integrate.wet_step(p, pos, q, sp, 6, pair_dtype=pair_dt)
+    assert rel_l2(Fs.double().cpu().numpy(), Fr) < TOL[prec]["force"]
+    d_gpu = min_image_disp(xd.double().cpu().numpy(), x0.double().cpu().numpy(), cfg.dims)
+    assert rel_l2(d_gpu, min_image_disp(new, pos, cfg.dims)) < TOL[prec]["step"]
+
+
+def test_species_config_checked():
+    cfg, _ = presets.eo_two_species_small(dg.FP64)
+    cfg.hy_w_s = [9, 4]
+    with pytest.raises(dg.DiscosError):
+        dg.Discos(cfg)
