@@ -22,7 +22,7 @@ replica, tag): tag 3 gives (Zxx, Zyy, Zzz, Zxy), tag 4 gives (Zxz, Zyz, -, -).
 
 Thermal forcing, Eq. thermforce, by random finite differences (only cited;
 reading): f_th = (kT/delta) [S(x + delta W/2) W - S(x - delta W/2) W] with W
-from Philox tag 2 per ion and delta = 1e-4 (1e-6 for the ES kernel: see
+from Philox tag 2 per ion and delta = 1e-4 (1e-7 for the ES kernel: see
 rfd_forcing).
 """
 import numpy as np
@@ -219,12 +219,14 @@ def rfd_forcing(kernel, pos, dims, kT, step, replica, seed, delta=None, first_in
     O(delta^2) for the Peskin kernels, whose first derivative is continuous.
     The ES kernel (Eq. eskernel) drops from exp(-beta) to 0 at the edge of
     its support, and a finite difference that straddles the edge picks up
-    that jump divided by delta; for ES kernels delta = 1e-6 (in double: the
-    rounding error of the difference stays near 1e-10 relative), which keeps
-    the stencil points of a few hundred ions clear of the edge."""
+    that jump divided by delta; near the edge its third derivative is also
+    unbounded, so the O(delta^2) error of the difference grows there.  For ES
+    kernels delta = 1e-7 (in double), where truncation and rounding are both
+    near 1e-9 relative and the stencil points of a few hundred ions stay
+    clear of the edge."""
     ks = kernel if isinstance(kernel, (list, tuple)) else [kernel]
     if delta is None:
-        delta = 1e-6 if any(k.kind == kernels.ES for k in ks) else 1e-4
+        delta = 1e-7 if any(k.kind == kernels.ES for k in ks) else 1e-4
     N = pos.shape[1]
     W = philox.ion_normals(N, step, replica, philox.TAG_RFD, seed, first_index)
     if species is None:

@@ -88,13 +88,13 @@ def test_thermal_forcing_of_one_species(species):
 
 
 def test_thermal_forcing_of_es_kernels_is_at_its_limit():
-    """The RFD of ES kernels is taken at delta = 1e-6: a ten times smaller
-    delta gives the same forcing to rounding for these positions (no
+    """The RFD of ES kernels is taken at delta = 1e-7: a ten times larger
+    delta gives the same forcing to O(delta^2) for these positions (no
     stencil point within delta |W| of a support edge), i.e. the default sits
     at the delta -> 0 limit that the reading asks for."""
     pos, sp, _, _ = _random_state(40, 24)
     ks = [K77, K48]
     a = stokes.rfd_forcing(ks, pos, DIMS, 1.0, 5, 0, 99, species=sp)
-    b = stokes.rfd_forcing(ks, pos, DIMS, 1.0, 5, 0, 99, delta=1e-7, species=sp)
+    b = stokes.rfd_forcing(ks, pos, DIMS, 1.0, 5, 0, 99, delta=1e-6, species=sp)
     for x, y in zip(a, b):
         assert np.linalg.norm(x - y) < 1e-6 * np.linalg.norm(y)
