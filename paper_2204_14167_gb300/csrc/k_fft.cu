@@ -909,12 +909,16 @@ cudaError_t tune_transforms_t(Params& P, Workspace& W, cudaStream_t s, float* be
   }
   // z: at least one 32-byte sector of consecutive x-modes per row access
   // (4 columns in float, 2 in double); narrower tiles can win on an
-  // L2-resident trial spectrum and lose on the step's larger ones
+  // L2-resident trial spectrum and lose on the step's larger ones.  With a
+  // fluid the trial is the three-field Stokes spectrum, the largest one.
   Q = P;
   const int tk0 = (int)(32 / sizeof(cplx<T>));
+  const bool mac = W.st_l1 != nullptr;   // the Stokes factors exist only with a fluid
   for (int tk = tk0; tk <= max_tile_z(P.Nz, sizeof(cplx<T>)) && e == cudaSuccess; tk *= 2) {
     Q.fz_tk = tk;
-    const float ms = time_it([&] { return fft_z<T>(Q, S, P.Ny, 1, 0, false, twz, s); });
+    const float ms = time_it([&] {
+      return mac ? fft_z_mac<T>(Q, S, false, twz, s) : fft_z<T>(Q, S, P.Ny, 1, 0, false, twz, s);
+    });
     if (ms < bz) { bz = ms; best_tk = tk; }
   }
   if (e0) cudaEventDestroy(e0);

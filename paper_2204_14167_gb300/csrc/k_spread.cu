@@ -194,6 +194,11 @@ __global__ void k_spread_charge_w(const T* __restrict__ x, const T* __restrict__
 }
 
 // LPI = lanes per ion: 4 for 4-point stencils (no idle lanes), else 8.
+// The three MAC components are spread by the same lanes one after another,
+// so the ion's data and its thermal draw are read and generated once, and
+// each lane evaluates its kernel weights (and derivatives) once per axis for
+// the two grid offsets a component can have (0 on its own face axis, 1/2 on
+// the others).
 template <typename T, int W, int LPI>
 __global__ void k_spread_force_w(const T* __restrict__ x, const T* __restrict__ F, int N, Params P,
                                  T* __restrict__ f, long long step, int rfd, const int* __restrict__ noise_index,
@@ -201,17 +206,16 @@ __global__ void k_spread_force_w(const T* __restrict__ x, const T* __restrict__ 
   constexpr int LOG = LPI == 4 ? 2 : 3;
   const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
   const KernelParams kp = P.khy;
-  const int c = blockIdx.y;
   int ion = spread_ion((blockIdx.x * blockDim.x + threadIdx.x) >> LOG, N, stride);
   int l = threadIdx.x & (LPI - 1);
   int gbase = (threadIdx.x & 31) & ~(LPI - 1);
   bool valid = ion < N && (P.hy_filter < 0 || sp[ion] == P.hy_filter);
   T p[3] = {T(0.5), T(0.5), T(0.5)};
-  T Fc = T(0);
+  T Fv[3] = {T(0), T(0), T(0)};
   T Wr[3] = {T(0), T(0), T(0)};
   if (valid) {
     p[0] = x[ion]; p[1] = x[N + ion]; p[2] = x[2 * N + ion];
-    Fc = F[(size_t)c * N + ion];
+    Fv[0] = F[ion]; Fv[1] = F[N + ion]; Fv[2] = F[2 * (size_t)N + ion];
     if (rfd) {
       T g[4];
       const int key = noise_index ? noise_index[ion] : ion;
@@ -219,76 +223,84 @@ __global__ void k_spread_force_w(const T* __restrict__ x, const T* __restrict__ 
       Wr[0] = g[0]; Wr[1] = g[1]; Wr[2] = g[2];
     }
   }
-  int st[3];
-  T wv[3], wd[3];
+  // this lane's weight and derivative at offset l, per axis, for grid
+  // points at offset 0 (h = 0) and 1/2 (h = 1)
+  int st[2][3];
+  T wv[2][3], wd[2][3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const T sd = p[d] - (d == c ? T(0) : T(0.5));
-    st[d] = stencil_start(sd, W);
-    const T z = sd - T(st[d] + l);
-    wv[d] = l < W ? kval(z, kp) : T(0);
-    wd[d] = (l < W && rfd) ? kder(z, kp) : T(0);
-  }
-  const T a = T(phys(P, T()).kT) * (c == 0 ? Wr[0] : (c == 1 ? Wr[1] : Wr[2]));
-  const int Nyg = (c == 1) ? Ny + 1 : Ny;
-  size_t off = 0;
-  if (c >= 1) off += (size_t)Nz * Ny * Nx;
-  if (c == 2) off += (size_t)Nz * (Ny + 1) * Nx;
-  T* g = f + off;
-  T wy[W], dy[W], wz[W], dz[W];
-  int roff[W];
+  for (int h = 0; h < 2; ++h)
 #pragma unroll
-  for (int j = 0; j < W; ++j) {
-    wy[j] = __shfl_sync(0xffffffffu, wv[1], gbase + j);
-    dy[j] = __shfl_sync(0xffffffffu, wd[1], gbase + j);
-    wz[j] = __shfl_sync(0xffffffffu, wv[2], gbase + j);
-    dz[j] = __shfl_sync(0xffffffffu, wd[2], gbase + j);
-    int iy = st[1] + j;
-    T sg = T(1);
-    bool ok;
-    if (c == 1) {             // y-faces 0..Ny; wall faces receive real + image = 0
-      if (iy < 0) { iy = -iy; sg = T(-1); }
-      else if (iy > Ny) { iy = 2 * Ny - iy; sg = T(-1); }
-      ok = iy > 0 && iy < Ny;
-    } else {                  // cell-centred in y
-      if (iy < 0) { iy = -1 - iy; sg = P.slip[0] ? T(1) : T(-1); }
-      else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = P.slip[1] ? T(1) : T(-1); }
-      ok = iy >= 0 && iy < Ny;
+    for (int d = 0; d < 3; ++d) {
+      const T sd = p[d] - (h == 0 ? T(0) : T(0.5));
+      st[h][d] = stencil_start(sd, W);
+      const T z = sd - T(st[h][d] + l);
+      wv[h][d] = l < W ? kval(z, kp) : T(0);
+      wd[h][d] = (l < W && rfd) ? kder(z, kp) : T(0);
     }
-    roff[j] = ok ? iy * Nx : 0;
-    const T keep = ok ? sg : T(0);
-    wy[j] *= keep;
-    dy[j] *= keep;
-  }
-  if (valid && l < W) {
-    const int ix = (st[0] + l) & (Nx - 1);
-    const T fx0 = Fc * wv[0];
-    const T r0 = a * Wr[0] * wd[0], r1 = a * Wr[1] * wv[0], r2 = a * Wr[2] * wv[0];
+  const T kT = T(phys(P, T()).kT);
 #pragma unroll
-    for (int jz = 0; jz < W; ++jz) {
-      const size_t zoff = (size_t)((st[2] + jz) & (Nz - 1)) * Nyg * Nx + ix;
+  for (int c = 0; c < 3; ++c) {
+    const int hx = c == 0 ? 0 : 1, hy = c == 1 ? 0 : 1, hz = c == 2 ? 0 : 1;
+    const T a = kT * Wr[c];
+    const int Nyg = (c == 1) ? Ny + 1 : Ny;
+    size_t off = 0;
+    if (c >= 1) off += (size_t)Nz * Ny * Nx;
+    if (c == 2) off += (size_t)Nz * (Ny + 1) * Nx;
+    T* g = f + off;
+    T wy[W], dy[W], wz[W], dz[W];
+    int roff[W];
 #pragma unroll
-      for (int jy = 0; jy < W; ++jy) {
-        if (wy[jy] == T(0) && dy[jy] == T(0)) continue;
-        T val = fx0 * wy[jy] * wz[jz];
-        if (rfd) val += r0 * wy[jy] * wz[jz] + r1 * dy[jy] * wz[jz] + r2 * wy[jy] * dz[jz];
-        atomicAdd(&g[zoff + roff[jy]], val);
+    for (int j = 0; j < W; ++j) {
+      wy[j] = __shfl_sync(0xffffffffu, wv[hy][1], gbase + j);
+      dy[j] = __shfl_sync(0xffffffffu, wd[hy][1], gbase + j);
+      wz[j] = __shfl_sync(0xffffffffu, wv[hz][2], gbase + j);
+      dz[j] = __shfl_sync(0xffffffffu, wd[hz][2], gbase + j);
+      int iy = st[hy][1] + j;
+      T sg = T(1);
+      bool ok;
+      if (c == 1) {             // y-faces 0..Ny; wall faces receive real + image = 0
+        if (iy < 0) { iy = -iy; sg = T(-1); }
+        else if (iy > Ny) { iy = 2 * Ny - iy; sg = T(-1); }
+        ok = iy > 0 && iy < Ny;
+      } else {                  // cell-centred in y: tangential, like image at a slip wall
+        if (iy < 0) { iy = -1 - iy; sg = P.slip[0] ? T(1) : T(-1); }
+        else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = P.slip[1] ? T(1) : T(-1); }
+        ok = iy >= 0 && iy < Ny;
+      }
+      roff[j] = ok ? iy * Nx : 0;
+      const T keep = ok ? sg : T(0);
+      wy[j] *= keep;
+      dy[j] *= keep;
+    }
+    if (valid && l < W) {
+      const int ix = (st[hx][0] + l) & (Nx - 1);
+      const T fx0 = Fv[c] * wv[hx][0];
+      const T r0 = a * Wr[0] * wd[hx][0], r1 = a * Wr[1] * wv[hx][0], r2 = a * Wr[2] * wv[hx][0];
+#pragma unroll
+      for (int jz = 0; jz < W; ++jz) {
+        const size_t zoff = (size_t)((st[hz][2] + jz) & (Nz - 1)) * Nyg * Nx + ix;
+#pragma unroll
+        for (int jy = 0; jy < W; ++jy) {
+          if (wy[jy] == T(0) && dy[jy] == T(0)) continue;
+          T val = fx0 * wy[jy] * wz[jz];
+          if (rfd) val += r0 * wy[jy] * wz[jz] + r1 * dy[jy] * wz[jz] + r2 * wy[jy] * dz[jz];
+          atomicAdd(&g[zoff + roff[jy]], val);
+        }
       }
     }
   }
 }
 
-// Single-precision spreading for 4-point stencils, one thread per ion.
-// The thread evaluates the 4 weights per axis once, walks the 16 x-rows
-// (jy, jz) of the 4 x 4 x 4 stencil, and adds each row's four values with
-// 16-byte vector reductions (red.global.add.v4.f32) on the aligned quads of
-// x that the row covers: one quad when the row starts on a multiple of 4,
-// else two, the other slots adding zero.  About 28 vector reductions per ion
-// and component instead of 64 scalar ones, and no work repeated across
-// lanes (the lane-group kernels above evaluate the weights and the thermal
-// draws once per lane).  Images, signs and thermal forcing are those of the
-// lane-group kernels.  Needs 16-byte aligned grids and Nx a multiple of 4
-// (quads never straddle the periodic wrap).
+// Single-precision charge spreading for 4-point stencils, one thread per
+// ion.  The thread evaluates the 4 weights per axis once, walks the 16
+// x-rows (jy, jz) of the 4 x 4 x 4 stencil, and adds each row's four values
+// with 16-byte vector reductions (atomicAdd on float4, red.global.add.v4.f32)
+// on the aligned quads of x that the row covers: one quad when the row
+// starts on a multiple of 4, else two, the other slots adding zero.  Images
+// and signs as in k_spread_charge_w.  Needs a 16-byte aligned grid and Nx a
+// multiple of 4 (quads never straddle the periodic wrap).  (For the MAC
+// forcing, a grid three times larger, the same scheme lost to the lane
+// groups: its scattered vector reductions thrash the L2.)
 __device__ __forceinline__ void red_row4(float* row, int ix0, int Nx, float v0, float v1, float v2, float v3) {
   const int o = ix0 & 3;
   const int q0 = ix0 - o;
@@ -434,10 +446,11 @@ cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, 
   int bs = 256;
   dim3 grid((unsigned)(((size_t)N * 8 + bs - 1) / bs), 3);
   const unsigned long long st = decorrelate ? spread_stride(N) : 0ull;
-  const dim3 grid4((unsigned)(((size_t)N * 4 + bs - 1) / bs), 3);
+  const dim3 grid4((unsigned)(((size_t)N * 4 + bs - 1) / bs), 1);
+  const dim3 grid8((unsigned)(((size_t)N * 8 + bs - 1) / bs), 1);
   auto one = [&](const Params& Q) {
     if (Q.khy.w == 4) k_spread_force_w<T, 4, 4><<<grid4, bs, 0, s>>>(x, F, N, Q, f, (long long)step, rfd ? 1 : 0, noise_index, st, species);
-    else if (Q.khy.w == 6) k_spread_force_w<T, 6, 8><<<grid, bs, 0, s>>>(x, F, N, Q, f, (long long)step, rfd ? 1 : 0, noise_index, st, species);
+    else if (Q.khy.w == 6) k_spread_force_w<T, 6, 8><<<grid8, bs, 0, s>>>(x, F, N, Q, f, (long long)step, rfd ? 1 : 0, noise_index, st, species);
     else k_spread_force<T><<<grid, bs, 0, s>>>(x, F, N, Q, f, (long long)step, rfd ? 1 : 0, noise_index, st, species);
     count_launches(1);
   };

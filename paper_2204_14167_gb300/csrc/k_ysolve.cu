@@ -589,6 +589,12 @@ __device__ __forceinline__ C<float> ldcf(const cplx<float>* p) {
 }
 __device__ __forceinline__ void stcf(cplx<float>* p, C<float> v, float s) { *p = cplx<float>{v.r * s, v.i * s}; }
 
+// Rows are handled in blocks of SB: the block's loads (spectra and factor
+// rows) are issued together before its sequential recurrence, so one memory
+// latency covers SB rows (the stores of a block may alias later loads only
+// through the in-place spectra, which is why the prefetch is explicit).
+constexpr int SB = 8;
+
 __global__ void k_poisson_sweep(cplx<float>* __restrict__ S, const float* __restrict__ piv,
                                 const unsigned char* __restrict__ skip, int Ny, int Nz, int Nxh, int Px,
                                 float norm) {
@@ -602,17 +608,43 @@ __global__ void k_poisson_sweep(cplx<float>* __restrict__ S, const float* __rest
   cplx<float>* col = S + (size_t)kz * Ny * Px + kx;
   // forward y_j = piv_j (b_j + y_{j-1}), in place
   C<float> y = cz<float>();
-  for (int j = 0; j < Ny; ++j) {
-    const float m = piv[(size_t)j * M + mode];
-    y = cscale(m, cadd2(ldcf(col + (size_t)j * Px), y));
-    stcf(col + (size_t)j * Px, y, 1.f);
+  for (int jb = 0; jb < Ny; jb += SB) {
+    C<float> b[SB];
+    float m[SB];
+#pragma unroll
+    for (int r = 0; r < SB; ++r) {
+      const int j = jb + r;
+      b[r] = j < Ny ? ldcf(col + (size_t)j * Px) : cz<float>();
+      m[r] = j < Ny ? piv[(size_t)j * M + mode] : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < SB; ++r) {
+      const int j = jb + r;
+      if (j < Ny) {
+        y = cscale(m[r], cadd2(b[r], y));
+        stcf(col + (size_t)j * Px, y, 1.f);
+      }
+    }
   }
   // backward x_j = y_j + piv_j x_{j+1}, x_{Ny-1} = y_{Ny-1}
   C<float> xn = cz<float>();
-  for (int j = Ny - 1; j >= 0; --j) {
-    const float a = j < Ny - 1 ? piv[(size_t)j * M + mode] : 0.f;
-    xn = cfma(a, xn, ldcf(col + (size_t)j * Px));
-    stcf(col + (size_t)j * Px, xn, norm);
+  for (int jt = Ny - 1; jt >= 0; jt -= SB) {
+    C<float> b[SB];
+    float a[SB];
+#pragma unroll
+    for (int r = 0; r < SB; ++r) {
+      const int j = jt - r;
+      b[r] = j >= 0 ? ldcf(col + (size_t)j * Px) : cz<float>();
+      a[r] = (j >= 0 && j < Ny - 1) ? piv[(size_t)j * M + mode] : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < SB; ++r) {
+      const int j = jt - r;
+      if (j >= 0) {
+        xn = cfma(a[r], xn, b[r]);
+        stcf(col + (size_t)j * Px, xn, norm);
+      }
+    }
   }
 }
 
@@ -645,67 +677,128 @@ __global__ void k_stokes_sweep(cplx<float>* __restrict__ S, cplx<float>* __restr
   {
     C<float> gprev = gsum(ldcf(Su), ldcf(Sw));
     C<float> y1 = cz<float>(), y2 = cz<float>();
-    for (int f = 1; f < Ny; ++f) {
-      const C<float> g = gsum(ldcf(Su + (size_t)f * Px), ldcf(Sw + (size_t)f * Px));
-      const C<float> fy = ldcf(Sv + (size_t)f * Px);
-      const C<float> rhs = cscale(ieta, C<float>{K2 * fy.r + (g.r - gprev.r), K2 * fy.i + (g.i - gprev.i)});
-      const float l1 = L1[(size_t)f * M + mode], l2 = L2[(size_t)f * M + mode];
-      const C<float> y = csub2(csub2(rhs, cscale(l1, y1)), cscale(l2, y2));
-      stcf(Sv + (size_t)f * Px, y, 1.f);
-      y2 = y1; y1 = y; gprev = g;
+    for (int fb = 1; fb < Ny; fb += SB) {
+      C<float> g[SB], fy[SB];
+      float l1[SB], l2[SB];
+#pragma unroll
+      for (int r = 0; r < SB; ++r) {
+        const int f = fb + r;
+        const bool in = f < Ny;
+        g[r] = in ? gsum(ldcf(Su + (size_t)f * Px), ldcf(Sw + (size_t)f * Px)) : cz<float>();
+        fy[r] = in ? ldcf(Sv + (size_t)f * Px) : cz<float>();
+        l1[r] = in ? L1[(size_t)f * M + mode] : 0.f;
+        l2[r] = in ? L2[(size_t)f * M + mode] : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < SB; ++r) {
+        const int f = fb + r;
+        if (f < Ny) {
+          const C<float> rhs =
+              cscale(ieta, C<float>{K2 * fy[r].r + (g[r].r - gprev.r), K2 * fy[r].i + (g[r].i - gprev.i)});
+          const C<float> y = csub2(csub2(rhs, cscale(l1[r], y1)), cscale(l2[r], y2));
+          stcf(Sv + (size_t)f * Px, y, 1.f);
+          y2 = y1; y1 = y; gprev = g[r];
+        }
+      }
     }
   }
   // B: v_f = di_f y_f - l1_{f+1} v_{f+1} - l2_{f+2} v_{f+2}, f = Ny-1..1 (over y, unscaled)
   {
     C<float> v1 = cz<float>(), v2 = cz<float>();
-    for (int f = Ny - 1; f >= 1; --f) {
-      const float a1 = f + 1 < Ny ? L1[(size_t)(f + 1) * M + mode] : 0.f;
-      const float a2 = f + 2 < Ny ? L2[(size_t)(f + 2) * M + mode] : 0.f;
-      const C<float> v = csub2(csub2(cscale(DI[(size_t)f * M + mode], ldcf(Sv + (size_t)f * Px)), cscale(a1, v1)),
-                               cscale(a2, v2));
-      stcf(Sv + (size_t)f * Px, v, 1.f);
-      v2 = v1; v1 = v;
+    for (int ft = Ny - 1; ft >= 1; ft -= SB) {
+      C<float> yv[SB];
+      float d[SB], a1[SB], a2[SB];
+#pragma unroll
+      for (int r = 0; r < SB; ++r) {
+        const int f = ft - r;
+        const bool in = f >= 1;
+        yv[r] = in ? ldcf(Sv + (size_t)f * Px) : cz<float>();
+        d[r] = in ? DI[(size_t)f * M + mode] : 0.f;
+        a1[r] = (in && f + 1 < Ny) ? L1[(size_t)(f + 1) * M + mode] : 0.f;
+        a2[r] = (in && f + 2 < Ny) ? L2[(size_t)(f + 2) * M + mode] : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < SB; ++r) {
+        const int f = ft - r;
+        if (f >= 1) {
+          const C<float> v = csub2(csub2(cscale(d[r], yv[r]), cscale(a1[r], v1)), cscale(a2[r], v2));
+          stcf(Sv + (size_t)f * Px, v, 1.f);
+          v2 = v1; v1 = v;
+        }
+      }
     }
   }
   // C: the pressure row by row from a window (v_{j-1}, v_j, v_{j+1}, v_{j+2})
   // (wall faces 0 and Ny carry v = 0), then the forward sweeps of the u and
-  // w tridiagonals, in place; face j of v is final (scaled) once row j is done
+  // w tridiagonals, in place; face j of v is final (scaled) once row j is
+  // done.  A block loads the v faces it will need (jb + 2 .. jb + SB + 1)
+  // before it overwrites faces jb .. jb + SB - 1.
   {
     C<float> vm1 = cz<float>(), v0 = cz<float>();
     C<float> vp1 = Ny >= 2 ? ldcf(Sv + (size_t)Px) : cz<float>();
-    C<float> vp2 = Ny >= 3 ? ldcf(Sv + 2 * (size_t)Px) : cz<float>();
     C<float> yu = cz<float>(), yw = cz<float>();
-    for (int j = 0; j < Ny; ++j) {
-      const C<float> fx = ldcf(Su + (size_t)j * Px), fz = ldcf(Sw + (size_t)j * Px);
-      // A_c's diagonal: the tangential ghost adds +1 at a no-slip wall, -1 at a slip wall
-      const float a = K2 + 2.f + (j == 0 ? wb : 0.f) + (j == Ny - 1 ? wt : 0.f);
-      C<float> acd = cscale(a, csub2(vp1, v0));
-      if (j >= 1) acd = csub2(acd, csub2(v0, vm1));
-      if (j <= Ny - 2) acd = csub2(acd, csub2(vp2, vp1));
-      const C<float> p = cscale(mik2, cfma(eta, acd, gsum(fx, fz)));
-      if (Sp) Sp[(size_t)kz * Ny * Px + kx + (size_t)j * Px] = cplx<float>{p.r * norm, p.i * norm};
-      const C<float> bu = cscale(ieta, C<float>{fx.r + gxr * p.r + gxi * p.i, fx.i + gxr * p.i - gxi * p.r});
-      const C<float> bw = cscale(ieta, C<float>{fz.r + gzr * p.r + gzi * p.i, fz.i + gzr * p.i - gzi * p.r});
-      const float c = CI[(size_t)j * M + mode];
-      yu = cscale(c, cadd2(bu, yu));
-      yw = cscale(c, cadd2(bw, yw));
-      stcf(Su + (size_t)j * Px, yu, 1.f);
-      stcf(Sw + (size_t)j * Px, yw, 1.f);
-      stcf(Sv + (size_t)j * Px, v0, norm);
-      vm1 = v0; v0 = vp1; vp1 = vp2;
-      vp2 = j + 3 <= Ny - 1 ? ldcf(Sv + (size_t)(j + 3) * Px) : cz<float>();
+    for (int jb = 0; jb < Ny; jb += SB) {
+      C<float> fx[SB], fz[SB], vn[SB];
+      float c[SB];
+#pragma unroll
+      for (int r = 0; r < SB; ++r) {
+        const int j = jb + r;
+        const bool in = j < Ny;
+        fx[r] = in ? ldcf(Su + (size_t)j * Px) : cz<float>();
+        fz[r] = in ? ldcf(Sw + (size_t)j * Px) : cz<float>();
+        c[r] = in ? CI[(size_t)j * M + mode] : 0.f;
+        vn[r] = (j + 2 <= Ny - 1) ? ldcf(Sv + (size_t)(j + 2) * Px) : cz<float>();   // v_{j+2}
+      }
+#pragma unroll
+      for (int r = 0; r < SB; ++r) {
+        const int j = jb + r;
+        if (j < Ny) {
+          const C<float> vp2 = vn[r];
+          // A_c's diagonal: the tangential ghost adds +1 at a no-slip wall, -1 at a slip wall
+          const float a = K2 + 2.f + (j == 0 ? wb : 0.f) + (j == Ny - 1 ? wt : 0.f);
+          C<float> acd = cscale(a, csub2(vp1, v0));
+          if (j >= 1) acd = csub2(acd, csub2(v0, vm1));
+          if (j <= Ny - 2) acd = csub2(acd, csub2(vp2, vp1));
+          const C<float> p = cscale(mik2, cfma(eta, acd, gsum(fx[r], fz[r])));
+          if (Sp) Sp[(size_t)kz * Ny * Px + kx + (size_t)j * Px] = cplx<float>{p.r * norm, p.i * norm};
+          const C<float> bu =
+              cscale(ieta, C<float>{fx[r].r + gxr * p.r + gxi * p.i, fx[r].i + gxr * p.i - gxi * p.r});
+          const C<float> bw =
+              cscale(ieta, C<float>{fz[r].r + gzr * p.r + gzi * p.i, fz[r].i + gzr * p.i - gzi * p.r});
+          yu = cscale(c[r], cadd2(bu, yu));
+          yw = cscale(c[r], cadd2(bw, yw));
+          stcf(Su + (size_t)j * Px, yu, 1.f);
+          stcf(Sw + (size_t)j * Px, yw, 1.f);
+          stcf(Sv + (size_t)j * Px, v0, norm);
+          vm1 = v0; v0 = vp1; vp1 = vp2;
+        }
+      }
     }
     Sv[(size_t)Ny * Px] = cplx<float>{0.f, 0.f};
   }
   // D: backward x_j = y_j + ci_j x_{j+1}, x_{Ny-1} = y_{Ny-1}
   {
     C<float> xu = cz<float>(), xw = cz<float>();
-    for (int j = Ny - 1; j >= 0; --j) {
-      const float a = j < Ny - 1 ? CI[(size_t)j * M + mode] : 0.f;
-      xu = cfma(a, xu, ldcf(Su + (size_t)j * Px));
-      xw = cfma(a, xw, ldcf(Sw + (size_t)j * Px));
-      stcf(Su + (size_t)j * Px, xu, norm);
-      stcf(Sw + (size_t)j * Px, xw, norm);
+    for (int jt = Ny - 1; jt >= 0; jt -= SB) {
+      C<float> bu[SB], bw[SB];
+      float a[SB];
+#pragma unroll
+      for (int r = 0; r < SB; ++r) {
+        const int j = jt - r;
+        bu[r] = j >= 0 ? ldcf(Su + (size_t)j * Px) : cz<float>();
+        bw[r] = j >= 0 ? ldcf(Sw + (size_t)j * Px) : cz<float>();
+        a[r] = (j >= 0 && j < Ny - 1) ? CI[(size_t)j * M + mode] : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < SB; ++r) {
+        const int j = jt - r;
+        if (j >= 0) {
+          xu = cfma(a[r], xu, bu[r]);
+          xw = cfma(a[r], xw, bw[r]);
+          stcf(Su + (size_t)j * Px, xu, norm);
+          stcf(Sw + (size_t)j * Px, xw, norm);
+        }
+      }
     }
   }
 }

@@ -10,13 +10,15 @@ from . import RunConfig, BC_DIRICHLET, BC_NEUMANN, KERNEL_PESKIN4, KERNEL_PESKIN
 from . import mobility
 
 WCA = 2.0 ** (1.0 / 6.0)
-A_WET_PESKIN4 = 0.91     # hydrodynamic radius of the 4-point kernel in grid units
-# hydrodynamic radii of the two ES kernels of App. B (cations: w = 7,
-# beta = 7; anions: w = 4, beta = 8), in grid units, measured with this
-# library's Stokes solver (calibrate.hydrodynamic_radius on a 64 x 64 x 64
-# channel, mid-channel perpendicular mobility)
-A_WET_ES77 = 1.60
-A_WET_ES48 = 0.95
+# Hydrodynamic radii in grid units of the 4-point kernel and of the two ES
+# kernels of App. B (cations: w = 7, beta = 7; anions: w = 4, beta = 8),
+# measured with this library's own Stokes solver (Sec. III.A): the
+# mid-channel perpendicular mobility of one particle (8 sub-cell offsets,
+# FP64) in a 128^3 no-slip channel, matched to Eq. mob_analytic by
+# calibrate.hydrodynamic_radius (64^3 gives the same to 0.2 %).
+A_WET_PESKIN4 = 1.25
+A_WET_ES77 = 2.08
+A_WET_ES48 = 1.08
 
 
 def _wca(sigma):
@@ -44,7 +46,7 @@ def dry_channel_32(precision=FP64):
 def wet_channel_128x64x128(precision=MIXED):
     """128 x 64 x 128 channel with dielectric (Neumann) walls, 10k + 10k ions,
     Debye length ~4 cells (l_B = 0.261), E_x = 0.05, fluctuating Stokes with
-    no-slip walls, 50% wet (4-point kernel, a_w = 0.91, a_t = a_w / 2).
+    no-slip walls, 50% wet (4-point kernel, a_w = 1.25, a_t = a_w / 2).
     dt = 0.001 keeps D_tot dt / a_t^2 ~ 0.01, the paper's ratio of time step
     to diffusive time (Sec. III.C)."""
     Ny = 64
@@ -100,7 +102,7 @@ def iceo_channel_256x128x256(precision=MIXED):
     cfg.max_ions = 400000
     # explicit Euler-Maruyama is stable near WCA contact for dt D_tot U''(r) < 1;
     # at the placement minimum r = 0.9 sigma = 0.54, U'' ~ 6500 kT per cell^2,
-    # and with D_tot ~ 2.2 this gives dt = 5e-5 (0.7)
+    # and with D_tot = 2 / a_w = 1.6 this gives dt = 5e-5 (0.5)
     cfg.dt = 5e-5
     for k, v in _wca(0.6).items():
         setattr(cfg, k, v)

@@ -127,15 +127,15 @@ def test_unaligned_grids(prec):
     a = torch.tensor(rho, dtype=_dtype(prec), device="cuda")
     b = torch.zeros(G + 1, dtype=_dtype(prec), device="cuda")[1:]
     b.copy_(a)
-    pa = h.solve_poisson(a).double().cpu().numpy()
-    pb = h.solve_poisson(b, out=torch.zeros(G + 1, dtype=_dtype(prec), device="cuda")[1:]).double().cpu().numpy()
+    pa = h.solve_poisson(a).double().cpu().numpy().ravel()
+    pb = h.solve_poisson(b, out=torch.zeros(G + 1, dtype=_dtype(prec), device="cuda")[1:]).double().cpu().numpy().ravel()
     ref = poisson.solve(rho.reshape(Nz, Ny, Nx), cfg.bc, cfg.lB, cfg.phi_b, cfg.surf_charge).ravel()
     assert rel_l2(pa, ref) < TOL[prec]["phi"]
     assert rel_l2(pb, ref) < TOL[prec]["phi"]
     xd, qd, pos, q, _ = _setup(cfg, rec, prec)
     ra = h.spread_charge(xd, qd).double().cpu().numpy().ravel()
     rb = h.spread_charge(xd, qd, out=torch.zeros(G + 1, dtype=_dtype(prec), device="cuda")[1:])
-    assert rel_l2(rb.double().cpu().numpy(), ra) < TOL[prec]["grid"]
+    assert rel_l2(rb.double().cpu().numpy().ravel(), ra) < TOL[prec]["grid"]
     ea = h.interpolate_efield(xd, torch.tensor(pa, dtype=_dtype(prec), device="cuda")).double().cpu().numpy()
     ub = torch.zeros(G + 1, dtype=_dtype(prec), device="cuda")[1:]
     ub.copy_(torch.tensor(pa, dtype=_dtype(prec), device="cuda"))

@@ -15,7 +15,12 @@ import paper_2204_14167_gb300 as dg  # noqa: E402
 from paper_2204_14167_gb300 import presets, synth  # noqa: E402
 from oracle import gridops, integrate  # noqa: E402
 
-TOL = {dg.FP64: dict(grid=1e-10, vel=1e-10, force=1e-10, step=1e-9),
+# FP64 steps at 1e-8: the oracle's thermal forcing is a finite difference
+# (delta = 1e-7 for the ES kernel), whose truncation and rounding errors are
+# both near 1e-9 relative because the ES kernel's third derivative is
+# unbounded at the edge of its support; the GPU evaluates the delta -> 0
+# limit exactly.
+TOL = {dg.FP64: dict(grid=1e-10, vel=1e-10, force=1e-10, step=1e-8),
        dg.MIXED: dict(grid=1e-6, vel=1e-4, force=1e-4, step=1e-4)}
 
 
