@@ -205,15 +205,19 @@ __device__ __forceinline__ void normals4(u32x4 c, uint64_t seed, double out[4]) 
   sincospi(2.0 * u3, &s3, &c3);
   out[0] = a * c1; out[1] = a * s1; out[2] = b * c3; out[3] = b * s3;
 }
+// Single precision: the hardware approximations of log and sin/cos (absolute
+// error near 2^-21 on these arguments, far below the mixed path's
+// tolerances) keep the Box-Muller transform off the slow library paths.
 __device__ __forceinline__ void normals4(u32x4 c, uint64_t seed, float out[4]) {
   u32x4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
   const float s = 2.3283064365386963e-10f, h = 1.1641532182693481e-10f;  // 2^-32, 2^-33
+  const float twopi = 6.283185307179586f;
   float u0 = fmaf((float)r.x, s, h), u1 = fmaf((float)r.y, s, h);
   float u2 = fmaf((float)r.z, s, h), u3 = fmaf((float)r.w, s, h);
-  float a = sqrtf(-2.0f * logf(u0)), b = sqrtf(-2.0f * logf(u2));
+  float a = sqrtf(-2.0f * __logf(u0)), b = sqrtf(-2.0f * __logf(u2));
   float s1, c1, s3, c3;
-  sincospif(2.0f * u1, &s1, &c1);
-  sincospif(2.0f * u3, &s3, &c3);
+  __sincosf(twopi * u1, &s1, &c1);
+  __sincosf(twopi * u3, &s3, &c3);
   out[0] = a * c1; out[1] = a * s1; out[2] = b * c3; out[3] = b * s3;
 }
 
@@ -232,9 +236,9 @@ __device__ __forceinline__ void normals2(u32x4 c, uint64_t seed, float out[2]) {
   u32x4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
   const float s = 2.3283064365386963e-10f, h = 1.1641532182693481e-10f;
   float u0 = fmaf((float)r.x, s, h), u1 = fmaf((float)r.y, s, h);
-  float a = sqrtf(-2.0f * logf(u0));
+  float a = sqrtf(-2.0f * __logf(u0));
   float s1, c1;
-  sincospif(2.0f * u1, &s1, &c1);
+  __sincosf(6.283185307179586f * u1, &s1, &c1);
   out[0] = a * c1; out[1] = a * s1;
 }
 

@@ -668,6 +668,7 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
     P.fx_pp = default_fx_pairs(c.Nx);
     P.fx_threads = 256;
     P.fx_staged = c.Nx >= 32 ? 1 : 0;
+    P.fz_tma = (c.precision == DISCOS_MIXED && c.Nz <= 256) ? 1 : 0;
     P.fz_tk = default_tile_z(c.Nz, elem);
   }
   {
@@ -1153,7 +1154,7 @@ discos_status discos_tune_transforms(discos_handle* h, int* fx_pairs, int* fx_th
   if (e != cudaSuccess) return cuda_status(e, "discos_tune_transforms");
   if (fx_pairs) *fx_pairs = h->P.fx_staged ? 0 : h->P.fx_pp;
   if (fx_threads) *fx_threads = h->P.fx_threads;
-  if (fz_tile) *fz_tile = h->P.fz_tk;
+  if (fz_tile) *fz_tile = h->P.fz_tma ? 0 : h->P.fz_tk;
   if (ms) { ms[0] = best[0]; ms[1] = best[1]; }
   return DISCOS_OK;
 }
@@ -1162,24 +1163,25 @@ discos_status discos_set_transform_shape(discos_handle* h, int fx_pairs, int fx_
   if (!h) return invalid("null handle");
   const size_t elem = h->mixed ? 2 * sizeof(float) : 2 * sizeof(double);
   const int N = h->P.Nx;
+  if (fz_tile == 0) {
+    if (!h->mixed || h->P.Nz > 256) return invalid("the tiled z transform (fz_tile = 0) needs MIXED and Nz <= 256");
+  } else if (fz_tile < 1 || (fz_tile & (fz_tile - 1)) || fz_tile > max_tile_z(h->P.Nz, elem)) {
+    return invalid("fz_tile: 0 or a power of two up to the shared-memory limit");
+  }
   if (fx_pairs == 0) {
     if (N < 32) return invalid("the staged x transform (fx_pairs = 0) needs Nx >= 32");
-    if (fz_tile < 1 || (fz_tile & (fz_tile - 1)) || fz_tile > max_tile_z(h->P.Nz, elem))
-      return invalid("fz_tile: a power of two up to the shared-memory limit");
-    h->P.fx_staged = 1;
-    h->P.fz_tk = fz_tile;
-    return DISCOS_OK;
+  } else {
+    if (fx_pairs < 1 || (size_t)fx_pairs * N > 2048 ||
+        (2 * (size_t)fx_pairs * N + N / 2) * elem + 2 * (size_t)fx_pairs * elem > 48 * 1024)
+      return invalid("fx_pairs: 0, or 1 .. 2048 / Nx row pairs within 48 KB of shared memory");
+    if (fx_threads < 32 || fx_threads > 1024 || fx_threads % 32)
+      return invalid("fx_threads: a multiple of 32 in 32..1024");
+    h->P.fx_pp = fx_pairs;
+    h->P.fx_threads = fx_threads;
   }
-  if (fx_pairs < 1 || (size_t)fx_pairs * N > 2048 ||
-      (2 * (size_t)fx_pairs * N + N / 2) * elem + 2 * (size_t)fx_pairs * elem > 48 * 1024)
-    return invalid("fx_pairs: 1 .. 2048 / Nx row pairs within 48 KB of shared memory");
-  if (fx_threads < 32 || fx_threads > 1024 || fx_threads % 32) return invalid("fx_threads: a multiple of 32 in 32..1024");
-  if (fz_tile < 1 || (fz_tile & (fz_tile - 1)) || fz_tile > max_tile_z(h->P.Nz, elem))
-    return invalid("fz_tile: a power of two up to the shared-memory limit");
-  h->P.fx_pp = fx_pairs;
-  h->P.fx_threads = fx_threads;
-  h->P.fx_staged = 0;
-  h->P.fz_tk = fz_tile;
+  h->P.fx_staged = fx_pairs == 0 ? 1 : 0;
+  h->P.fz_tma = fz_tile == 0 ? 1 : 0;
+  if (fz_tile > 0) h->P.fz_tk = fz_tile;
   return DISCOS_OK;
 }
 

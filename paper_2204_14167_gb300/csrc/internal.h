@@ -56,6 +56,7 @@ struct Params {
   int max_refine;              // residual refinement sweeps of the mixed Poisson solve
   int fx_pp, fx_threads, fz_tk;  // transform launch shapes (k_fft.cu; discos_tune_transforms)
   int fx_staged;               // 1: bulk-staged persistent x transforms (fx_pp, fx_threads unused)
+  int fz_tma;                  // 1: TMA-tiled z transforms (single precision, 16 <= Nz <= 256; fz_tk unused)
   // metal strip in the bottom wall (k_strip.cu): Dirichlet on the cell columns [strip_i0, strip_i1) with
   // phi_m(x) = strip_phi + E_ext[0] (x - strip_xc); strip_singular: the all-dielectric base operator is
   // singular (top wall Neumann); strip_walls: the sum of the base solve's wall terms over the grid

@@ -10,6 +10,8 @@
 //    warp-parallel scans over pre-factored pivots (k_ysolve.cu).
 #include <atomic>
 #include <type_traits>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include "internal.h"
 #include "bulk.cuh"
 
@@ -91,7 +93,7 @@ template <typename T>
 __global__ void k_rfft_x(const T* __restrict__ in, int R, int N, int logN, int Px, cplx<T>* __restrict__ out,
                          T scale, int Nyr, T add0, T add1, const cplx<T>* __restrict__ tw, int pairs_per_block,
                          const T* __restrict__ add0x) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int PP = pairs_per_block;
   cplx<T>* bufa = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* bufb = bufa + (size_t)PP * N;
@@ -136,7 +138,7 @@ __global__ void k_rfft_x(const T* __restrict__ in, int R, int N, int logN, int P
 template <typename T>
 __global__ void k_irfft_x(const cplx<T>* __restrict__ in, int R, int N, int logN, int Px, T* __restrict__ out,
                           T scale, const cplx<T>* __restrict__ tw, int pairs_per_block) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int PP = pairs_per_block;
   cplx<T>* bufa = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* bufb = bufa + (size_t)PP * N;
@@ -237,7 +239,7 @@ template <typename T, int P>
 __global__ void k_rfft_x_w(const T* __restrict__ in, int R, int Px, cplx<T>* __restrict__ out, T scale, int Nyr,
                            T add0, T add1, const cplx<T>* __restrict__ tw, const T* __restrict__ add0x) {
   constexpr int N = 32 * P;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   cplx<T>* sz = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)wib * 32 * (P + 1);
   const int ra = 2 * (blockIdx.x * (blockDim.x >> 5) + wib), rb = ra + 1;
@@ -280,7 +282,7 @@ template <typename T, int P>
 __global__ void k_irfft_x_w(const cplx<T>* __restrict__ in, int R, int Px, T* __restrict__ out, T scale,
                             const cplx<T>* __restrict__ tw) {
   constexpr int N = 32 * P;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   cplx<T>* sz = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)wib * 32 * (P + 1);
   const int ra = 2 * (blockIdx.x * (blockDim.x >> 5) + wib), rb = ra + 1;
@@ -400,7 +402,7 @@ __global__ void k_rfft_x_staged(const T* __restrict__ in, int R, int Px, cplx<T>
                                 const T* __restrict__ add0x, unsigned* __restrict__ fault) {
   constexpr int N = 32 * P;
   const int C = 2 * (blockDim.x >> 5);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   T* buf = reinterpret_cast<T*>(smem_raw + 32);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -473,7 +475,7 @@ __global__ void k_irfft_x_staged(const cplx<T>* __restrict__ in, int R, int Px, 
                                  const cplx<T>* __restrict__ tw, unsigned* __restrict__ fault) {
   constexpr int N = 32 * P;
   const int C = 2 * (blockDim.x >> 5);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw + 32);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -580,6 +582,94 @@ __global__ void k_fft_z_w(cplx<T>* __restrict__ data, int Nyr, int Px, int Nxh, 
   }
 }
 
+
+// ------------------------------------------------------------------------
+// TMA-tiled z transform (single precision, 16 <= Nz <= 256).  One CTA per
+// (32 x-modes, y row, field): a 3-D tensor map over the field's spectrum
+// ([Px complex as 2 Px floats][Nyr][Nz]) lets one cp.async.bulk.tensor copy
+// bring the whole [Nz][32] column tile into shared memory, completing on an
+// mbarrier.  The CTA's 8 warps then run the Nz = N1 x 16 point transform as
+// two passes of register DFTs with the lanes across the 32 columns, so each
+// access to the tile is one conflict-free row: pass 1, for each i1, the
+// 16-point DFT of x[i1 + N1 m] over m times W^(i1 k2), back into the same
+// rows of the tile; pass 2, for each k2, the N1-point DFT over i1, written
+// as X[k2 + 16 k1] straight to the spectrum (one coalesced 256-byte row per
+// warp access; padding columns are skipped).  Several CTAs per SM keep
+// their tiles in flight.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, unsigned bytes,
+                                            uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+struct ZField {
+  cplx<float>* base;   // the field's spectrum [Nz][Nyr][Px]
+  int Nyr;
+};
+
+template <int N1>
+__global__ void __launch_bounds__(256) k_fft_z_tma(const __grid_constant__ CUtensorMap m0,
+                                                   const __grid_constant__ CUtensorMap m1,
+                                                   const __grid_constant__ CUtensorMap m2, ZField f0, ZField f1,
+                                                   ZField f2, int Px, int Nxh, int inverse,
+                                                   const cplx<float>* __restrict__ tw, unsigned* __restrict__ fault) {
+  constexpr int N2 = 16, Nz = N1 * N2;
+  const int field = blockIdx.z;
+  const ZField F = field == 0 ? f0 : (field == 1 ? f1 : f2);
+  const CUtensorMap* map = field == 0 ? &m0 : (field == 1 ? &m1 : &m2);
+  const int kx0 = blockIdx.x * 32, y = blockIdx.y;
+  if (y >= F.Nyr) return;                           // whole blocks
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  cplx<float>* tile = reinterpret_cast<cplx<float>*>(smem_raw + 128);     // [Nz][32]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) tma_load_3d(tile, map, 2 * kx0, y, 0, (unsigned)(Nz * 32 * sizeof(cplx<float>)), bar);
+  const bool ok = mbar_wait(bar, 0);
+  if (!__syncthreads_and(ok)) {
+    if (threadIdx.x == 0) {
+      if (fault) atomicOr(fault, FAULT_ASYNC_WAIT);
+      mbar_wait(bar, 0);                            // let the copy land before the CTA leaves
+    }
+    return;
+  }
+  const bool inv = inverse != 0;
+  for (int i1 = w; i1 < N1; i1 += nw) {
+    cplx<float> v[N2];
+#pragma unroll
+    for (int m = 0; m < N2; ++m) v[m] = tile[(i1 + N1 * m) * 32 + lane];
+    reg_dft<float, N2>(v, tw, Nz, inv);
+#pragma unroll
+    for (int p = 0; p < N2; ++p) {
+      const int k2 = brev_c<N2>(p);
+      tile[(i1 + N1 * k2) * 32 + lane] = p == 0 ? v[p] : cmul(v[p], twid(tw, i1 * k2, Nz, inv));
+    }
+  }
+  __syncthreads();
+  const bool col_ok = kx0 + lane < Nxh;
+  cplx<float>* col = F.base + (size_t)y * Px + kx0 + lane;
+  const size_t zs = (size_t)F.Nyr * Px;
+  for (int k2 = w; k2 < N2; k2 += nw) {
+    cplx<float> u[N1];
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) u[i1] = tile[(i1 + N1 * k2) * 32 + lane];
+    reg_dft<float, N1>(u, tw, Nz, inv);
+    if (col_ok) {
+#pragma unroll
+      for (int p = 0; p < N1; ++p) col[(size_t)(k2 + N2 * brev_c<N1>(p)) * zs] = u[p];
+    }
+  }
+}
+
 }  // namespace
 
 // Default launch shapes of the transforms (discos_tune_transforms may replace
@@ -667,7 +757,6 @@ cudaError_t rfft_x_staged(const Params& P, const T* in, int R, cplx<T>* out, T s
 template <typename T, int PP>
 cudaError_t irfft_x_staged(const Params& P, const cplx<T>* in, int R, T* out, T scale, const cplx<T>* tw,
                            cudaStream_t s) {
-  constexpr int N = 32 * PP;
   const int W = staged_warps(P.Px * sizeof(cplx<T>)), C = 2 * W;
   const size_t sm = 32 + XS_NB * (size_t)C * P.Px * sizeof(cplx<T>) + (size_t)W * 32 * (PP + 1) * sizeof(cplx<T>);
   int grid = 0;
@@ -778,6 +867,75 @@ void fft_z_dispatch(const Params& P, dim3 grid, int threads, cplx<T>* data, int 
   }
 }
 
+
+// The driver's tensor-map encoder, fetched once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::atomic<int> state{0};
+  if (state.load() == 0) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess && p)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    state.store(fn ? 1 : 2);
+  }
+  return fn;
+}
+
+// Tensor map of one field's spectrum [Nz][Nyr][Px] (complex as 2 floats),
+// box [32 complex][1][Nz].
+bool encode_z_map(CUtensorMap* map, cplx<float>* base, int Px, int Nyr, int Nz) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * Px, (cuuint64_t)Nyr, (cuuint64_t)Nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)Px * sizeof(cplx<float>), (cuuint64_t)Nyr * Px * sizeof(cplx<float>)};
+  const cuuint32_t box[3] = {64, 1, (cuuint32_t)Nz};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int N1>
+cudaError_t fft_z_tma_launch(const Params& P, const ZField* f, int nfields, int grid_y, bool inverse,
+                             const cplx<float>* tw, cudaStream_t s) {
+  CUtensorMap m[3];
+  for (int i = 0; i < 3; ++i) {
+    const ZField& g = f[i < nfields ? i : 0];
+    if (!encode_z_map(&m[i], g.base, P.Px, g.Nyr, P.Nz)) return cudaErrorNotSupported;
+  }
+  const size_t sm = 128 + (size_t)P.Nz * 32 * sizeof(cplx<float>);
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !(done.load() & (1ull << dev))) {
+    cudaError_t e = cudaFuncSetAttribute(k_fft_z_tma<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    done.fetch_or(1ull << dev);
+  }
+  dim3 grid((P.Nxh + 31) / 32, grid_y, nfields);
+  k_fft_z_tma<N1><<<grid, 256, sm, s>>>(m[0], m[1], m[2], f[0], f[nfields > 1 ? 1 : 0], f[nfields > 2 ? 2 : 0], P.Px,
+                                         P.Nxh, inverse ? 1 : 0, tw, P.fault);
+  return cudaGetLastError();
+}
+
+// The tiled z transform applies to single-precision spectra with
+// 16 <= Nz <= 256 whose rows start on 16-byte boundaries.
+bool z_tma_ok(const Params& P, const void* data) {
+  return P.fz_tma && P.Nz >= 16 && P.Nz <= 256 && ((uintptr_t)data & 15u) == 0 && tensor_map_encoder() != nullptr;
+}
+
+cudaError_t fft_z_tma(const Params& P, const ZField* f, int nfields, int grid_y, bool inverse, const cplx<float>* tw,
+                      cudaStream_t s) {
+  switch (P.Nz) {
+    case 16: return fft_z_tma_launch<1>(P, f, nfields, grid_y, inverse, tw, s);
+    case 32: return fft_z_tma_launch<2>(P, f, nfields, grid_y, inverse, tw, s);
+    case 64: return fft_z_tma_launch<4>(P, f, nfields, grid_y, inverse, tw, s);
+    case 128: return fft_z_tma_launch<8>(P, f, nfields, grid_y, inverse, tw, s);
+    default: return fft_z_tma_launch<16>(P, f, nfields, grid_y, inverse, tw, s);
+  }
+}
+
 template <typename T>
 cudaError_t fft_z_launch(const Params& P, cplx<T>* data, int Nyr, int grid_y, int nfields, size_t field_stride,
                          bool inverse, const cplx<T>* tw, int mac, cudaStream_t s) {
@@ -789,6 +947,32 @@ cudaError_t fft_z_launch(const Params& P, cplx<T>* data, int Nyr, int grid_y, in
   dim3 grid((P.Nxh + cpw * wpb - 1) / (cpw * wpb), grid_y, nfields);
   const int inv = inverse ? 1 : 0;
   probe_begin(PROBE_FFT_Z, s);
+  if constexpr (std::is_same<T, float>::value) {
+    if (z_tma_ok(P, data)) {
+      ZField f[3];
+      int nf = nfields;
+      if (mac) {
+        const int Ny = Nyr;
+        f[0] = ZField{data, Ny};
+        f[1] = ZField{data + (size_t)P.Nz * Ny * P.Px, Ny + 1};
+        f[2] = ZField{data + (size_t)P.Nz * (2 * Ny + 1) * P.Px, Ny};
+        nf = 3;
+      } else {
+        for (int i = 0; i < nfields && i < 3; ++i) f[i] = ZField{data + (size_t)i * field_stride, Nyr};
+      }
+      cudaError_t e = nf <= 3 ? fft_z_tma(P, f, nf, grid_y, inverse, tw, s) : cudaErrorNotSupported;
+      if (e == cudaSuccess) {
+        count_launches(1);
+        probe_end(PROBE_FFT_Z, s);
+        return cudaSuccess;
+      }
+      if (e != cudaErrorNotSupported) {
+        probe_end(PROBE_FFT_Z, s);
+        return e;
+      }
+      (void)cudaGetLastError();
+    }
+  }
   if (G == 8) fft_z_dispatch<T, 8>(P, grid, 32 * wpb, data, Nyr, inv, tw, field_stride, mac, s);
   else fft_z_dispatch<T, 16>(P, grid, 32 * wpb, data, Nyr, inv, tw, field_stride, mac, s);
   count_launches(1);
@@ -912,14 +1096,24 @@ cudaError_t tune_transforms_t(Params& P, Workspace& W, cudaStream_t s, float* be
   // L2-resident trial spectrum and lose on the step's larger ones.  With a
   // fluid the trial is the three-field Stokes spectrum, the largest one.
   Q = P;
+  Q.fz_tma = 0;
   const int tk0 = (int)(32 / sizeof(cplx<T>));
   const bool mac = W.st_l1 != nullptr;   // the Stokes factors exist only with a fluid
+  bool best_tma = false;
+  if (std::is_same<T, float>::value && P.Nz >= 16 && P.Nz <= 256 && e == cudaSuccess) {
+    Q.fz_tma = 1;
+    const float ms = time_it([&] {
+      return mac ? fft_z_mac<T>(Q, S, false, twz, s) : fft_z<T>(Q, S, P.Ny, 1, 0, false, twz, s);
+    });
+    if (ms < bz) { bz = ms; best_tma = true; }
+    Q.fz_tma = 0;
+  }
   for (int tk = tk0; tk <= max_tile_z(P.Nz, sizeof(cplx<T>)) && e == cudaSuccess; tk *= 2) {
     Q.fz_tk = tk;
     const float ms = time_it([&] {
       return mac ? fft_z_mac<T>(Q, S, false, twz, s) : fft_z<T>(Q, S, P.Ny, 1, 0, false, twz, s);
     });
-    if (ms < bz) { bz = ms; best_tk = tk; }
+    if (ms < bz) { bz = ms; best_tk = tk; best_tma = false; }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -928,6 +1122,7 @@ cudaError_t tune_transforms_t(Params& P, Workspace& W, cudaStream_t s, float* be
   P.fx_threads = best_th;
   P.fx_staged = best_staged ? 1 : 0;
   P.fz_tk = best_tk;
+  P.fz_tma = best_tma ? 1 : 0;
   best_ms[0] = bx;
   best_ms[1] = bz;
   return cudaSuccess;

@@ -275,8 +275,11 @@ __global__ void k_interp_velocity_w(const T* __restrict__ x, int N, Params P, co
   T p[3] = {T(0.5), T(0.5), T(0.5)};
   if (valid) { p[0] = x[ion]; p[1] = x[N + ion]; p[2] = x[2 * N + ion]; }
   const size_t G = (size_t)Nx * Ny * Nz;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
+  // one velocity component per blockIdx.y: the blocks of a component run
+  // together, so the gathers of that time hit one component's grid, which
+  // stays in L2 (the three together do not at 256 x 128 x 256)
+  {
+    const int c = blockIdx.y;
     const T* g = v + (c >= 1 ? G : 0) + (c == 2 ? (size_t)Nx * (Ny + 1) * Nz : 0);
     const int Nyg = c == 1 ? Ny + 1 : Ny;
     int st[3];
@@ -462,8 +465,10 @@ cudaError_t launch_interp_velocity(const Params& P, const T* x, int N, const T* 
   probe_begin(PROBE_INTERP_V, s);
   auto one = [&](const Params& Q) {
     if (Q.khy.w == 4)
-      k_interp_velocity_w<T, 4, 4><<<(int)(((size_t)N * 4 + bs - 1) / bs), bs, 0, s>>>(x, N, Q, v, out, out_index, species);
-    else if (Q.khy.w == 6) k_interp_velocity_w<T, 6, 8><<<nb, bs, 0, s>>>(x, N, Q, v, out, out_index, species);
+      k_interp_velocity_w<T, 4, 4><<<dim3((unsigned)(((size_t)N * 4 + bs - 1) / bs), 3), bs, 0, s>>>(x, N, Q, v, out,
+                                                                                             out_index, species);
+    else if (Q.khy.w == 6)
+      k_interp_velocity_w<T, 6, 8><<<dim3((unsigned)nb, 3), bs, 0, s>>>(x, N, Q, v, out, out_index, species);
     else k_interp_velocity<T><<<nb, bs, 0, s>>>(x, N, Q, v, out, out_index, species);
     count_launches(1);
   };

@@ -194,11 +194,12 @@ __global__ void k_spread_charge_w(const T* __restrict__ x, const T* __restrict__
 }
 
 // LPI = lanes per ion: 4 for 4-point stencils (no idle lanes), else 8.
-// The three MAC components are spread by the same lanes one after another,
-// so the ion's data and its thermal draw are read and generated once, and
-// each lane evaluates its kernel weights (and derivatives) once per axis for
-// the two grid offsets a component can have (0 on its own face axis, 1/2 on
-// the others).
+// One MAC component per blockIdx.y: the blocks of one component run before
+// those of the next, so the grid that the atomics hit at any time is one
+// component (a third of the forcing), which stays in L2.  (Spreading all
+// three components from each thread shares the ion's loads and thermal draw
+// but keeps the whole forcing hot at once; on the 256 x 128 x 256 channel
+// that tripled the DRAM write-back and was slower.)
 template <typename T, int W, int LPI>
 __global__ void k_spread_force_w(const T* __restrict__ x, const T* __restrict__ F, int N, Params P,
                                  T* __restrict__ f, long long step, int rfd, const int* __restrict__ noise_index,
@@ -206,16 +207,17 @@ __global__ void k_spread_force_w(const T* __restrict__ x, const T* __restrict__ 
   constexpr int LOG = LPI == 4 ? 2 : 3;
   const int Nx = P.Nx, Ny = P.Ny, Nz = P.Nz;
   const KernelParams kp = P.khy;
+  const int c = blockIdx.y;
   int ion = spread_ion((blockIdx.x * blockDim.x + threadIdx.x) >> LOG, N, stride);
   int l = threadIdx.x & (LPI - 1);
   int gbase = (threadIdx.x & 31) & ~(LPI - 1);
   bool valid = ion < N && (P.hy_filter < 0 || sp[ion] == P.hy_filter);
   T p[3] = {T(0.5), T(0.5), T(0.5)};
-  T Fv[3] = {T(0), T(0), T(0)};
+  T Fc = T(0);
   T Wr[3] = {T(0), T(0), T(0)};
   if (valid) {
     p[0] = x[ion]; p[1] = x[N + ion]; p[2] = x[2 * N + ion];
-    Fv[0] = F[ion]; Fv[1] = F[N + ion]; Fv[2] = F[2 * (size_t)N + ion];
+    Fc = F[(size_t)c * N + ion];
     if (rfd) {
       T g[4];
       const int key = noise_index ? noise_index[ion] : ion;
@@ -223,69 +225,60 @@ __global__ void k_spread_force_w(const T* __restrict__ x, const T* __restrict__ 
       Wr[0] = g[0]; Wr[1] = g[1]; Wr[2] = g[2];
     }
   }
-  // this lane's weight and derivative at offset l, per axis, for grid
-  // points at offset 0 (h = 0) and 1/2 (h = 1)
-  int st[2][3];
-  T wv[2][3], wd[2][3];
+  int st[3];
+  T wv[3], wd[3];
 #pragma unroll
-  for (int h = 0; h < 2; ++h)
+  for (int d = 0; d < 3; ++d) {
+    const T sd = p[d] - (d == c ? T(0) : T(0.5));
+    st[d] = stencil_start(sd, W);
+    const T z = sd - T(st[d] + l);
+    wv[d] = l < W ? kval(z, kp) : T(0);
+    wd[d] = (l < W && rfd) ? kder(z, kp) : T(0);
+  }
+  const T a = T(phys(P, T()).kT) * (c == 0 ? Wr[0] : (c == 1 ? Wr[1] : Wr[2]));
+  const int Nyg = (c == 1) ? Ny + 1 : Ny;
+  size_t off = 0;
+  if (c >= 1) off += (size_t)Nz * Ny * Nx;
+  if (c == 2) off += (size_t)Nz * (Ny + 1) * Nx;
+  T* g = f + off;
+  T wy[W], dy[W], wz[W], dz[W];
+  int roff[W];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const T sd = p[d] - (h == 0 ? T(0) : T(0.5));
-      st[h][d] = stencil_start(sd, W);
-      const T z = sd - T(st[h][d] + l);
-      wv[h][d] = l < W ? kval(z, kp) : T(0);
-      wd[h][d] = (l < W && rfd) ? kder(z, kp) : T(0);
+  for (int j = 0; j < W; ++j) {
+    wy[j] = __shfl_sync(0xffffffffu, wv[1], gbase + j);
+    dy[j] = __shfl_sync(0xffffffffu, wd[1], gbase + j);
+    wz[j] = __shfl_sync(0xffffffffu, wv[2], gbase + j);
+    dz[j] = __shfl_sync(0xffffffffu, wd[2], gbase + j);
+    int iy = st[1] + j;
+    T sg = T(1);
+    bool ok;
+    if (c == 1) {             // y-faces 0..Ny; wall faces receive real + image = 0
+      if (iy < 0) { iy = -iy; sg = T(-1); }
+      else if (iy > Ny) { iy = 2 * Ny - iy; sg = T(-1); }
+      ok = iy > 0 && iy < Ny;
+    } else {                  // cell-centred in y: tangential, like image at a slip wall
+      if (iy < 0) { iy = -1 - iy; sg = P.slip[0] ? T(1) : T(-1); }
+      else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = P.slip[1] ? T(1) : T(-1); }
+      ok = iy >= 0 && iy < Ny;
     }
-  const T kT = T(phys(P, T()).kT);
+    roff[j] = ok ? iy * Nx : 0;
+    const T keep = ok ? sg : T(0);
+    wy[j] *= keep;
+    dy[j] *= keep;
+  }
+  if (valid && l < W) {
+    const int ix = (st[0] + l) & (Nx - 1);
+    const T fx0 = Fc * wv[0];
+    const T r0 = a * Wr[0] * wd[0], r1 = a * Wr[1] * wv[0], r2 = a * Wr[2] * wv[0];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const int hx = c == 0 ? 0 : 1, hy = c == 1 ? 0 : 1, hz = c == 2 ? 0 : 1;
-    const T a = kT * Wr[c];
-    const int Nyg = (c == 1) ? Ny + 1 : Ny;
-    size_t off = 0;
-    if (c >= 1) off += (size_t)Nz * Ny * Nx;
-    if (c == 2) off += (size_t)Nz * (Ny + 1) * Nx;
-    T* g = f + off;
-    T wy[W], dy[W], wz[W], dz[W];
-    int roff[W];
+    for (int jz = 0; jz < W; ++jz) {
+      const size_t zoff = (size_t)((st[2] + jz) & (Nz - 1)) * Nyg * Nx + ix;
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
-      wy[j] = __shfl_sync(0xffffffffu, wv[hy][1], gbase + j);
-      dy[j] = __shfl_sync(0xffffffffu, wd[hy][1], gbase + j);
-      wz[j] = __shfl_sync(0xffffffffu, wv[hz][2], gbase + j);
-      dz[j] = __shfl_sync(0xffffffffu, wd[hz][2], gbase + j);
-      int iy = st[hy][1] + j;
-      T sg = T(1);
-      bool ok;
-      if (c == 1) {             // y-faces 0..Ny; wall faces receive real + image = 0
-        if (iy < 0) { iy = -iy; sg = T(-1); }
-        else if (iy > Ny) { iy = 2 * Ny - iy; sg = T(-1); }
-        ok = iy > 0 && iy < Ny;
-      } else {                  // cell-centred in y: tangential, like image at a slip wall
-        if (iy < 0) { iy = -1 - iy; sg = P.slip[0] ? T(1) : T(-1); }
-        else if (iy >= Ny) { iy = 2 * Ny - 1 - iy; sg = P.slip[1] ? T(1) : T(-1); }
-        ok = iy >= 0 && iy < Ny;
-      }
-      roff[j] = ok ? iy * Nx : 0;
-      const T keep = ok ? sg : T(0);
-      wy[j] *= keep;
-      dy[j] *= keep;
-    }
-    if (valid && l < W) {
-      const int ix = (st[hx][0] + l) & (Nx - 1);
-      const T fx0 = Fv[c] * wv[hx][0];
-      const T r0 = a * Wr[0] * wd[hx][0], r1 = a * Wr[1] * wv[hx][0], r2 = a * Wr[2] * wv[hx][0];
-#pragma unroll
-      for (int jz = 0; jz < W; ++jz) {
-        const size_t zoff = (size_t)((st[hz][2] + jz) & (Nz - 1)) * Nyg * Nx + ix;
-#pragma unroll
-        for (int jy = 0; jy < W; ++jy) {
-          if (wy[jy] == T(0) && dy[jy] == T(0)) continue;
-          T val = fx0 * wy[jy] * wz[jz];
-          if (rfd) val += r0 * wy[jy] * wz[jz] + r1 * dy[jy] * wz[jz] + r2 * wy[jy] * dz[jz];
-          atomicAdd(&g[zoff + roff[jy]], val);
-        }
+      for (int jy = 0; jy < W; ++jy) {
+        if (wy[jy] == T(0) && dy[jy] == T(0)) continue;
+        T val = fx0 * wy[jy] * wz[jz];
+        if (rfd) val += r0 * wy[jy] * wz[jz] + r1 * dy[jy] * wz[jz] + r2 * wy[jy] * dz[jz];
+        atomicAdd(&g[zoff + roff[jy]], val);
       }
     }
   }
@@ -446,8 +439,8 @@ cudaError_t launch_spread_force(const Params& P, const T* x, const T* F, int N, 
   int bs = 256;
   dim3 grid((unsigned)(((size_t)N * 8 + bs - 1) / bs), 3);
   const unsigned long long st = decorrelate ? spread_stride(N) : 0ull;
-  const dim3 grid4((unsigned)(((size_t)N * 4 + bs - 1) / bs), 1);
-  const dim3 grid8((unsigned)(((size_t)N * 8 + bs - 1) / bs), 1);
+  const dim3 grid4((unsigned)(((size_t)N * 4 + bs - 1) / bs), 3);
+  const dim3 grid8((unsigned)(((size_t)N * 8 + bs - 1) / bs), 3);
   auto one = [&](const Params& Q) {
     if (Q.khy.w == 4) k_spread_force_w<T, 4, 4><<<grid4, bs, 0, s>>>(x, F, N, Q, f, (long long)step, rfd ? 1 : 0, noise_index, st, species);
     else if (Q.khy.w == 6) k_spread_force_w<T, 6, 8><<<grid8, bs, 0, s>>>(x, F, N, Q, f, (long long)step, rfd ? 1 : 0, noise_index, st, species);
