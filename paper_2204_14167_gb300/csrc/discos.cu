@@ -387,8 +387,11 @@ discos_status forces_impl(discos_handle* h, const T* x, const T* q, const int* s
   if (e == cudaSuccess) e = cudaEventRecord(h->ev_fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
   if (e == cudaSuccess) e = launch_near_field_sorted<T>(P, W, N, Fn, nbr, nullptr, W.perm, h->side, false);
-  if (e == cudaSuccess) e = side_extra(h->side);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->side);
+  // the extra side work (the step's stochastic stress) runs on past the
+  // field interpolation; the caller waits for ev_extra before using it
+  if (e == cudaSuccess) e = side_extra(h->side);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_extra, h->side);
   const T* xs = reinterpret_cast<const T*>(W.xs);
   const T* qs = reinterpret_cast<const T*>(W.qs);
   if (e == cudaSuccess) e = launch_spread_charge<T>(P, xs, qs, N, phi, s, true);
@@ -430,9 +433,15 @@ discos_status step_impl(discos_handle* h, T* x, const T* q, const int* species, 
     }
     // the stochastic stress (or a zero fill) initialises the fluid forcing on
     // the side stream, overlapping the electrostatics
+    // the fluid forcing starts from zero; the stochastic stress is added on
+    // the side stream while the main stream spreads the forces into the same
+    // grid (both with atomics)
+    if (wet) {
+      cudaError_t ez = launch_fill_zero<T>(fg, nf, s);
+      if (ez != cudaSuccess) return cuda_status(ez, "discos_step");
+    }
     auto side = [&](cudaStream_t ss) -> cudaError_t {
-      if (!wet) return cudaSuccess;
-      return thermal ? launch_stress_noise<T>(P, fg, step, ss, true) : launch_fill_zero<T>(fg, nf, ss);
+      return (wet && thermal) ? launch_stress_noise<T>(P, fg, step, ss) : cudaSuccess;
     };
     // F comes back in cell order: everything below works on the sorted ions
     // and the update writes each new position back to the caller's index
@@ -441,6 +450,7 @@ discos_status step_impl(discos_handle* h, T* x, const T* q, const int* species, 
     cudaError_t e = cudaSuccess;
     if (wet) {
       e = launch_spread_force<T>(P, xsrt, F, N, fg, step, drift && thermal, s, true, W.perm, true, W.sps);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_extra, 0);
       if (e == cudaSuccess) e = launch_stokes<T>(P, W, fg, fg, nullptr, s);
       if (e == cudaSuccess) e = launch_interp_velocity<T>(P, xsrt, N, fg, V, s, nullptr, W.sps);
       if (drift) {
@@ -870,6 +880,7 @@ discos_status discos_create(const discos_config* cfg, discos_alloc_fn alloc_fn, 
       cudaEventCreateWithFlags(&W.yev1, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_extra, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fault, cudaEventDisableTiming) != cudaSuccess ||
       cudaHostAlloc((void**)&h->fault_host, sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess) {
     free_workspace(h);
@@ -910,6 +921,7 @@ discos_status discos_destroy(discos_handle* h) {
     for (int i = 0; i < 2 * Probe::kMax; ++i) cudaEventDestroy(h->probe.ev[i]);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_extra) cudaEventDestroy(h->ev_extra);
   if (h->ev_fault) cudaEventDestroy(h->ev_fault);
   if (h->fault_host) cudaFreeHost(h->fault_host);
   delete h;

@@ -234,6 +234,7 @@ struct discos_handle {
   discos::Probe probe;
   cudaStream_t side = nullptr;       // independent work of a step runs here
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_extra = nullptr;        // the side stream's extra work (the stochastic stress) is done
   discos::BatchState* batch = nullptr;   // batched replicas (batch_api.cu)
   unsigned* fault_host = nullptr;        // pinned copy of the fault word, written after each discos_step
   cudaEvent_t ev_fault = nullptr;
@@ -265,8 +266,8 @@ double es_normalisation(int w, double beta);
 template <typename T> cudaError_t launch_cell_list(const Params& P, Workspace& W, const T* x, int N, cudaStream_t s);
 template <typename T> cudaError_t launch_spread_charge(const Params& P, const T* x, const T* q, int N, T* rho, cudaStream_t s,
                                                        bool decorrelate = false);
-template <typename T> cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_t s,
-                                                      bool overwrite = false);
+// Adds the stochastic stress divergence into f with atomics (f prepared by the caller).
+template <typename T> cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_t s);
 template <typename T> cudaError_t launch_poisson(const Params& P, Workspace& W, const T* rho, T* phi, cudaStream_t s);
 template <typename T> cudaError_t launch_poisson_strip(const Params& P, Workspace& W, const T* rho, T* phi, T fourpi_lB,
                                                        T add1, cudaStream_t s);

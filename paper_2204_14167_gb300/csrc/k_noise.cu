@@ -10,7 +10,9 @@
 // Each block generates Z for a 32 x 8 x 8 tile of cells plus a one-cell halo
 // in shared memory (two Philox draws per halo cell; of the second only the
 // two normals that are used) and then forms the three face divergences of
-// its cells, adding them to the force grids.
+// its cells, adding them to the force grids with atomics: the step runs this
+// kernel on its side stream while the force spreading adds into the same
+// (zeroed) grids on the main stream.
 #include <atomic>
 #include "internal.h"
 
@@ -23,7 +25,7 @@ constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
 constexpr int HN = HX * HY * HZ;
 
 template <typename T>
-__global__ void k_stress_noise(T* __restrict__ f, Params P, long long step, T amp, int overwrite) {
+__global__ void k_stress_noise(T* __restrict__ f, Params P, long long step, T amp) {
   extern __shared__ unsigned char smem_raw[];
   T (*Zd)[HN] = reinterpret_cast<T (*)[HN]>(smem_raw);            // xx, yy, zz
   T (*Ze)[HN] = reinterpret_cast<T (*)[HN]>(smem_raw) + 3;        // xy, xz, yz
@@ -67,15 +69,12 @@ __global__ void k_stress_noise(T* __restrict__ f, Params P, long long step, T am
     T dx = (Zd[0][h] - Zd[0][h - sx]) + (Ze[0][h + sy] - Ze[0][h]) + (Ze[1][h + sz] - Ze[1][h]);
     // z-face (i+1/2, j+1/2, k)
     T dz = (Ze[1][h + sx] - Ze[1][h]) + (Ze[2][h + sy] - Ze[2][h]) + (Zd[2][h] - Zd[2][h - sz]);
-    T* px = &fx[((size_t)k * Ny + j) * Nx + i];
-    T* pz = &fz[((size_t)k * Ny + j) * Nx + i];
-    *px = overwrite ? amp * dx : *px + amp * dx;
-    *pz = overwrite ? amp * dz : *pz + amp * dz;
+    atomicAdd(&fx[((size_t)k * Ny + j) * Nx + i], amp * dx);
+    atomicAdd(&fz[((size_t)k * Ny + j) * Nx + i], amp * dz);
     if (j >= 1) {
       // y-face (i+1/2, j, k+1/2)
       T dy = (Ze[0][h + sx] - Ze[0][h]) + (Zd[1][h] - Zd[1][h - sy]) + (Ze[2][h + sz] - Ze[2][h]);
-      T* py = &fy[((size_t)k * (Ny + 1) + j) * Nx + i];
-      *py = overwrite ? amp * dy : *py + amp * dy;
+      atomicAdd(&fy[((size_t)k * (Ny + 1) + j) * Nx + i], amp * dy);
     }
   }
 }
@@ -83,7 +82,7 @@ __global__ void k_stress_noise(T* __restrict__ f, Params P, long long step, T am
 }  // namespace
 
 template <typename T>
-cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_t s, bool overwrite) {
+cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_t s) {
   dim3 grid((P.Nx + TX - 1) / TX, (P.Ny + TY - 1) / TY, (P.Nz + TZ - 1) / TZ);
   T amp = T(sqrt(2.0 * P.kT * P.eta / P.dt));
   const size_t sm = 6 * (size_t)HN * sizeof(T);
@@ -96,13 +95,13 @@ cudaError_t launch_stress_noise(const Params& P, T* f, int64_t step, cudaStream_
     done.fetch_or(1ull << dev);
   }
   probe_begin(PROBE_NOISE, s);
-  k_stress_noise<T><<<grid, 256, sm, s>>>(f, P, (long long)step, amp, overwrite ? 1 : 0);
+  k_stress_noise<T><<<grid, 256, sm, s>>>(f, P, (long long)step, amp);
   count_launches(1);
   probe_end(PROBE_NOISE, s);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_stress_noise<float>(const Params&, float*, int64_t, cudaStream_t, bool);
-template cudaError_t launch_stress_noise<double>(const Params&, double*, int64_t, cudaStream_t, bool);
+template cudaError_t launch_stress_noise<float>(const Params&, float*, int64_t, cudaStream_t);
+template cudaError_t launch_stress_noise<double>(const Params&, double*, int64_t, cudaStream_t);
 
 }  // namespace discos

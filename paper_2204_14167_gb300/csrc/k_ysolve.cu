@@ -593,7 +593,7 @@ __device__ __forceinline__ void stcf(cplx<float>* p, C<float> v, float s) { *p =
 // rows) are issued together before its sequential recurrence, so one memory
 // latency covers SB rows (the stores of a block may alias later loads only
 // through the in-place spectra, which is why the prefetch is explicit).
-constexpr int SB = 8;
+constexpr int SB = 16;
 
 __global__ void k_poisson_sweep(cplx<float>* __restrict__ S, const float* __restrict__ piv,
                                 const unsigned char* __restrict__ skip, int Ny, int Nz, int Nxh, int Px,
@@ -936,7 +936,8 @@ cudaError_t launch_stokes_y_impl(const Params& P, Workspace& W, cplx<T>* S, cplx
     if (e == cudaSuccess) e = cudaEventRecord(W.yev1, W.ystream);
     if (e == cudaSuccess) {
       const int nt = P.Nz * ((P.Nxh + 31) & ~31);
-      k_stokes_sweep<<<(nt + 127) / 128, 128, 0, s>>>(S, Sp, P, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf,
+      // 64-thread blocks: the sweep holds SB rows of three fields in registers
+      k_stokes_sweep<<<(nt + 63) / 64, 64, 0, s>>>(S, Sp, P, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf,
                                                      W.is_lo);
       count_launches(1);
       e = cudaGetLastError();
