@@ -593,7 +593,9 @@ __device__ __forceinline__ void stcf(cplx<float>* p, C<float> v, float s) { *p =
 // rows) are issued together before its sequential recurrence, so one memory
 // latency covers SB rows (the stores of a block may alias later loads only
 // through the in-place spectra, which is why the prefetch is explicit).
-constexpr int SB = 16;
+// 16 rows for the Poisson sweep; 8 for the Stokes sweep, which holds three
+// fields per row (16 there needs all 255 registers and runs slower).
+constexpr int SB_POISSON = 16, SB_STOKES = 8;
 
 __global__ void k_poisson_sweep(cplx<float>* __restrict__ S, const float* __restrict__ piv,
                                 const unsigned char* __restrict__ skip, int Ny, int Nz, int Nxh, int Px,
@@ -608,17 +610,17 @@ __global__ void k_poisson_sweep(cplx<float>* __restrict__ S, const float* __rest
   cplx<float>* col = S + (size_t)kz * Ny * Px + kx;
   // forward y_j = piv_j (b_j + y_{j-1}), in place
   C<float> y = cz<float>();
-  for (int jb = 0; jb < Ny; jb += SB) {
-    C<float> b[SB];
-    float m[SB];
+  for (int jb = 0; jb < Ny; jb += SB_POISSON) {
+    C<float> b[SB_POISSON];
+    float m[SB_POISSON];
 #pragma unroll
-    for (int r = 0; r < SB; ++r) {
+    for (int r = 0; r < SB_POISSON; ++r) {
       const int j = jb + r;
       b[r] = j < Ny ? ldcf(col + (size_t)j * Px) : cz<float>();
       m[r] = j < Ny ? piv[(size_t)j * M + mode] : 0.f;
     }
 #pragma unroll
-    for (int r = 0; r < SB; ++r) {
+    for (int r = 0; r < SB_POISSON; ++r) {
       const int j = jb + r;
       if (j < Ny) {
         y = cscale(m[r], cadd2(b[r], y));
@@ -628,17 +630,17 @@ __global__ void k_poisson_sweep(cplx<float>* __restrict__ S, const float* __rest
   }
   // backward x_j = y_j + piv_j x_{j+1}, x_{Ny-1} = y_{Ny-1}
   C<float> xn = cz<float>();
-  for (int jt = Ny - 1; jt >= 0; jt -= SB) {
-    C<float> b[SB];
-    float a[SB];
+  for (int jt = Ny - 1; jt >= 0; jt -= SB_POISSON) {
+    C<float> b[SB_POISSON];
+    float a[SB_POISSON];
 #pragma unroll
-    for (int r = 0; r < SB; ++r) {
+    for (int r = 0; r < SB_POISSON; ++r) {
       const int j = jt - r;
       b[r] = j >= 0 ? ldcf(col + (size_t)j * Px) : cz<float>();
       a[r] = (j >= 0 && j < Ny - 1) ? piv[(size_t)j * M + mode] : 0.f;
     }
 #pragma unroll
-    for (int r = 0; r < SB; ++r) {
+    for (int r = 0; r < SB_POISSON; ++r) {
       const int j = jt - r;
       if (j >= 0) {
         xn = cfma(a[r], xn, b[r]);
@@ -677,11 +679,11 @@ __global__ void k_stokes_sweep(cplx<float>* __restrict__ S, cplx<float>* __restr
   {
     C<float> gprev = gsum(ldcf(Su), ldcf(Sw));
     C<float> y1 = cz<float>(), y2 = cz<float>();
-    for (int fb = 1; fb < Ny; fb += SB) {
-      C<float> g[SB], fy[SB];
-      float l1[SB], l2[SB];
+    for (int fb = 1; fb < Ny; fb += SB_STOKES) {
+      C<float> g[SB_STOKES], fy[SB_STOKES];
+      float l1[SB_STOKES], l2[SB_STOKES];
 #pragma unroll
-      for (int r = 0; r < SB; ++r) {
+      for (int r = 0; r < SB_STOKES; ++r) {
         const int f = fb + r;
         const bool in = f < Ny;
         g[r] = in ? gsum(ldcf(Su + (size_t)f * Px), ldcf(Sw + (size_t)f * Px)) : cz<float>();
@@ -690,7 +692,7 @@ __global__ void k_stokes_sweep(cplx<float>* __restrict__ S, cplx<float>* __restr
         l2[r] = in ? L2[(size_t)f * M + mode] : 0.f;
       }
 #pragma unroll
-      for (int r = 0; r < SB; ++r) {
+      for (int r = 0; r < SB_STOKES; ++r) {
         const int f = fb + r;
         if (f < Ny) {
           const C<float> rhs =
@@ -705,11 +707,11 @@ __global__ void k_stokes_sweep(cplx<float>* __restrict__ S, cplx<float>* __restr
   // B: v_f = di_f y_f - l1_{f+1} v_{f+1} - l2_{f+2} v_{f+2}, f = Ny-1..1 (over y, unscaled)
   {
     C<float> v1 = cz<float>(), v2 = cz<float>();
-    for (int ft = Ny - 1; ft >= 1; ft -= SB) {
-      C<float> yv[SB];
-      float d[SB], a1[SB], a2[SB];
+    for (int ft = Ny - 1; ft >= 1; ft -= SB_STOKES) {
+      C<float> yv[SB_STOKES];
+      float d[SB_STOKES], a1[SB_STOKES], a2[SB_STOKES];
 #pragma unroll
-      for (int r = 0; r < SB; ++r) {
+      for (int r = 0; r < SB_STOKES; ++r) {
         const int f = ft - r;
         const bool in = f >= 1;
         yv[r] = in ? ldcf(Sv + (size_t)f * Px) : cz<float>();
@@ -718,7 +720,7 @@ __global__ void k_stokes_sweep(cplx<float>* __restrict__ S, cplx<float>* __restr
         a2[r] = (in && f + 2 < Ny) ? L2[(size_t)(f + 2) * M + mode] : 0.f;
       }
 #pragma unroll
-      for (int r = 0; r < SB; ++r) {
+      for (int r = 0; r < SB_STOKES; ++r) {
         const int f = ft - r;
         if (f >= 1) {
           const C<float> v = csub2(csub2(cscale(d[r], yv[r]), cscale(a1[r], v1)), cscale(a2[r], v2));
@@ -731,17 +733,17 @@ __global__ void k_stokes_sweep(cplx<float>* __restrict__ S, cplx<float>* __restr
   // C: the pressure row by row from a window (v_{j-1}, v_j, v_{j+1}, v_{j+2})
   // (wall faces 0 and Ny carry v = 0), then the forward sweeps of the u and
   // w tridiagonals, in place; face j of v is final (scaled) once row j is
-  // done.  A block loads the v faces it will need (jb + 2 .. jb + SB + 1)
-  // before it overwrites faces jb .. jb + SB - 1.
+  // done.  A block loads the v faces it will need (jb + 2 .. jb + SB_STOKES + 1)
+  // before it overwrites faces jb .. jb + SB_STOKES - 1.
   {
     C<float> vm1 = cz<float>(), v0 = cz<float>();
     C<float> vp1 = Ny >= 2 ? ldcf(Sv + (size_t)Px) : cz<float>();
     C<float> yu = cz<float>(), yw = cz<float>();
-    for (int jb = 0; jb < Ny; jb += SB) {
-      C<float> fx[SB], fz[SB], vn[SB];
-      float c[SB];
+    for (int jb = 0; jb < Ny; jb += SB_STOKES) {
+      C<float> fx[SB_STOKES], fz[SB_STOKES], vn[SB_STOKES];
+      float c[SB_STOKES];
 #pragma unroll
-      for (int r = 0; r < SB; ++r) {
+      for (int r = 0; r < SB_STOKES; ++r) {
         const int j = jb + r;
         const bool in = j < Ny;
         fx[r] = in ? ldcf(Su + (size_t)j * Px) : cz<float>();
@@ -750,7 +752,7 @@ __global__ void k_stokes_sweep(cplx<float>* __restrict__ S, cplx<float>* __restr
         vn[r] = (j + 2 <= Ny - 1) ? ldcf(Sv + (size_t)(j + 2) * Px) : cz<float>();   // v_{j+2}
       }
 #pragma unroll
-      for (int r = 0; r < SB; ++r) {
+      for (int r = 0; r < SB_STOKES; ++r) {
         const int j = jb + r;
         if (j < Ny) {
           const C<float> vp2 = vn[r];
@@ -779,18 +781,18 @@ __global__ void k_stokes_sweep(cplx<float>* __restrict__ S, cplx<float>* __restr
   // D: backward x_j = y_j + ci_j x_{j+1}, x_{Ny-1} = y_{Ny-1}
   {
     C<float> xu = cz<float>(), xw = cz<float>();
-    for (int jt = Ny - 1; jt >= 0; jt -= SB) {
-      C<float> bu[SB], bw[SB];
-      float a[SB];
+    for (int jt = Ny - 1; jt >= 0; jt -= SB_STOKES) {
+      C<float> bu[SB_STOKES], bw[SB_STOKES];
+      float a[SB_STOKES];
 #pragma unroll
-      for (int r = 0; r < SB; ++r) {
+      for (int r = 0; r < SB_STOKES; ++r) {
         const int j = jt - r;
         bu[r] = j >= 0 ? ldcf(Su + (size_t)j * Px) : cz<float>();
         bw[r] = j >= 0 ? ldcf(Sw + (size_t)j * Px) : cz<float>();
         a[r] = (j >= 0 && j < Ny - 1) ? CI[(size_t)j * M + mode] : 0.f;
       }
 #pragma unroll
-      for (int r = 0; r < SB; ++r) {
+      for (int r = 0; r < SB_STOKES; ++r) {
         const int j = jt - r;
         if (j >= 0) {
           xu = cfma(a[r], xu, bu[r]);
@@ -809,7 +811,7 @@ cudaError_t poisson_scan_launch(const Params& P, cplx<TS>* S, const TC* piv, con
   const int Ny = P.Ny;
   const int singular = (P.bc[0] == DISCOS_BC_NEUMANN && P.bc[1] == DISCOS_BC_NEUMANN) ? 1 : 0;
   const TC norm = (TC)P.inv_nxnz;
-  const int bs = 256;
+  const int bs = list ? 64 : 256;          // a list: 2 warps per block (as in stokes_scan_launch)
   const int nb = (n * 32 + bs - 1) / bs;
   if (n <= 0) return cudaSuccess;
   if (!list) {
@@ -878,7 +880,9 @@ cudaError_t stokes_scan_launch(const Params& P, cplx<TS>* S, cplx<TS>* Sp, const
     return stokes_staged_launch<TS, TC, 8, TM>(P, S, L1, L2, DI, CI, MC, skip, s);
   }
   const size_t per_warp = (size_t)(2 * Ny + 1) * sizeof(C<TC>);
-  int warps = 8;
+  // a list (the double-precision low modes, a few percent of all) runs 2
+  // warps per block, so that its FP64-bound warps spread over all SMs
+  int warps = list ? 2 : 8;
   while (warps > 1 && warps * per_warp > 48 * 1024) --warps;   // stay within the default shared-memory limit
   const size_t sm = (size_t)warps * per_warp;
   const int nb = (n + warps - 1) / warps;
@@ -936,8 +940,7 @@ cudaError_t launch_stokes_y_impl(const Params& P, Workspace& W, cplx<T>* S, cplx
     if (e == cudaSuccess) e = cudaEventRecord(W.yev1, W.ystream);
     if (e == cudaSuccess) {
       const int nt = P.Nz * ((P.Nxh + 31) & ~31);
-      // 64-thread blocks: the sweep holds SB rows of three fields in registers
-      k_stokes_sweep<<<(nt + 63) / 64, 64, 0, s>>>(S, Sp, P, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf,
+      k_stokes_sweep<<<(nt + 127) / 128, 128, 0, s>>>(S, Sp, P, W.st_l1f, W.st_l2f, W.st_dif, W.st_cif, W.st_mcf,
                                                      W.is_lo);
       count_launches(1);
       e = cudaGetLastError();
