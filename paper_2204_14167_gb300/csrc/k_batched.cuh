@@ -197,7 +197,6 @@ __global__ void __launch_bounds__(NT, 1) k_batched_step(Params P, BatchArgs B) {
   const float Lx = 32.0f, Lz = 32.0f, hx = 16.0f, hz = 16.0f;
   const float psi = P.f.psi;
   const float psi2 = mul_rn(psi, psi);
-  const float cut2 = pair_cut2(P, psi2);
   const float lB = P.f.lB, tscale = P.f.tab_scale;
   const bool dir0 = P.bc[0] == DISCOS_BC_DIRICHLET, dir1 = P.bc[1] == DISCOS_BC_DIRICHLET;
   const float s0 = dir0 ? -1.0f : 1.0f, s1 = dir1 ? -1.0f : 1.0f;
@@ -455,8 +454,8 @@ __global__ void __launch_bounds__(NT, 1) k_batched_step(Params P, BatchArgs B) {
             for (int k = cstart[c]; k < cstart[c + 1]; ++k) {
               const int j = slist[k];
               if (j == i) continue;
-              pair_terms(xi, yi, zi, qi, si, sx[j], sy[j], sz[j], sq[j], ssp + j, true, P, stab, Lx, hx, Lz, hz,
-                         psi2, cut2, lB, tscale, fx, fy, fz, cnt);
+              pair_terms(xi, yi, zi, qi, si, sx[j], sy[j], sz[j], sq[j], ssp[j], true, P, stab, Lx, hx, Lz, hz,
+                         psi2, lB, tscale, fx, fy, fz, cnt);
             }
           }
         }
@@ -476,8 +475,8 @@ __global__ void __launch_bounds__(NT, 1) k_batched_step(Params P, BatchArgs B) {
             const int j = slist[k];
             const float yj = sy[j];
             const float yimg = wall == 0 ? -yj : sub_rn((float)(2 * NY), yj);
-            pair_terms(xi, yi, zi, qi, si, sx[j], yimg, sz[j], sgn * sq[j], static_cast<const int*>(nullptr), false, P, stab, Lx, hx, Lz, hz,
-                       psi2, psi2, lB, tscale, fx, fy, fz, cnt);
+            pair_terms(xi, yi, zi, qi, si, sx[j], yimg, sz[j], sgn * sq[j], 0, false, P, stab, Lx, hx, Lz, hz,
+                       psi2, lB, tscale, fx, fy, fz, cnt);
           }
         }
 #pragma unroll

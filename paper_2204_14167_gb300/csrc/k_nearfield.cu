@@ -75,7 +75,6 @@ __global__ void __launch_bounds__(128) k_near_field(const typename Vec4<T>::type
   const T Lx = T(P.Nx), Lz = T(P.Nz), hx = mul_rn(T(0.5), Lx), hz = mul_rn(T(0.5), Lz);
   const T psi = T(P.psi);
   const T psi2 = mul_rn(psi, psi);
-  const T cut2 = pair_cut2(P, psi2);
   const T lB = T(P.lB), scale = T(P.tab_scale);
   const bool near0 = yi < psi && cy == 0, near1 = sub_rn(T(P.Ny), yi) < psi && cy == P.ncy - 1;
   const T sg0 = P.bc[0] == DISCOS_BC_DIRICHLET ? T(-1) : T(1);
@@ -97,19 +96,20 @@ __global__ void __launch_bounds__(128) k_near_field(const typename Vec4<T>::type
         for (int j = a; j < b; ++j) {
           T xj, yj, zj, qj;
           load_vec4(xq[j], xj, yj, zj, qj);
+          const int sj = sps[j];
           if (j != s)
-            pair_terms(xi, yi, zi, qi, si, xj, yj, zj, qj, sps + j, true, P, tab, Lx, hx, Lz, hz, psi2, cut2, lB,
-                       scale, fx, fy, fz, cnt);
+            pair_terms(xi, yi, zi, qi, si, xj, yj, zj, qj, sj, true, P, tab, Lx, hx, Lz, hz, psi2, lB, scale, fx,
+                       fy, fz, cnt);
           if (img) {
             // a metal strip in the bottom wall: the partner's image is the
             // conducting wall's (opposite sign) above the strip's columns
             const T sgj = P.strip ? (on_strip(P, (int)floor(xj)) ? T(-1) : T(1)) : sg0;
             if (near0)
-              pair_terms(xi, yi, zi, qi, si, xj, -yj, zj, sgj * qj, static_cast<const int*>(nullptr), false, P, tab,
-                         Lx, hx, Lz, hz, psi2, psi2, lB, scale, fx, fy, fz, cnt);
+              pair_terms(xi, yi, zi, qi, si, xj, -yj, zj, sgj * qj, 0, false, P, tab, Lx, hx, Lz, hz, psi2, lB,
+                         scale, fx, fy, fz, cnt);
             if (near1)
-              pair_terms(xi, yi, zi, qi, si, xj, sub_rn(twoNy, yj), zj, sg1 * qj, static_cast<const int*>(nullptr),
-                         false, P, tab, Lx, hx, Lz, hz, psi2, psi2, lB, scale, fx, fy, fz, cnt);
+              pair_terms(xi, yi, zi, qi, si, xj, sub_rn(twoNy, yj), zj, sg1 * qj, 0, false, P, tab, Lx, hx, Lz,
+                         hz, psi2, lB, scale, fx, fy, fz, cnt);
           }
         }
       }

@@ -62,41 +62,20 @@ __device__ __forceinline__ T fp_lookup(const T* __restrict__ tab, int n_tab, T s
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
-// The largest squared cutoff of a pair (psi or any LJ cutoff), rounded as
-// pair_terms rounds each: a candidate beyond it is rejected before the
-// partner's species is read.
-template <typename T>
-__device__ __forceinline__ T pair_cut2(const Params& P, T psi2) {
-  const auto& Q = phys(P, T());
-  T c = psi2;
-  for (int a = 0; a < P.nspecies; ++a)
-    for (int b = 0; b < P.nspecies; ++b) {
-      const T rc = T(Q.lj_rc[a][b]);
-      const T r = mul_rn(rc, rc);
-      c = r > c ? r : c;
-    }
-  return c;
-}
-
-// spj: the partner's species (read only inside the cutoff), null for an image.
 template <typename T>
 __device__ __forceinline__ void pair_terms(const T xi, const T yi, const T zi, const T qi, const int si,
-                                           const T xj, const T yj, const T zj, const T qj, const int* spj,
+                                           const T xj, const T yj, const T zj, const T qj, const int sj,
                                            bool real, const Params& P, const T* __restrict__ tab, T Lx, T hx,
-                                           T Lz, T hz, T psi2, T cut2, T lB, T scale, T& fx, T& fy, T& fz,
-                                           int& cnt) {
+                                           T Lz, T hz, T psi2, T lB, T scale, T& fx, T& fy, T& fz, int& cnt) {
   const auto& Q = phys(P, T());
   T ddx = min_image(sub_rn(xi, xj), Lx, hx);
   T ddy = sub_rn(yi, yj);
   T ddz = min_image(sub_rn(zi, zj), Lz, hz);
   T r2 = add_rn(add_rn(mul_rn(ddx, ddx), mul_rn(ddy, ddy)), mul_rn(ddz, ddz));
-  if (!(r2 < cut2)) return;
   bool in_psi = r2 < psi2;
   bool in_lj = false;
-  int sj = 0;
   T rcl = T(0);
   if (real) {
-    sj = *spj;
     rcl = T(Q.lj_rc[si][sj]);
     in_lj = r2 < mul_rn(rcl, rcl);
   }
