@@ -680,13 +680,15 @@ __global__ void k_stokes_sweep(cplx<float>* __restrict__ S, cplx<float>* __restr
     C<float> gprev = gsum(ldcf(Su), ldcf(Sw));
     C<float> y1 = cz<float>(), y2 = cz<float>();
     for (int fb = 1; fb < Ny; fb += SB_STOKES) {
-      C<float> g[SB_STOKES], fy[SB_STOKES];
+      // raw loads first (nothing computed from them until all are issued)
+      C<float> ux[SB_STOKES], uz[SB_STOKES], fy[SB_STOKES];
       float l1[SB_STOKES], l2[SB_STOKES];
 #pragma unroll
       for (int r = 0; r < SB_STOKES; ++r) {
         const int f = fb + r;
         const bool in = f < Ny;
-        g[r] = in ? gsum(ldcf(Su + (size_t)f * Px), ldcf(Sw + (size_t)f * Px)) : cz<float>();
+        ux[r] = in ? ldcf(Su + (size_t)f * Px) : cz<float>();
+        uz[r] = in ? ldcf(Sw + (size_t)f * Px) : cz<float>();
         fy[r] = in ? ldcf(Sv + (size_t)f * Px) : cz<float>();
         l1[r] = in ? L1[(size_t)f * M + mode] : 0.f;
         l2[r] = in ? L2[(size_t)f * M + mode] : 0.f;
@@ -695,11 +697,12 @@ __global__ void k_stokes_sweep(cplx<float>* __restrict__ S, cplx<float>* __restr
       for (int r = 0; r < SB_STOKES; ++r) {
         const int f = fb + r;
         if (f < Ny) {
+          const C<float> g = gsum(ux[r], uz[r]);
           const C<float> rhs =
-              cscale(ieta, C<float>{K2 * fy[r].r + (g[r].r - gprev.r), K2 * fy[r].i + (g[r].i - gprev.i)});
+              cscale(ieta, C<float>{K2 * fy[r].r + (g.r - gprev.r), K2 * fy[r].i + (g.i - gprev.i)});
           const C<float> y = csub2(csub2(rhs, cscale(l1[r], y1)), cscale(l2[r], y2));
           stcf(Sv + (size_t)f * Px, y, 1.f);
-          y2 = y1; y1 = y; gprev = g[r];
+          y2 = y1; y1 = y; gprev = g;
         }
       }
     }

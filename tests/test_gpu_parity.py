@@ -78,7 +78,8 @@ BCS = [(0, 0), (1, 1), (0, 1), (1, 0)]
 
 
 # fx_pairs = 0: the bulk-staged persistent x transform
-SHAPES = [(1, 32, 1), (4, 64, 4), (16, 256, 16), (32, 512, 2), (0, 32, 4), (0, 32, 16)]
+# fz_tile = 0: the TMA-tiled z transform (single precision only; the FP64 handle rejects it)
+SHAPES = [(1, 32, 1), (4, 64, 4), (16, 256, 16), (32, 512, 2), (0, 32, 4), (0, 32, 16), (0, 32, 0), (4, 64, 0)]
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -93,6 +94,10 @@ def test_transform_shapes(prec, shape):
     cfg.eta = 0.7
     cfg.wet = True
     h = dg.Discos(cfg)
+    if shape[2] == 0 and prec == dg.FP64:
+        with pytest.raises(dg.DiscosError):
+            h.set_transform_shape(*shape)
+        return
     h.set_transform_shape(*shape)
     Nx, Ny, Nz = cfg.dims
     rho = rng.normal(size=(Nz, Ny, Nx))
@@ -149,7 +154,8 @@ def test_transform_tuner(prec):
     cfg.precision = prec
     h = dg.Discos(cfg)
     pp, th, tk, ms = h.tune_transforms()
-    assert (pp == 0 or (1 <= pp and pp * cfg.Nx <= 2048)) and th % 32 == 0 and tk in (1, 2, 4, 8, 16)
+    # 0: the bulk-staged x kernel / the TMA-tiled z kernel
+    assert (pp == 0 or (1 <= pp and pp * cfg.Nx <= 2048)) and th % 32 == 0 and tk in (0, 1, 2, 4, 8, 16)
     assert min(ms) > 0
     xd, qd, pos, q, _ = _setup(cfg, rec, prec)
     rho = h.spread_charge(xd, qd)
