@@ -64,3 +64,40 @@ def test_binding_rejects_bad_arrays():
     for bad in (torch.zeros(10), torch.zeros(5, dtype=torch.float32), torch.zeros(20, dtype=torch.float32)[::2]):
         with pytest.raises(ValueError):
             dg._need(bad, 10, torch.float32, "q")                 # on the host, short, or strided
+
+
+def _c_offsets(struct, fields):
+    """offsetof() of each field and sizeof() of the struct, from a tiny C
+    program compiled against include/discos.h with the host compiler."""
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(ROOT, "include")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "discos.h"', "int main(void) {"]
+    lines.append(f'  printf("size %zu\\n", sizeof({struct}));')
+    for f in fields:
+        lines.append(f'  printf("{f} %zu\\n", offsetof({struct}, {f}));')
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "l.c"), os.path.join(d, "l")
+        open(src, "w").write("\n".join(lines))
+        subprocess.run([cc, "-I", inc, src, "-o", exe], check=True, capture_output=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    return {k: int(v) for k, v in (l.split() for l in out.splitlines())}
+
+
+@pytest.mark.parametrize("pystruct,cstruct", [("Config", "discos_config"), ("Batch", "discos_batch")])
+def test_binding_struct_layout_matches_header(pystruct, cstruct):
+    """The ctypes mirrors of the C structs have the header's field offsets
+    and size, so the library reads every field the binding writes."""
+    import ctypes
+    from paper_2204_14167_gb300 import _lib
+    S = getattr(_lib, pystruct)
+    names = [f[0] for f in S._fields_]
+    c = _c_offsets(cstruct, names)
+    assert c["size"] == ctypes.sizeof(S)
+    for n in names:
+        assert c[n] == getattr(S, n).offset, n
