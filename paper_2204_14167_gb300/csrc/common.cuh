@@ -110,6 +110,23 @@ template <typename T> __host__ __device__ __forceinline__ T kval(T z, const Kern
   return eskernel(z, kp);
 }
 
+// Single precision: the square root of Eq. peskin1d through the hardware
+// reciprocal square root (about 2 ulp), x * rsqrt(x); its argument lies in
+// [1, 2] inside the support.
+__host__ __device__ __forceinline__ float sqrt_pos(float x) {
+#ifdef __CUDA_ARCH__
+  return x > 0.f ? x * rsqrtf(x) : 0.f;
+#else
+  return x > 0.f ? sqrtf(x) : 0.f;
+#endif
+}
+__host__ __device__ __forceinline__ float peskin4(float z) {
+  const float a = fabsf(z);
+  if (a <= 1.f) return (3.f - 2.f * a + sqrt_pos(1.f + 4.f * a - 4.f * a * a)) * 0.125f;
+  if (a <= 2.f) return (5.f - 2.f * a - sqrt_pos(-7.f + 12.f * a - 4.f * a * a)) * 0.125f;
+  return 0.f;
+}
+
 // Derivatives d phi / dz of the three kernels (used by the thermal forcing,
 // whose random finite difference is evaluated in its delta -> 0 form).
 template <typename T> __device__ __forceinline__ T peskin4_d(T z) {
@@ -124,6 +141,16 @@ template <typename T> __device__ __forceinline__ T peskin4_d(T z) {
     return sg * (T(-2) - (T(6) - T(4) * a) / s) * T(0.125);
   }
   return T(0);
+}
+// single precision: 1 / sqrt through the hardware reciprocal square root
+__device__ __forceinline__ float peskin4_d(float z) {
+  const float a = fabsf(z), sg = z < 0.f ? -1.f : 1.f;
+  if (a <= 1.f) return sg * (-2.f + (2.f - 4.f * a) * rsqrtf(1.f + 4.f * a - 4.f * a * a)) * 0.125f;
+  if (a < 2.f) {
+    const float s = -7.f + 12.f * a - 4.f * a * a;
+    return s > 0.f ? sg * (-2.f - (6.f - 4.f * a) * rsqrtf(s)) * 0.125f : 0.f;
+  }
+  return 0.f;
 }
 template <typename T> __device__ __forceinline__ T peskin6_d(T z) {
   if (!(fabs(z) < T(3))) return T(0);
