@@ -314,10 +314,10 @@ __global__ void k_interp_velocity_w(const T* __restrict__ x, int N, Params P, co
       const int ix = (st[0] + l) & (Nx - 1);
 #pragma unroll
       for (int jz = 0; jz < W; ++jz) {
-        const size_t zoff = (size_t)((st[2] + jz) & (Nz - 1)) * Nyg * Nx + ix;
+        const T* gz = g + (size_t)((st[2] + jz) & (Nz - 1)) * Nyg * Nx + ix;
         T a = T(0);
 #pragma unroll
-        for (int jy = 0; jy < W; ++jy) a += wy[jy] * g[zoff + roff[jy]];
+        for (int jy = 0; jy < W; ++jy) a += wy[jy] * gz[roff[jy]];
         acc += a * wz[jz];
       }
       acc *= wv[0];

@@ -268,17 +268,24 @@ __global__ void k_spread_force_w(const T* __restrict__ x, const T* __restrict__ 
   }
   if (valid && l < W) {
     const int ix = (st[0] + l) & (Nx - 1);
+    // value at (jy, jz) = ay[jy] wz[jz] + cy[jy] dz[jz]: the force term
+    // Fc wx wy wz and the three RFD terms a W_d (d/dd of the kernel product)
+    // grouped by their z factor, so a point costs one multiply-add pair
     const T fx0 = Fc * wv[0];
     const T r0 = a * Wr[0] * wd[0], r1 = a * Wr[1] * wv[0], r2 = a * Wr[2] * wv[0];
+    T ay[W], cy[W];
+#pragma unroll
+    for (int jy = 0; jy < W; ++jy) {
+      ay[jy] = rfd ? (fx0 + r0) * wy[jy] + r1 * dy[jy] : fx0 * wy[jy];
+      cy[jy] = rfd ? r2 * wy[jy] : T(0);
+    }
 #pragma unroll
     for (int jz = 0; jz < W; ++jz) {
-      const size_t zoff = (size_t)((st[2] + jz) & (Nz - 1)) * Nyg * Nx + ix;
+      T* gz = g + (size_t)((st[2] + jz) & (Nz - 1)) * Nyg * Nx + ix;
 #pragma unroll
       for (int jy = 0; jy < W; ++jy) {
         if (wy[jy] == T(0) && dy[jy] == T(0)) continue;
-        T val = fx0 * wy[jy] * wz[jz];
-        if (rfd) val += r0 * wy[jy] * wz[jz] + r1 * dy[jy] * wz[jz] + r2 * wy[jy] * dz[jz];
-        atomicAdd(&g[zoff + roff[jy]], val);
+        atomicAdd(gz + roff[jy], ay[jy] * wz[jz] + cy[jy] * dz[jz]);
       }
     }
   }
