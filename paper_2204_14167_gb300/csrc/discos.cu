@@ -431,8 +431,6 @@ discos_status step_impl(discos_handle* h, T* x, const T* q, const int* species, 
         e = launch_neutral_flag(W.nsum, surface_total(h, false), surface_total(h, true), neutral_tol(h), W.fault, s);
       if (e != cudaSuccess) return cuda_status(e, "discos_step");
     }
-    // the stochastic stress (or a zero fill) initialises the fluid forcing on
-    // the side stream, overlapping the electrostatics
     // the fluid forcing starts from zero; the stochastic stress is added on
     // the side stream while the main stream spreads the forces into the same
     // grid (both with atomics)
