@@ -101,3 +101,70 @@ def test_binding_struct_layout_matches_header(pystruct, cstruct):
     assert c["size"] == ctypes.sizeof(S)
     for n in names:
         assert c[n] == getattr(S, n).offset, n
+
+
+def _prototypes():
+    """(name, return type, [parameter types]) of every function the header
+    declares, comments stripped."""
+    src = open(os.path.join(ROOT, "include", "discos.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    out = []
+    for m in re.finditer(r"([A-Za-z_][A-Za-z_0-9 \*]*?)\b(discos_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+        params = " ".join(m.group(3).split())
+        types = []
+        if params != "void":
+            for p in params.split(","):
+                p = p.strip()
+                # drop the parameter name: the last identifier when it follows a type
+                t = re.sub(r"\s*\b[A-Za-z_][A-Za-z_0-9]*$", "", p) if re.search(r"[\s\*][A-Za-z_]\w*$", p) else p
+                types.append(" ".join(t.replace("*", " * ").split()))
+        ret = " ".join(m.group(1).replace("*", " * ").split())
+        out.append((m.group(2), ret, types))
+    return out
+
+
+def _ctype_kind(t):
+    """The ctypes class family one C parameter type must be bound with."""
+    import ctypes
+    if "*" in t or t in ("discos_alloc_fn", "discos_free_fn"):
+        return "pointer"
+    scalar = {"int": ctypes.c_int, "int64_t": ctypes.c_int64, "double": ctypes.c_double, "float": ctypes.c_float,
+              "unsigned": ctypes.c_uint, "size_t": ctypes.c_size_t, "long long": ctypes.c_longlong}
+    return scalar[t.replace("const ", "")]
+
+
+def _is_pointer_type(ct):
+    import ctypes
+    return ct in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(ct, ctypes._Pointer)
+
+
+def test_binding_prototypes_match_header(lib):
+    """Every entry point is called with the header's number of arguments,
+    each bound with a matching ctypes type (a pointer for a pointer, the
+    same integer width, double for double), and returns what the header
+    says: a wrong width or a missing argument would hand the library garbage."""
+    import ctypes
+    protos = _prototypes()
+    assert len(protos) == len(_declared())
+    for name, ret, types in protos:
+        fn = getattr(lib, name)
+        if types:
+            assert fn.argtypes is not None and len(fn.argtypes) == len(types), name
+            for i, (t, ct) in enumerate(zip(types, fn.argtypes)):
+                kind = _ctype_kind(t)
+                if kind == "pointer":
+                    assert _is_pointer_type(ct), (name, i, t, ct)
+                else:
+                    assert ct is kind or ctypes.sizeof(ct) == ctypes.sizeof(kind) and ct._type_ == kind._type_, \
+                        (name, i, t, ct)
+        else:
+            assert not fn.argtypes, name
+        if ret == "discos_status":
+            assert fn.restype is ctypes.c_int, name
+        elif ret == "const char *":
+            assert fn.restype is ctypes.c_char_p, name
+        elif ret == "long long":
+            assert fn.restype is ctypes.c_longlong, name
+        else:
+            raise AssertionError(f"{name}: unexpected return type {ret!r}")
