@@ -574,15 +574,14 @@ def _peaks():
         return None
 
 
-# DRAM bytes per launch of a family (cold-cache, one ncu capture of one
-# measured step of `bench.py --profile`; the command and the per-kernel table
-# are in profiles/transforms_scans_dram_wet_channel_128x64x128.md).
 # DRAM bytes (read + write) per launch from ncu captures of the current kernels
-# on the 256 x 128 x 256 channel (profiles/kernels_iceo_channel_256x128x256.md),
-# averaged over a step's launches of the family; none yet for 128 x 64 x 128
+# on the 256 x 128 x 256 channel (the per-kernel summary of that channel under
+# profiles/), averaged over a step's launches of the family; a family whose
+# kernel changed after its capture has no entry (reported as null), and the
+# 128 x 64 x 128 channel has none
 MEASURED_TRAFFIC = {"wet_channel_128x64x128": {},
                     "iceo_channel_256x128x256": {"fft_z": 100.7e6, "fft_x": 98.3e6, "stokes_y": 451.6e6,
-                                                 "spread_force": 156.3e6, "interp_v": 111.5e6, "noise": 139.3e6,
+                                                 "spread_force": 156.3e6, "interp_v": 111.5e6,
                                                  "interp_e": 45.0e6, "spread_charge": 40.0e6, "near_field": 8.5e6}}
 
 

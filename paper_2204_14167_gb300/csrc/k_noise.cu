@@ -7,12 +7,17 @@
 // operator with those walls (discrete fluctuation-dissipation balance).  Normals come from Philox counters
 // (cell of an Nx x (Ny+1) x Nz lattice, step, 0, tag 3 / tag 4).
 //
-// Each block generates Z for a 32 x 8 x 8 tile of cells plus a one-cell halo
-// in shared memory (two Philox draws per halo cell; of the second only the
-// two normals that are used) and then forms the three face divergences of
-// its cells, adding them to the force grids with atomics: the step runs this
-// kernel on its side stream while the force spreading adds into the same
-// (zeroed) grids on the main stream.
+// Each block generates Z for a 32 x 8 x 8 tile of cells plus the six faces of
+// its one-cell halo in shared memory and then forms the three face
+// divergences of its cells, adding them to the force grids with atomics: the
+// step runs this kernel on its side stream while the force spreading adds
+// into the same (zeroed) grids on the main stream.  A tile cell takes two
+// Philox draws (A: xx, yy | zz, xy; B: xz, yz); a halo face takes only the
+// draws whose entries the divergences read there (the low x and y faces the
+// first normal pair of A, the low z face all of A, the high x and y faces
+// the second pair of A and B, the high z face B).  The halo's edges and
+// corners are never read.  Every entry keeps the value of its own counter,
+// whichever draws a cell takes.
 #include <atomic>
 #include "internal.h"
 
@@ -24,8 +29,46 @@ constexpr int TX = 32, TY = 8, TZ = 8;
 constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
 constexpr int HN = HX * HY * HZ;
 
+constexpr int N_TILE = TX * TY * TZ;
+constexpr int N_XF = TY * TZ, N_YF = TX * TZ, N_ZF = TX * TY;   // cells of one halo face
+constexpr int N_HALO_ITEMS = N_TILE + 2 * (N_XF + N_YF + N_ZF);
+// draws a halo item takes: bit 0 the first normal pair of A, bit 1 its
+// second pair, bit 2 draw B
+constexpr unsigned DRAW_A01 = 1u, DRAW_A23 = 2u, DRAW_B = 4u;
+
+// Item t of a block's halo fill: the tile's cells first, then the low and
+// high x faces, the y faces and the z faces.  Every segment is a multiple of
+// 32 items long, so the draws a warp takes are the same for all its lanes.
+__device__ __forceinline__ void halo_item(int t, int& hx, int& hy, int& hz, unsigned& need) {
+  if (t < N_TILE) {
+    hx = 1 + t % TX; hy = 1 + (t / TX) % TY; hz = 1 + t / (TX * TY);
+    need = DRAW_A01 | DRAW_A23 | DRAW_B;
+    return;
+  }
+  t -= N_TILE;
+  if (t < 2 * N_XF) {
+    const int hi = t / N_XF, r = t - hi * N_XF;
+    hx = hi ? TX + 1 : 0; hy = 1 + r % TY; hz = 1 + r / TY;
+    need = hi ? (DRAW_A23 | DRAW_B) : DRAW_A01;
+    return;
+  }
+  t -= 2 * N_XF;
+  if (t < 2 * N_YF) {
+    const int hi = t / N_YF, r = t - hi * N_YF;
+    hy = hi ? TY + 1 : 0; hx = 1 + r % TX; hz = 1 + r / TX;
+    need = hi ? (DRAW_A23 | DRAW_B) : DRAW_A01;
+    return;
+  }
+  t -= 2 * N_YF;
+  const int hi = t / N_ZF, r = t - hi * N_ZF;
+  hz = hi ? TZ + 1 : 0; hx = 1 + r % TX; hy = 1 + r / TX;
+  need = hi ? DRAW_B : (DRAW_A01 | DRAW_A23);
+}
+
 template <typename T>
 __global__ void k_stress_noise(T* __restrict__ f, Params P, long long step, T amp) {
+  static_assert(N_TILE % 32 == 0 && N_XF % 32 == 0 && N_YF % 32 == 0 && N_ZF % 32 == 0,
+                "halo segments must be whole warps");
   extern __shared__ unsigned char smem_raw[];
   T (*Zd)[HN] = reinterpret_cast<T (*)[HN]>(smem_raw);            // xx, yy, zz
   T (*Ze)[HN] = reinterpret_cast<T (*)[HN]>(smem_raw) + 3;        // xy, xz, yz
@@ -33,26 +76,37 @@ __global__ void k_stress_noise(T* __restrict__ f, Params P, long long step, T am
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * TZ;
   const int tid = threadIdx.x;
   const T r2 = T(1.4142135623730951);
-  for (int h = tid; h < HN; h += blockDim.x) {
-    int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+  for (int t = tid; t < N_HALO_ITEMS; t += blockDim.x) {
+    int hx, hy, hz;
+    unsigned need;
+    halo_item(t, hx, hy, hz, need);
+    const int h = (hz * HY + hy) * HX + hx;
     int i = (i0 + hx - 1) & (Nx - 1);
     int j = j0 + hy - 1;
     int k = (k0 + hz - 1) & (Nz - 1);
-    T a[4] = {T(0), T(0), T(0), T(0)}, b[4] = {T(0), T(0), T(0), T(0)};
-    if (j >= 0 && j <= Ny) {
+    T a[4] = {T(0), T(0), T(0), T(0)}, b[2] = {T(0), T(0)};
+    const bool edge_row = j >= 0 && j <= Ny;      // xy and yz live on j = 0..Ny
+    if (edge_row) {
       uint32_t cell = (uint32_t)(((size_t)k * (Ny + 1) + j) * Nx + i);
-      normals4(u32x4{cell, (uint32_t)step, 0u, (uint32_t)TAG_STRESS_A}, P.seed, a);
-      normals2(u32x4{cell, (uint32_t)step, 0u, (uint32_t)TAG_STRESS_B}, P.seed, b);
+      if (need & DRAW_A23) normals4(u32x4{cell, (uint32_t)step, 0u, (uint32_t)TAG_STRESS_A}, P.seed, a);
+      else if (need & DRAW_A01) normals2(u32x4{cell, (uint32_t)step, 0u, (uint32_t)TAG_STRESS_A}, P.seed, a);
+      if (need & DRAW_B) normals2(u32x4{cell, (uint32_t)step, 0u, (uint32_t)TAG_STRESS_B}, P.seed, b);
     }
-    bool centre = j >= 0 && j < Ny;
+    const bool centre = j >= 0 && j < Ny;
     // wall edges: sqrt 2 at a no-slip wall, no shear stress at a slip wall
-    T wall = j == 0 ? (P.slip[0] ? T(0) : r2) : (j == Ny ? (P.slip[1] ? T(0) : r2) : T(1));
-    Zd[0][h] = centre ? r2 * a[0] : T(0);
-    Zd[1][h] = centre ? r2 * a[1] : T(0);
-    Zd[2][h] = centre ? r2 * a[2] : T(0);
-    Ze[0][h] = (j >= 0 && j <= Ny) ? wall * a[3] : T(0);   // xy
-    Ze[1][h] = centre ? b[0] : T(0);                         // xz
-    Ze[2][h] = (j >= 0 && j <= Ny) ? wall * b[1] : T(0);   // yz
+    const T wall = j == 0 ? (P.slip[0] ? T(0) : r2) : (j == Ny ? (P.slip[1] ? T(0) : r2) : T(1));
+    if (need & DRAW_A01) {
+      Zd[0][h] = centre ? r2 * a[0] : T(0);
+      Zd[1][h] = centre ? r2 * a[1] : T(0);
+    }
+    if (need & DRAW_A23) {
+      Zd[2][h] = centre ? r2 * a[2] : T(0);
+      Ze[0][h] = edge_row ? wall * a[3] : T(0);                // xy
+    }
+    if (need & DRAW_B) {
+      Ze[1][h] = centre ? b[0] : T(0);                         // xz
+      Ze[2][h] = edge_row ? wall * b[1] : T(0);                // yz
+    }
   }
   __syncthreads();
   const size_t G = (size_t)Nx * Ny * Nz;
