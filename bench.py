@@ -78,25 +78,33 @@ def clocks_sampler():
         except Exception:
             p.kill()
         f.close()
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(path):
-            parts = [s.strip() for s in line.split(",")]
-            if len(parts) < 9 or parts[0] != str(dev):
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
-            return None
-        sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        with open(path) as lines:
+            return parse_clocks(lines, dev)
     return stop
+
+
+def parse_clocks(lines, dev):
+    """Summary of nvidia-smi samples (the query of clocks_sampler, csv without
+    header or units) for GPU `dev`: median SM clock under load, the maximum
+    SM clock, and every throttle reason seen active; None without samples."""
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [s.strip() for s in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(dev):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx = float(parts[2])
+        except ValueError:
+            continue
+        for n, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not sm:
+        return None
+    sm.sort()
+    return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # Conjugate-gradient iterations the oracle's Poisson solve (rtol 1e-13,

@@ -56,3 +56,22 @@ def test_single_process_rate():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.whole_job_rate(500.0, 10.0) == (50000.0, 10.0)
+
+
+def test_clock_samples_summary():
+    """The clock record of a bench line: median SM clock of the sampled GPU
+    only, its maximum clock, and every throttle reason seen active."""
+    sys.path.insert(0, ROOT)
+    import bench
+    lines = [
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "1, 1200, 2070, 300.0, 0x0000000000000008, Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1400.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1010.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+    ]
+    c = bench.parse_clocks(lines, 0)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert bench.parse_clocks(lines, 1)["reasons"] == ["hw_slowdown"]
+    assert bench.parse_clocks(lines, 3) is None
